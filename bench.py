@@ -1,0 +1,445 @@
+#!/usr/bin/env python3
+"""Light-field rendering benchmark: DirectL vs the standard paradigm on GB300.
+
+Workload (``--workload 4k``, the default): a 3840x2160 lenticular panel with
+45 views (pitch 8.1 subpixels, slant tan 0.18, offset 0, views spanning 40
+degrees at distance 4, fov 40 degrees) and a seeded synthetic scene of 1M
+Gaussians, SH degree 3, scale/rotation/opacity/SH stored in BF16 (means FP32),
+with a 200-pose camera path sweeping the light-field centre's yaw over +-5
+degrees.
+
+One step = one DirectL light-field frame through the C ABI: view cameras,
+multi-view EWA projection with SH colour, tile keys and the depth sort, and
+front-to-back compositing of the required rays straight into the encoded
+image.  The standard paradigm (every view rendered at panel resolution with
+the tile rasteriser, then interweaved) is timed the same way on the same GPU
+and reported under "standard".  Every step works on more than L2's worth of
+data (2.2 GB of per-view splat records alone), so no L2 flush is added.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(a bounded sample of rays per step, extrapolated to frames/s).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "light-field frames/s & subpixels/s: DirectL vs 45-view+interweave, same GB300, at oracle tol"
+# compositing work per (ray, Gaussian) pair: dx, dy (2), quadratic form (9),
+# clamp and threshold compare (2) -> 13 FP32 ops + 1 ex2; a composited pair
+# adds T(1-alpha), alpha*T and three colour FMAs (9 more).
+FLOP_PER_EVAL = 13
+FLOP_PER_BLEND = 9
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="4k", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--no-standard", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(wl: W.Workload) -> str:
+    d, s = wl.display, wl.scene
+    return (f"{wl.name}: {d.width}x{d.height} panel, {d.num_views} views, pitch {d.pitch_lx}, "
+            f"slant {d.tan_slant:.4g}, P_w {d.p_w}; {s.n} Gaussians SH{s.sh_degree} "
+            f"{s.layout}, {s.dtype} storage")
+
+
+# --------------------------------------------------------------- ranks ----
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        import torch
+        if not torch.cuda.is_available():
+            backend = "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Maximum of a float over ranks (the slowest rank sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(self.REASONS, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_id_for(device_index: int) -> str:
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(device_index).uuid
+        return "GPU-" + str(u)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[device_index] if vis else str(device_index)
+
+
+# --------------------------------------------------------- CPU oracle -----
+def oracle_frame_estimate(wl: W.Workload, per_view: int, seed: int, n_rays_frame: int,
+                          scene=None, tables=None) -> dict:
+    """Time the FP64 oracle on two ray samples of a DirectL frame and
+    extrapolate a whole frame: T = N_v * T_project + N_rays * T_ray.
+
+    Sample A holds one ray per view, sample B ``per_view`` rays per view, all
+    drawn from the oracle's own view map and repurposing table."""
+    import oracle
+    d = wl.display
+    if tables is None:
+        V = oracle.view_map(d)
+        tables = (V, oracle.repurpose(d, V))
+    V, src = tables
+    if scene is None:
+        scene = oracle.Scene(W.make_scene(wl.scene) if wl.scene.dtype == "f32" else
+                             W.quantise_storage(W.make_scene(wl.scene), wl.scene.dtype))
+    rng = np.random.default_rng(seed)
+    sub = rng.integers(0, 3 * d.width * d.height, size=400 * d.num_views)
+    rays = oracle.subpixel_rays(d, sub, V, src)
+    picks_a, picks_b = [], []
+    for v in range(d.num_views):
+        idx = np.where(rays[:, 0] == v)[0]
+        if idx.size == 0:
+            continue
+        picks_a.append(idx[:1])
+        picks_b.append(idx[:per_view])
+    ra = rays[np.concatenate(picks_a)]
+    rb = rays[np.concatenate(picks_b)]
+    L0 = W.light_field_centre(wl.camera_distance, 1.0)
+    t0 = time.perf_counter()
+    oracle.render_rays(scene, d, L0, ra)
+    ta = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render_rays(scene, d, L0, rb)
+    tb = time.perf_counter() - t0
+    nv = len(picks_a)
+    t_ray = max((tb - ta) / max(rb.shape[0] - ra.shape[0], 1), 1e-9)
+    t_proj = max((ta - ra.shape[0] * t_ray) / nv, 0.0)
+    frame_s = d.num_views * t_proj + n_rays_frame * t_ray
+    return {"frame_s": frame_s, "t_project_view_s": t_proj, "t_ray_s": t_ray,
+            "sample_s": ta + tb, "rays_sampled": int(ra.shape[0] + rb.shape[0]),
+            "threads": oracle.max_threads()}
+
+
+def run_reference(args):
+    """FP64 oracle arm: each step times a bounded ray sample and extrapolates."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    wl = W.WORKLOADS[args.workload]
+    d = wl.display
+    V = oracle.view_map(d)
+    src = oracle.repurpose(d, V)
+    _, rays = oracle.ray_table(d, V, src)
+    n_rays = int(rays.shape[0])
+    sc = W.make_scene(wl.scene)
+    scene = oracle.Scene(W.quantise_storage(sc, wl.scene.dtype))
+    frame_times, last = [], None
+    for i in range(args.warmup + args.steps):
+        est = oracle_frame_estimate(wl, 4, 100 + i, n_rays, scene, (V, src))
+        if i >= args.warmup:
+            frame_times.append(est["frame_s"])
+        last = est
+    ms = 1e3 * statistics.mean(frame_times)
+    fps = 1e3 / ms
+    cores = int(last["threads"])
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": workload_desc(wl), "global_batch": 1, "parallelism": "none"},
+            "subpixels_per_s": fps * 3 * d.width * d.height,
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": ("per step: one ray per view, then 4 rays per view "
+                                        f"({last['rays_sampled']} rays, all 45 views projected "
+                                        "twice); frame time extrapolated as N_v*T_project + "
+                                        f"N_rays*T_ray with N_rays={n_rays}")},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------- GPU arm ----
+def timed_loop(fn, steps, world, device):
+    import torch
+    barrier(world)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for i in range(steps):
+        fn(i)
+    end.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    return start.elapsed_time(end)
+
+
+def per_frame(totals: dict, n: int) -> dict:
+    keys = ("ms_project", "ms_scan", "ms_sync", "ms_emit", "ms_sort", "ms_ranges", "ms_composite",
+            "ms_interweave", "ms_total")
+    out = {k[3:]: totals[k] / max(n, 1) for k in keys}
+    out["keys"] = totals["n_keys"] / max(n, 1)
+    out["pairs_evaluated"] = totals["pairs_evaluated"] / max(n, 1)
+    out["pairs_blended"] = totals["pairs_blended"] / max(n, 1)
+    return out
+
+
+def load_traffic(kernel: str, workload: str, source_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(f"{kernel}@{workload}")
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha256(open(source_file, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    from paper_2407_14053_gb300 import Renderer
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.WORKLOADS[args.workload]
+    d = wl.display
+    scene = W.make_scene(wl.scene)
+    r = Renderer(local)
+    sid = r.load_gaussians(scene, wl.scene.dtype)
+    t0 = time.perf_counter()
+    did = r.set_display(d)
+    offline_s = time.perf_counter() - t0
+    n_rays, beta = r.display_info(did)
+    poses = W.camera_path(200, wl.camera_distance, 10.0)
+    out = torch.empty((d.height, d.width, 3), dtype=torch.float32, device=dev)
+    subpix = 3 * d.width * d.height
+
+    # ---- DirectL frames ----
+    for i in range(args.warmup):
+        r.render(sid, did, poses[i % 200], "directl", out)
+    r.enable_stage_timing(True)
+    torch.cuda.synchronize()
+    r.stage_totals()
+    sampler = ClockSampler(gpu_id_for(local)).start() if rank == 0 else None
+    ms = timed_loop(lambda i: r.render(sid, did, poses[i % 200], "directl", out), args.steps, world,
+                    dev)
+    clocks = sampler.stop() if sampler else None
+    tot, nf = r.stage_totals()
+    dl_stages = per_frame(tot, nf)
+    launches = int(tot["n_launches"])
+    ms_max = reduce_max(ms, world, dev)
+    frames_total = reduce_sum(args.steps, world, dev)
+    fps = frames_total / (ms_max / 1e3)
+
+    # ---- standard paradigm ----
+    std = None
+    if not args.no_standard:
+        k_std = max(3, args.steps // 2)
+        for i in range(2):
+            r.render(sid, did, poses[i % 200], "standard", out)
+        torch.cuda.synchronize()
+        r.stage_totals()
+        ms_s = timed_loop(lambda i: r.render(sid, did, poses[(7 * i) % 200], "standard", out), k_std,
+                          world, dev)
+        tot_s, nf_s = r.stage_totals()
+        ms_s = reduce_max(ms_s, world, dev)
+        fps_s = reduce_sum(k_std, world, dev) / (ms_s / 1e3)
+        std = {"frames_per_s": fps_s, "subpixels_per_s": fps_s * subpix, "ms_per_frame": ms_s / k_std,
+               "steps": k_std, "stages_ms": per_frame(tot_s, nf_s),
+               "speedup_directl_over_standard": fps / fps_s}
+    r.enable_stage_timing(False)
+
+    # ---- end to end through the C ABI with a host (pinned) frame ----
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((d.height, d.width, 3), dtype=torch.float32).pin_memory()
+        for i in range(2):
+            r.render_to_host(sid, did, poses[i % 200], host, "directl")
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            r.render_to_host(sid, did, poses[i % 200], host, "directl")
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier(world)
+        wall = reduce_max(wall, world, dev)
+        cam_bytes = 15 * 4 * 128 * math.ceil(d.num_views / 128)
+        e2e = {"value": reduce_sum(args.steps, world, dev) / wall, "unit": "frames/s",
+               "h2d_bytes_per_step": cam_bytes, "d2h_bytes_per_step": 12 * d.width * d.height}
+
+    # ---- roofline of the compositing kernel (ALU bound) ----
+    comp_ms = dl_stages["composite"]
+    flops = FLOP_PER_EVAL * dl_stages["pairs_evaluated"] + FLOP_PER_BLEND * dl_stages["pairs_blended"]
+    clk = 2070.0
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    achieved = flops / (comp_ms / 1e3) / 1e12 if comp_ms > 0 else 0.0
+    src_file = os.path.join(ROOT, "paper_2407_14053_gb300", "csrc", "composite.cu")
+    roofline = {"kernel": "composite_rays_kernel", "bound": "alu", "achieved": achieved,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+                "traffic": load_traffic("composite_rays_kernel", args.workload, src_file),
+                "flop_per_launch": flops, "ms_per_launch": comp_ms}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est = oracle_frame_estimate(wl, 4, 7, int(n_rays))
+        cpu = {"value": 1.0 / est["frame_s"], "unit": "frames/s", "cores": int(est["threads"]),
+               "kind": "oracle",
+               "sample": (f"one ray per view then 4 rays per view ({est['rays_sampled']} rays; "
+                          f"every view's {wl.scene.n} Gaussians projected in FP64), frame time "
+                          f"extrapolated as N_v*T_project + N_rays*T_ray, N_rays={n_rays}; "
+                          f"{est['sample_s']:.1f} s of CPU time")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scene and camera path)",
+            "config": {"workload": workload_desc(wl), "global_batch": 1,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "no flush: each frame streams > 2 GB (inputs larger than L2)",
+                       "storage": wl.scene.dtype, "beta": beta, "n_rays": int(n_rays)},
+            "subpixels_per_s": fps * subpix,
+            "stages_ms": dl_stages,
+            "offline_tables_s": offline_s,
+            "standard": std,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    r.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

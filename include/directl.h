@@ -1,0 +1,210 @@
+/*
+ * directl.h -- C ABI of the GB300 DirectL light-field renderer.
+ *
+ * DirectL (arXiv 2407.14053) renders a radiance field straight into the
+ * encoded image of a lenticular light-field display: for every screen
+ * subpixel it evaluates the interweave map (Sec. 3.1, Eqs. (1)-(3)), picks
+ * the subpixel's ray after subpixel repurposing (Sec. 5, Alg. 2), and
+ * composites 3D Gaussians front to back only for the rays and channels the
+ * panel shows (Sec. 3.3, Eqs. (5), (8)-(10)).  Beside it the library builds
+ * the paper's standard paradigm: render every view with a tile rasteriser,
+ * then interweave (Alg. 1).
+ *
+ * Conventions for every call:
+ *  - Return value: DL_OK (0) or a negative dl_status.  No call aborts the
+ *    process or lets a C++ exception escape.  dl_last_error_detail() gives a
+ *    one-line description of the last failure on a context.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Calls enqueue their device work on that stream.
+ *    Calls that return sizes computed on the device (dl_set_display,
+ *    dl_render_frame) synchronise `stream` once; see each call.
+ *  - Ownership: the library owns scenes, display tables and its scratch
+ *    memory (resident on the device until freed or the context is
+ *    destroyed).  The caller owns every buffer it passes in; input buffers
+ *    are only read during the call (they are copied), output buffers are
+ *    written on `stream`.
+ *  - Memory kinds: a pointer argument is device memory when the matching
+ *    `*_on_device` flag is 1 and host memory when it is 0.
+ *  - A context is bound to one device and is not thread-safe: callers that
+ *    share a context between threads must serialise their calls.
+ */
+#ifndef DIRECTL_H
+#define DIRECTL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dl_status;
+enum {
+    DL_OK = 0,
+    DL_ERR_INVALID_ARG = -1,  /* a parameter is out of range or NULL        */
+    DL_ERR_OOM = -2,          /* device or host allocation failed           */
+    DL_ERR_CUDA = -3,         /* a CUDA runtime call failed                 */
+    DL_ERR_NOT_FOUND = -4,    /* unknown scene or display id                */
+    DL_ERR_TIMEOUT = -5,      /* a bounded device wait gave up              */
+    DL_ERR_DEVICE_CHECK = -6, /* a kernel's own bounds check tripped        */
+    DL_ERR_CAPACITY = -7      /* a frame needs more than 2^31-1 tile keys   */
+};
+
+/* Storage types of Gaussian attributes other than the means. */
+enum { DL_F32 = 0, DL_BF16 = 1, DL_F16 = 2 };
+
+/* Rendering paths. */
+enum {
+    DL_DIRECTL = 0,       /* repurposed rays only (Sec. 5 and Sec. 4)     */
+    DL_STANDARD = 1,      /* all N_v views at panel resolution + Alg. 1   */
+    DL_REQUIRED_ONLY = 2  /* identity ray assignment: blend only the pixels
+                             the panel shows (Table 3, "Required Only")   */
+};
+
+typedef struct dl_ctx dl_ctx;
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+dl_status dl_create(dl_ctx** out, int32_t device);
+/* Free every scene, display and scratch buffer of the context. */
+dl_status dl_destroy(dl_ctx* ctx);
+/* Static string naming a status code. */
+const char* dl_status_string(dl_status s);
+/* Copy the last error description (NUL-terminated, truncated to len). */
+dl_status dl_last_error_detail(dl_ctx* ctx, char* buf, size_t len);
+
+/*
+ * 3D Gaussian scene, structure of arrays (Sec. 3.3: mean mu, covariance
+ * Sigma = R S S^T R^T from a quaternion and per-axis log-scales, opacity,
+ * spherical-harmonic colour).  Layouts: mean n*3 (always float32),
+ * log_scale n*3, rot_wxyz n*4 (any length; normalised on use),
+ * opacity_logit n (opacity = sigmoid(logit)), sh n*(d+1)^2*3 with the
+ * coefficient index outer and RGB inner.  All but the means are stored in
+ * `dtype` (DL_F32, DL_BF16 or DL_F16) as given.  1 <= n <= 2^28,
+ * 0 <= sh_degree <= 3.
+ */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t dtype;
+    const float* mean;
+    const void* log_scale;
+    const void* rot_wxyz;
+    const void* opacity_logit;
+    const void* sh;
+    int32_t on_device; /* 1: the five pointers are device memory */
+} dl_gaussians_desc;
+
+/* Copy a scene into library-owned device memory; *scene_id names it.
+ * Enqueued on `stream`; the input may be reused once the call returns when
+ * it is host memory, and once `stream` reaches this point when it is device
+ * memory. */
+dl_status dl_load_gaussians(dl_ctx* ctx, const dl_gaussians_desc* desc, void* stream,
+                            int32_t* scene_id);
+dl_status dl_free_scene(dl_ctx* ctx, int32_t scene_id);
+
+/*
+ * Lenticular display (Sec. 3.1 and Table 1).  width x height pixels of
+ * three subpixels each; num_views = N_v; pitch_lx = line count L_x in
+ * subpixel widths (0 < L_x <= 1024); tan_slant = tan(alpha) of the lens
+ * tilt (|tan| <= 8); offset_k = K_offset in subpixel widths.  The map uses
+ * these three rounded once to Q32 fixed point (round(3 tan 2^32),
+ * round(L_x 2^32), round(K 2^32), nearest-even, in double precision); that
+ * rounding is part of the display's definition and makes the map exact.
+ * p_w = grating units per repurposing area (Sec. 5).  view_span_deg =
+ * theta_d, the angle between the outermost cameras of the arc;
+ * fov_x_deg = horizontal field of view of every camera.  repurpose = 1
+ * applies Alg. 2, 0 gives every subpixel its own pixel.  reverse_views = 1
+ * makes view 0 the rightmost camera.  1 <= width, height <= 16384,
+ * 1 <= num_views <= 65535.
+ */
+typedef struct {
+    int32_t width, height, num_views, p_w;
+    double pitch_lx, tan_slant, offset_k;
+    double view_span_deg, fov_x_deg;
+    int32_t repurpose, reverse_views;
+} dl_display_params;
+
+/*
+ * Build a display's offline tables on the device (the paper's offline step,
+ * Sec. 4 step (1)): the view-index map V (Eqs. (1)-(3)), the repurposed
+ * source pixel of every subpixel (Alg. 2) and the ray table (unique rays in
+ * R-first order, Sec. 5).  Synchronises `stream` once to learn the ray
+ * count.  *display_id names the result.
+ */
+dl_status dl_set_display(dl_ctx* ctx, const dl_display_params* params, void* stream,
+                         int32_t* display_id);
+dl_status dl_free_display(dl_ctx* ctx, int32_t display_id);
+/* Number of rays N_rays and beta = N_rays / (w h) (either may be NULL). */
+dl_status dl_display_info(dl_ctx* ctx, int32_t display_id, int64_t* n_rays, double* beta);
+
+/* V, uint16, h rows of 3w entries: V[x*3w + 3y + k] = view of subpixel
+ * (row x, column y, channel k) (Alg. 1, "Align with LCD panel"). */
+dl_status dl_get_view_map(dl_ctx* ctx, int32_t display_id, uint16_t* out, int32_t out_on_device,
+                          void* stream);
+/* Encoded-image index matrix M_i (Sec. 5) as packed source pixels:
+ * out[(x*w + y)*3 + k] = (x' << 16) | y' of the pixel of view V(x,3y+k)
+ * whose channel k the subpixel shows. */
+dl_status dl_get_subpixel_map(dl_ctx* ctx, int32_t display_id, uint32_t* out,
+                              int32_t out_on_device, void* stream);
+/* Ray table: ray_of[(x*w + y)*3 + k] = ray id of the subpixel (3wh
+ * entries); rays[3*r .. 3*r+2] = (view, row, col) of ray r (N_rays*3
+ * entries).  Rays 0..wh-1 belong to the R subpixels in row-major order; the
+ * rest follow in order of first use by G, then B subpixels.  Either output
+ * may be NULL. */
+dl_status dl_get_ray_table(dl_ctx* ctx, int32_t display_id, uint32_t* ray_of, int32_t* rays,
+                           int32_t out_on_device, void* stream);
+
+/*
+ * Render one encoded light-field frame (h x w x 3 float32, row-major,
+ * RGB inner) of scene `scene_id` on display `display_id`.
+ * L0_c2w: camera-to-world pose of the light-field centre, 4x4 row-major,
+ * camera axes x right, y down, z forward (host memory, read during the
+ * call).  View v's camera is T_v = R_y(-theta_v) L0 with theta_v =
+ * -theta_d/2 + v theta_d/(N_v-1) (Eq. (17)).
+ * mode: DL_DIRECTL, DL_STANDARD or DL_REQUIRED_ONLY.
+ * out: h*w*3 floats, device memory if out_on_device else host memory (the
+ * call then copies the frame back and returns once it is there).
+ * Synchronises `stream` once per frame to size the tile-key buffers.
+ */
+dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
+                          const double L0_c2w[16], int32_t mode, float* out,
+                          int32_t out_on_device, void* stream);
+
+/* Device bytes the last frame of (scene, display, mode) used for scratch,
+ * or an estimate before any frame was rendered. */
+dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, int32_t mode,
+                             size_t* bytes);
+
+/* Compositing tile shape of a mode (powers of two, 8..256 pixels each
+ * side).  Defaults: DL_STANDARD and DL_REQUIRED_ONLY 16x16, DL_DIRECTL 64x64. */
+dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h);
+
+/* Statistics of frames rendered on the context. */
+typedef struct {
+    int64_t n_keys;          /* (view, tile, Gaussian) overlaps sorted        */
+    int64_t n_rays;          /* rays composited (w*h*N_v for DL_STANDARD)    */
+    int64_t pairs_evaluated; /* (ray, Gaussian) alpha evaluations, when
+                                stage timing is on                           */
+    int64_t pairs_blended;   /* of those, the ones composited (Eq. (5))      */
+    int32_t tile_w, tile_h;
+    int32_t sort_bits;       /* key bits the radix sort ordered              */
+    int32_t n_launches;      /* kernels the frame launched                   */
+    float ms_project, ms_scan, ms_sync, ms_emit, ms_sort, ms_ranges, ms_composite,
+        ms_interweave, ms_total; /* stage durations (CUDA events)        */
+} dl_frame_stats;
+
+/* While enabled, every dl_render_frame records CUDA events around its
+ * stages on its stream and counts compositing pairs, without synchronising.
+ * Disabled by default. */
+dl_status dl_enable_stage_timing(dl_ctx* ctx, int32_t enable);
+/* Counters of the last frame (stage times are 0: see dl_stage_totals). */
+dl_status dl_last_frame_stats(dl_ctx* ctx, dl_frame_stats* out);
+/* Sums of every field over the frames rendered with stage timing on since
+ * the previous call (waits for those frames to finish), and their number.
+ * tile_w/tile_h/sort_bits are those of the last frame. */
+dl_status dl_stage_totals(dl_ctx* ctx, dl_frame_stats* sum, int32_t* n_frames);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

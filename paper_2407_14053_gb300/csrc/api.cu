@@ -1,0 +1,855 @@
+// Host side of the C ABI declared in include/directl.h: contexts, scenes,
+// displays and the per-frame orchestration of the DirectL and standard paths.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/directl.h"
+#include "dl_internal.cuh"
+
+namespace dl {
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        release();
+        const size_t want = n + n / 8 + 256;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return e;
+        }
+        bytes = want;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+struct Scene {
+    int64_t n = 0;
+    int32_t sh_degree = 0, dtype = DL_F32;
+    DevBuf mean, log_scale, rot, opacity, sh;
+};
+
+struct TileGroups {
+    int32_t tw = 0, th = 0, ntx = 0, nty = 0, ntiles = 0;
+    int64_t n_work = 0;
+    DevBuf grouped, work;
+};
+
+struct RaySet {
+    bool built = false;
+    int64_t n_rays = 0;
+    DevBuf src, ray_of, ray_view, ray_pix, ray_slot;
+    std::map<int64_t, std::unique_ptr<TileGroups>> groups;
+};
+
+struct Display {
+    dl_display_params prm{};
+    DisplayQ q{};
+    DevBuf V;
+    RaySet rep;    // Alg. 2 assignment (or identity when repurpose == 0)
+    RaySet ident;  // identity assignment, built on first DL_REQUIRED_ONLY frame
+};
+
+// Events around the stages of one frame (see dl_render_frame).
+constexpr int kStageEvents = 9;
+struct StageEvents {
+    cudaEvent_t e[kStageEvents] = {};
+};
+struct PendingFrame {
+    StageEvents* ev;
+    int64_t n_keys, n_rays;
+    int32_t launches;
+};
+
+struct Workspace {
+    DevBuf cams, rec, count, offset, scan_tmp, keys[2], vals[2], ranges, radix_tmp, Mm, out, small,
+        pairs;
+    unsigned long long* h_total = nullptr;  // pinned
+    size_t last_bytes = 0;
+    std::vector<StageEvents*> ev_free;
+    std::vector<PendingFrame> pending;
+    ~Workspace() {
+        if (h_total) cudaFreeHost(h_total);
+        for (auto& f : pending) ev_free.push_back(f.ev);
+        for (StageEvents* s : ev_free) {
+            for (auto& e : s->e)
+                if (e) cudaEventDestroy(e);
+            delete s;
+        }
+    }
+    size_t footprint() const {
+        size_t b = cams.bytes + rec.bytes + count.bytes + offset.bytes + scan_tmp.bytes + ranges.bytes +
+                   radix_tmp.bytes + Mm.bytes + out.bytes + small.bytes;
+        for (int i = 0; i < 2; ++i) b += keys[i].bytes + vals[i].bytes;
+        return b;
+    }
+};
+
+}  // namespace dl
+
+struct dl_ctx {
+    int32_t device = 0;
+    std::string err;
+    int32_t next_id = 1;
+    std::map<int32_t, std::unique_ptr<dl::Scene>> scenes;
+    std::map<int32_t, std::unique_ptr<dl::Display>> displays;
+    dl::Workspace ws;
+    int32_t tile[3][2] = {{64, 64}, {16, 16}, {16, 16}};
+    bool timing = false;
+    dl_frame_stats stats{};
+};
+
+using namespace dl;
+
+namespace {
+
+dl_status fail(dl_ctx* c, dl_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+dl_status cuda_fail(dl_ctx* c, cudaError_t e, const char* what) {
+    const dl_status s = (e == cudaErrorMemoryAllocation) ? DL_ERR_OOM : DL_ERR_CUDA;
+    return fail(c, s, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define DL_CK(expr, what)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+int bits_for(int64_t n) {  // bits to hold values 0..n-1
+    int b = 0;
+    while ((int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+int64_t floor_div_h(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1;
+    return q;
+}
+
+bool pow2_in(int32_t v, int32_t lo, int32_t hi) {
+    return v >= lo && v <= hi && (v & (v - 1)) == 0;
+}
+
+// Q32 display constants (the display's exact definition) and the search
+// range of Eq. (14): dx = floor(5 N_v / (2 L)), dy = ceil(N_v / (3 L)).
+dl_status make_display_q(dl_ctx* ctx, const dl_display_params& p, DisplayQ* q) {
+    if (p.width < 1 || p.height < 1 || p.width > 16384 || p.height > 16384)
+        return fail(ctx, DL_ERR_INVALID_ARG, "panel size %dx%d out of range", p.width, p.height);
+    if (p.num_views < 1 || p.num_views > 65535)
+        return fail(ctx, DL_ERR_INVALID_ARG, "num_views %d out of range", p.num_views);
+    if (p.p_w < 1) return fail(ctx, DL_ERR_INVALID_ARG, "p_w must be >= 1");
+    if (!(p.pitch_lx > 0.0 && p.pitch_lx <= 1024.0))
+        return fail(ctx, DL_ERR_INVALID_ARG, "pitch_lx out of (0, 1024]");
+    if (!(std::fabs(p.tan_slant) <= 8.0) || !(std::fabs(p.offset_k) <= 1048576.0))
+        return fail(ctx, DL_ERR_INVALID_ARG, "tan_slant or offset_k out of range");
+    if (!(p.fov_x_deg > 0.0 && p.fov_x_deg < 179.0) || !(p.view_span_deg >= 0.0 && p.view_span_deg < 360.0))
+        return fail(ctx, DL_ERR_INVALID_ARG, "fov_x_deg or view_span_deg out of range");
+    const double q32 = 4294967296.0;
+    q->w = p.width;
+    q->h = p.height;
+    q->nv = p.num_views;
+    q->pw = p.p_w;
+    q->t3q = int64_t(std::nearbyint(3.0 * p.tan_slant * q32));
+    q->lq = int64_t(std::nearbyint(p.pitch_lx * q32));
+    q->kq = int64_t(std::nearbyint(p.offset_k * q32));
+    if (q->lq <= 0) return fail(ctx, DL_ERR_INVALID_ARG, "pitch_lx rounds to zero");
+    q->win_dx = int32_t((5 * int64_t(p.num_views) * (int64_t(1) << 31)) / q->lq);
+    q->win_dy = int32_t((int64_t(p.num_views) * (int64_t(1) << 32) + 3 * q->lq - 1) / (3 * q->lq));
+    q->slant_neg = q->t3q < 0;
+    // d_offset is monotone in the column and in the row, so its extremes sit
+    // at the panel's corners.
+    const int64_t S = 3 * int64_t(p.width);
+    auto d = [&](int64_t x, int64_t s) { return s * (int64_t(1) << 32) + x * q->t3q - q->kq; };
+    const int64_t dmin = std::min(d(0, 0), d(p.height - 1, 0));
+    const int64_t dmax = std::max(d(0, S - 1), d(p.height - 1, S - 1));
+    const int64_t amin = floor_div_h(floor_div_h(dmin, q->lq), p.p_w);
+    const int64_t amax = floor_div_h(floor_div_h(dmax, q->lq), p.p_w);
+    q->area_min = amin;
+    q->n_areas = int32_t(amax - amin + 1);
+    return DL_OK;
+}
+
+dl_status build_rayset(dl_ctx* ctx, Display& D, RaySet& R, bool identity, cudaStream_t s) {
+    const DisplayQ& q = D.q;
+    const size_t n = 3 * size_t(q.w) * q.h;
+    DL_CK(R.src.reserve(4 * n), "alloc src");
+    DL_CK(launch_repurpose(q, D.V.as<uint16_t>(), R.src.as<uint32_t>(), identity ? 1 : 0, s),
+          "repurpose");
+    DL_CK(R.ray_of.reserve(4 * n), "alloc ray_of");
+    DevBuf tmp;
+    DL_CK(tmp.reserve(ray_table_tmp_bytes(q)), "alloc ray-table scratch");
+    DL_CK(ctx->ws.small.reserve(256), "alloc small");
+    uint32_t* d_new = ctx->ws.small.as<uint32_t>();
+    DL_CK(launch_ray_table(q, D.V.as<uint16_t>(), R.src.as<uint32_t>(), R.ray_of.as<uint32_t>(),
+                           tmp.p, d_new, s),
+          "ray table");
+    uint32_t h_new = 0;
+    DL_CK(cudaMemcpyAsync(&h_new, d_new, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "copy");
+    DL_CK(cudaStreamSynchronize(s), "sync");
+    R.n_rays = int64_t(q.w) * q.h + h_new;
+    DL_CK(R.ray_view.reserve(4 * size_t(R.n_rays)), "alloc rays");
+    DL_CK(R.ray_pix.reserve(4 * size_t(R.n_rays)), "alloc rays");
+    DL_CK(R.ray_slot.reserve(12 * size_t(R.n_rays)), "alloc rays");
+    DL_CK(launch_ray_attributes(q, D.V.as<uint16_t>(), R.ray_of.as<uint32_t>(), tmp.p,
+                                R.ray_view.as<uint32_t>(), R.ray_pix.as<uint32_t>(),
+                                R.ray_slot.as<int32_t>(), R.n_rays, s),
+          "ray attributes");
+    DL_CK(cudaStreamSynchronize(s), "sync");
+    R.groups.clear();
+    R.built = true;
+    return DL_OK;
+}
+
+constexpr int kRaysPerBlock = 128;
+
+// Rays of a ray set grouped by (view, tile) for one tile shape, and the work
+// list of the DirectL compositing kernel (chunks of <= 128 rays).
+dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th, cudaStream_t s,
+                     TileGroups** out) {
+    const int64_t key = int64_t(tw) * 100000 + th;
+    auto it = R.groups.find(key);
+    if (it != R.groups.end()) {
+        *out = it->second.get();
+        return DL_OK;
+    }
+    auto G = std::make_unique<TileGroups>();
+    G->tw = tw;
+    G->th = th;
+    G->ntx = (D.q.w + tw - 1) / tw;
+    G->nty = (D.q.h + th - 1) / th;
+    G->ntiles = G->ntx * G->nty;
+    const int64_t ngroups = int64_t(D.q.nv) * G->ntiles;
+    const int64_t nr = R.n_rays;
+    DevBuf k0, k1, v0, v1, rtmp, ranges;
+    DL_CK(k0.reserve(8 * size_t(nr)), "alloc");
+    DL_CK(k1.reserve(8 * size_t(nr)), "alloc");
+    DL_CK(v0.reserve(4 * size_t(nr)), "alloc");
+    DL_CK(v1.reserve(4 * size_t(nr)), "alloc");
+    DL_CK(rtmp.reserve(radix_tmp_bytes(nr)), "alloc");
+    DL_CK(ranges.reserve(8 * size_t(ngroups)), "alloc");
+    DL_CK(launch_ray_group_keys(R.ray_view.as<uint32_t>(), R.ray_pix.as<uint32_t>(), nr, tw, th,
+                                G->ntx, G->ntiles, k0.as<unsigned long long>(), v0.as<uint32_t>(), s),
+          "group keys");
+    int alt = 0;
+    DL_CK(radix_sort_pairs(k0.as<unsigned long long>(), v0.as<uint32_t>(),
+                           k1.as<unsigned long long>(), v1.as<uint32_t>(), nr, bits_for(ngroups),
+                           rtmp.p, &alt, s),
+          "group sort");
+    unsigned long long* ks = alt ? k1.as<unsigned long long>() : k0.as<unsigned long long>();
+    uint32_t* vs = alt ? v1.as<uint32_t>() : v0.as<uint32_t>();
+    DL_CK(cudaMemsetAsync(ranges.p, 0, 8 * size_t(ngroups), s), "memset");
+    DL_CK(launch_key_ranges(ks, nr, 0, ranges.as<uint2>(), s), "group ranges");
+    DL_CK(G->grouped.reserve(16 * size_t(nr)), "alloc");
+    DL_CK(launch_ray_group_gather(vs, R.ray_pix.as<uint32_t>(), R.ray_slot.as<int32_t>(), nr,
+                                  G->grouped.as<int4>(), s),
+          "group gather");
+    std::vector<uint2> h_ranges(static_cast<size_t>(ngroups));
+    DL_CK(cudaMemcpyAsync(h_ranges.data(), ranges.p, 8 * size_t(ngroups), cudaMemcpyDeviceToHost, s),
+          "copy");
+    DL_CK(cudaStreamSynchronize(s), "sync");
+    std::vector<int4> work;
+    work.reserve(size_t(nr / kRaysPerBlock + ngroups / 4 + 16));
+    for (int64_t g = 0; g < ngroups; ++g) {
+        const uint2 r = h_ranges[size_t(g)];
+        for (uint32_t b = r.x; b < r.y; b += kRaysPerBlock)
+            work.push_back(make_int4(int(g), int(b), int(std::min<uint32_t>(b + kRaysPerBlock, r.y)), 0));
+    }
+    G->n_work = int64_t(work.size());
+    DL_CK(G->work.reserve(16 * std::max<size_t>(work.size(), 1)), "alloc");
+    if (!work.empty())
+        DL_CK(cudaMemcpyAsync(G->work.p, work.data(), 16 * work.size(), cudaMemcpyHostToDevice, s),
+              "copy");
+    DL_CK(cudaStreamSynchronize(s), "sync");
+    *out = G.get();
+    R.groups[key] = std::move(G);
+    return DL_OK;
+}
+
+// View cameras: T_v = R_y(-theta_v) L0 (Eq. (17)); theta_v = -theta_d/2 +
+// v theta_d/(N_v-1), view 0 the leftmost unless reverse_views.  Computed in
+// double on the host, handed to the kernels as float world->camera matrices.
+void make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>& cams) {
+    cams.resize(size_t(p.num_views));
+    const double pi = 3.14159265358979323846;
+    for (int32_t v = 0; v < p.num_views; ++v) {
+        const int32_t vv = p.reverse_views ? p.num_views - 1 - v : v;
+        double th = 0.0;
+        if (p.num_views > 1)
+            th = (-0.5 * p.view_span_deg + vv * p.view_span_deg / (p.num_views - 1)) * pi / 180.0;
+        const double ph = -th, cs = std::cos(ph), sn = std::sin(ph);
+        const double Ry[3][3] = {{cs, 0, sn}, {0, 1, 0}, {-sn, 0, cs}};
+        double T[3][4];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 4; ++j) {
+                double a = 0.0;
+                for (int k = 0; k < 3; ++k) a += Ry[i][k] * L0[4 * k + j];
+                T[i][j] = a;  // last row of L0 is (0,0,0,1): no contribution
+            }
+        Cam& c = cams[size_t(v)];
+        // world->camera: R_wc = R_cw^T, t = -R_cw^T centre
+        for (int i = 0; i < 3; ++i) {
+            c.c[i] = float(T[i][3]);
+            double t = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                c.r[3 * i + k] = float(T[k][i]);
+                t -= T[k][i] * T[k][3];
+            }
+            c.t[i] = float(t);
+        }
+    }
+}
+
+dl_status upload_cams(dl_ctx* ctx, const std::vector<Cam>& cams, cudaStream_t s) {
+    DL_CK(ctx->ws.cams.reserve(sizeof(Cam) * cams.size()), "alloc cams");
+    Cam* dst = ctx->ws.cams.as<Cam>();
+    for (size_t v0 = 0; v0 < cams.size(); v0 += kCamBatch) {
+        CamBatch b;
+        const int32_t n = int32_t(std::min<size_t>(kCamBatch, cams.size() - v0));
+        std::memcpy(b.cam, cams.data() + v0, sizeof(Cam) * size_t(n));
+        DL_CK(launch_store_cams(b, n, dst + v0, s), "store cams");
+    }
+    return DL_OK;
+}
+
+dl_status check_ctx(dl_ctx* ctx) {
+    if (!ctx) return DL_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return DL_OK;
+}
+
+size_t dtype_size(int32_t dt) { return dt == DL_F32 ? 4 : 2; }
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dl_status_string(dl_status s) {
+    switch (s) {
+        case DL_OK: return "DL_OK";
+        case DL_ERR_INVALID_ARG: return "DL_ERR_INVALID_ARG";
+        case DL_ERR_OOM: return "DL_ERR_OOM";
+        case DL_ERR_CUDA: return "DL_ERR_CUDA";
+        case DL_ERR_NOT_FOUND: return "DL_ERR_NOT_FOUND";
+        case DL_ERR_TIMEOUT: return "DL_ERR_TIMEOUT";
+        case DL_ERR_DEVICE_CHECK: return "DL_ERR_DEVICE_CHECK";
+        case DL_ERR_CAPACITY: return "DL_ERR_CAPACITY";
+        default: return "DL_ERR_UNKNOWN";
+    }
+}
+
+dl_status dl_create(dl_ctx** out, int32_t device) {
+    if (!out) return DL_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return DL_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess || cudaFree(nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        return DL_ERR_CUDA;
+    }
+    dl_ctx* c = new (std::nothrow) dl_ctx();
+    if (!c) return DL_ERR_OOM;
+    c->device = device;
+    if (cudaMallocHost(&c->ws.h_total, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return DL_ERR_OOM;
+    }
+    *out = c;
+    return DL_OK;
+}
+
+dl_status dl_destroy(dl_ctx* ctx) {
+    if (!ctx) return DL_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    delete ctx;
+    return DL_OK;
+}
+
+dl_status dl_last_error_detail(dl_ctx* ctx, char* buf, size_t len) {
+    if (!ctx || !buf || len == 0) return DL_ERR_INVALID_ARG;
+    std::snprintf(buf, len, "%s", ctx->err.c_str());
+    return DL_OK;
+}
+
+dl_status dl_load_gaussians(dl_ctx* ctx, const dl_gaussians_desc* d, void* stream,
+                            int32_t* scene_id) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!d || !scene_id || !d->mean || !d->log_scale || !d->rot_wxyz || !d->opacity_logit || !d->sh)
+        return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
+    if (d->n < 1 || d->n > (int64_t(1) << 28))
+        return fail(ctx, DL_ERR_INVALID_ARG, "n = %lld out of [1, 2^28]", (long long)d->n);
+    if (d->sh_degree < 0 || d->sh_degree > 3)
+        return fail(ctx, DL_ERR_INVALID_ARG, "sh_degree %d out of [0, 3]", d->sh_degree);
+    if (d->dtype != DL_F32 && d->dtype != DL_BF16 && d->dtype != DL_F16)
+        return fail(ctx, DL_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto sc = std::make_unique<Scene>();
+    sc->n = d->n;
+    sc->sh_degree = d->sh_degree;
+    sc->dtype = d->dtype;
+    const size_t n = size_t(d->n), es = dtype_size(d->dtype);
+    const size_t nc = size_t((d->sh_degree + 1) * (d->sh_degree + 1));
+    const cudaMemcpyKind kind = d->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    struct {
+        DevBuf* b;
+        const void* src;
+        size_t bytes;
+    } parts[5] = {{&sc->mean, d->mean, 12 * n},
+                  {&sc->log_scale, d->log_scale, 3 * es * n},
+                  {&sc->rot, d->rot_wxyz, 4 * es * n},
+                  {&sc->opacity, d->opacity_logit, es * n},
+                  {&sc->sh, d->sh, 3 * nc * es * n}};
+    for (auto& pt : parts) {
+        DL_CK(pt.b->reserve(pt.bytes), "alloc scene");
+        DL_CK(cudaMemcpyAsync(pt.b->p, pt.src, pt.bytes, kind, s), "copy scene");
+    }
+    if (!d->on_device) DL_CK(cudaStreamSynchronize(s), "sync");
+    const int32_t id = ctx->next_id++;
+    ctx->scenes[id] = std::move(sc);
+    *scene_id = id;
+    return DL_OK;
+}
+
+dl_status dl_free_scene(dl_ctx* ctx, int32_t scene_id) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    auto it = ctx->scenes.find(scene_id);
+    if (it == ctx->scenes.end()) return fail(ctx, DL_ERR_NOT_FOUND, "scene %d", scene_id);
+    cudaDeviceSynchronize();
+    ctx->scenes.erase(it);
+    return DL_OK;
+}
+
+dl_status dl_set_display(dl_ctx* ctx, const dl_display_params* params, void* stream,
+                         int32_t* display_id) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!params || !display_id) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto D = std::make_unique<Display>();
+    D->prm = *params;
+    st = make_display_q(ctx, D->prm, &D->q);
+    if (st) return st;
+    const size_t n = 3 * size_t(D->q.w) * D->q.h;
+    DL_CK(D->V.reserve(2 * n), "alloc V");
+    DL_CK(launch_view_map(D->q, D->V.as<uint16_t>(), s), "view map");
+    st = build_rayset(ctx, *D, D->rep, D->prm.repurpose == 0, s);
+    if (st) return st;
+    TileGroups* G = nullptr;
+    st = get_groups(ctx, *D, D->rep, ctx->tile[DL_DIRECTL][0], ctx->tile[DL_DIRECTL][1], s, &G);
+    if (st) return st;
+    const int32_t id = ctx->next_id++;
+    ctx->displays[id] = std::move(D);
+    *display_id = id;
+    return DL_OK;
+}
+
+dl_status dl_free_display(dl_ctx* ctx, int32_t display_id) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    auto it = ctx->displays.find(display_id);
+    if (it == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    cudaDeviceSynchronize();
+    ctx->displays.erase(it);
+    return DL_OK;
+}
+
+dl_status dl_display_info(dl_ctx* ctx, int32_t display_id, int64_t* n_rays, double* beta) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    auto it = ctx->displays.find(display_id);
+    if (it == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    const Display& D = *it->second;
+    if (n_rays) *n_rays = D.rep.n_rays;
+    if (beta) *beta = double(D.rep.n_rays) / (double(D.q.w) * D.q.h);
+    return DL_OK;
+}
+
+static dl_status copy_out(dl_ctx* ctx, void* dst, const void* src, size_t bytes, int32_t on_device,
+                          cudaStream_t s) {
+    DL_CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          s),
+          "copy out");
+    if (!on_device) DL_CK(cudaStreamSynchronize(s), "sync");
+    return DL_OK;
+}
+
+dl_status dl_get_view_map(dl_ctx* ctx, int32_t display_id, uint16_t* out, int32_t out_on_device,
+                          void* stream) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    auto it = ctx->displays.find(display_id);
+    if (it == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    if (!out) return fail(ctx, DL_ERR_INVALID_ARG, "null out");
+    const Display& D = *it->second;
+    return copy_out(ctx, out, D.V.p, 2 * 3 * size_t(D.q.w) * D.q.h, out_on_device,
+                    static_cast<cudaStream_t>(stream));
+}
+
+dl_status dl_get_subpixel_map(dl_ctx* ctx, int32_t display_id, uint32_t* out,
+                              int32_t out_on_device, void* stream) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    auto it = ctx->displays.find(display_id);
+    if (it == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    if (!out) return fail(ctx, DL_ERR_INVALID_ARG, "null out");
+    const Display& D = *it->second;
+    return copy_out(ctx, out, D.rep.src.p, 4 * 3 * size_t(D.q.w) * D.q.h, out_on_device,
+                    static_cast<cudaStream_t>(stream));
+}
+
+dl_status dl_get_ray_table(dl_ctx* ctx, int32_t display_id, uint32_t* ray_of, int32_t* rays,
+                           int32_t out_on_device, void* stream) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    auto it = ctx->displays.find(display_id);
+    if (it == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    const Display& D = *it->second;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ray_of) {
+        st = copy_out(ctx, ray_of, D.rep.ray_of.p, 4 * 3 * size_t(D.q.w) * D.q.h, out_on_device, s);
+        if (st) return st;
+    }
+    if (rays) {
+        const size_t bytes = 12 * size_t(D.rep.n_rays);
+        if (out_on_device) {
+            DL_CK(launch_rays_export(D.rep.ray_view.as<uint32_t>(), D.rep.ray_pix.as<uint32_t>(),
+                                     D.rep.n_rays, rays, s),
+                  "rays export");
+        } else {
+            DevBuf tmp;
+            DL_CK(tmp.reserve(bytes), "alloc");
+            DL_CK(launch_rays_export(D.rep.ray_view.as<uint32_t>(), D.rep.ray_pix.as<uint32_t>(),
+                                     D.rep.n_rays, tmp.as<int32_t>(), s),
+                  "rays export");
+            st = copy_out(ctx, rays, tmp.p, bytes, 0, s);
+            if (st) return st;
+        }
+    }
+    return DL_OK;
+}
+
+dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (mode < 0 || mode > 2) return fail(ctx, DL_ERR_INVALID_ARG, "mode %d", mode);
+    if (!pow2_in(tile_w, 8, 256) || !pow2_in(tile_h, 8, 256))
+        return fail(ctx, DL_ERR_INVALID_ARG, "tile %dx%d: powers of two in [8, 256]", tile_w, tile_h);
+    if (mode == DL_STANDARD && tile_w * tile_h > 1024)
+        return fail(ctx, DL_ERR_INVALID_ARG, "standard tiles hold at most 1024 pixels");
+    ctx->tile[mode][0] = tile_w;
+    ctx->tile[mode][1] = tile_h;
+    return DL_OK;
+}
+
+dl_status dl_enable_stage_timing(dl_ctx* ctx, int32_t enable) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (enable && !ctx->ws.pairs.p) {
+        DL_CK(ctx->ws.pairs.reserve(16), "alloc counters");
+        DL_CK(cudaMemset(ctx->ws.pairs.p, 0, 16), "memset");
+    }
+    ctx->timing = enable != 0;
+    return DL_OK;
+}
+
+dl_status dl_last_frame_stats(dl_ctx* ctx, dl_frame_stats* out) {
+    if (!ctx || !out) return DL_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return DL_OK;
+}
+
+dl_status dl_stage_totals(dl_ctx* ctx, dl_frame_stats* sum, int32_t* n_frames) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!sum || !n_frames) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
+    dl_frame_stats t{};
+    t.tile_w = ctx->stats.tile_w;
+    t.tile_h = ctx->stats.tile_h;
+    t.sort_bits = ctx->stats.sort_bits;
+    Workspace& W = ctx->ws;
+    for (PendingFrame& f : W.pending) {
+        DL_CK(cudaEventSynchronize(f.ev->e[kStageEvents - 1]), "event sync");
+        cudaEvent_t* e = f.ev->e;
+        t.ms_project += elapsed(e[0], e[1]);
+        t.ms_scan += elapsed(e[1], e[2]);
+        t.ms_sync += elapsed(e[2], e[3]);
+        t.ms_emit += elapsed(e[3], e[4]);
+        t.ms_sort += elapsed(e[4], e[5]);
+        t.ms_ranges += elapsed(e[5], e[6]);
+        t.ms_composite += elapsed(e[6], e[7]);
+        t.ms_interweave += elapsed(e[7], e[8]);
+        t.ms_total += elapsed(e[0], e[8]);
+        t.n_keys += f.n_keys;
+        t.n_rays += f.n_rays;
+        t.n_launches += f.launches;
+        W.ev_free.push_back(f.ev);
+    }
+    *n_frames = int32_t(W.pending.size());
+    W.pending.clear();
+    if (W.pairs.p) {
+        unsigned long long h[2] = {0, 0};
+        DL_CK(cudaMemcpy(h, W.pairs.p, 16, cudaMemcpyDeviceToHost), "copy counters");
+        DL_CK(cudaMemset(W.pairs.p, 0, 16), "memset");
+        t.pairs_evaluated = int64_t(h[0]);
+        t.pairs_blended = int64_t(h[1]);
+    }
+    *sum = t;
+    return DL_OK;
+}
+
+dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, int32_t mode,
+                             size_t* bytes) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!bytes) return fail(ctx, DL_ERR_INVALID_ARG, "null bytes");
+    auto si = ctx->scenes.find(scene_id);
+    auto di = ctx->displays.find(display_id);
+    if (si == ctx->scenes.end() || di == ctx->displays.end())
+        return fail(ctx, DL_ERR_NOT_FOUND, "scene %d / display %d", scene_id, display_id);
+    const Scene& S = *si->second;
+    const Display& D = *di->second;
+    const size_t ne = size_t(D.q.nv) * size_t(S.n);
+    size_t b = ne * (48 + 8) + scan_tmp_bytes(int64_t(ne));
+    // tile keys: about two tiles per (view, Gaussian) at the default shapes
+    const size_t keys = 2 * ne;
+    b += 2 * keys * 12 + radix_tmp_bytes(int64_t(keys));
+    if (mode == DL_STANDARD) b += size_t(D.q.nv) * D.q.w * D.q.h * 12;
+    *bytes = std::max(b, ctx->ws.last_bytes);
+    return DL_OK;
+}
+
+dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
+                          const double L0_c2w[16], int32_t mode, float* out, int32_t out_on_device,
+                          void* stream) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!L0_c2w || !out) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
+    if (mode < 0 || mode > 2) return fail(ctx, DL_ERR_INVALID_ARG, "mode %d", mode);
+    auto si = ctx->scenes.find(scene_id);
+    if (si == ctx->scenes.end()) return fail(ctx, DL_ERR_NOT_FOUND, "scene %d", scene_id);
+    auto di = ctx->displays.find(display_id);
+    if (di == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    Scene& S = *si->second;
+    Display& D = *di->second;
+    Workspace& W = ctx->ws;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool timing = ctx->timing;
+    StageEvents* E = nullptr;
+    if (timing) {
+        if (W.ev_free.empty()) {
+            auto* ne = new (std::nothrow) StageEvents();
+            if (!ne) return fail(ctx, DL_ERR_OOM, "events");
+            for (auto& e : ne->e) DL_CK(cudaEventCreate(&e), "event create");
+            W.ev_free.push_back(ne);
+        }
+        E = W.ev_free.back();
+        W.ev_free.pop_back();
+        W.pending.push_back(PendingFrame{E, 0, 0, 0});
+    }
+    auto mark = [&](int i) -> cudaError_t {
+        return timing ? cudaEventRecord(E->e[i], s) : cudaSuccess;
+    };
+    DL_CK(mark(0), "event");
+
+    const int32_t nv = D.q.nv, w = D.q.w, h = D.q.h;
+    const int32_t tw = ctx->tile[mode][0], th = ctx->tile[mode][1];
+    RaySet* R = nullptr;
+    TileGroups* G = nullptr;
+    if (mode != DL_STANDARD) {
+        R = &D.rep;
+        if (mode == DL_REQUIRED_ONLY) {
+            if (D.prm.repurpose == 0) {
+                R = &D.rep;
+            } else {
+                if (!D.ident.built) {
+                    st = build_rayset(ctx, D, D.ident, true, s);
+                    if (st) return st;
+                }
+                R = &D.ident;
+            }
+        }
+        st = get_groups(ctx, D, *R, tw, th, s, &G);
+        if (st) return st;
+    }
+
+    // ---- cameras (Eq. (17)) and projection (Eqs. (8)-(10)) ----
+    std::vector<Cam> cams;
+    make_cams(D.prm, L0_c2w, cams);
+    st = upload_cams(ctx, cams, s);
+    if (st) return st;
+    const double pi = 3.14159265358979323846;
+    const double focal = 0.5 * w / std::tan(0.5 * D.prm.fov_x_deg * pi / 180.0);
+    ProjectParams pp{};
+    pp.n = S.n;
+    pp.sh_degree = S.sh_degree;
+    pp.width = w;
+    pp.height = h;
+    pp.focal = float(focal);
+    pp.half_w = 0.5f * float(w);
+    pp.half_h = 0.5f * float(h);
+    pp.lim_x = float(1.3 * (0.5 * w / focal));
+    pp.lim_y = float(1.3 * (0.5 * h / focal));
+    pp.tile_w = tw;
+    pp.tile_h = th;
+    pp.ntx = (w + tw - 1) / tw;
+    pp.nty = (h + th - 1) / th;
+    const int64_t ntiles = int64_t(pp.ntx) * pp.nty;
+    const int64_t ne = int64_t(nv) * S.n;
+    if (ne >= (int64_t(1) << 31)) return fail(ctx, DL_ERR_CAPACITY, "views x Gaussians >= 2^31");
+    DL_CK(W.rec.reserve(48 * size_t(ne)), "alloc records");
+    DL_CK(W.count.reserve(4 * size_t(ne)), "alloc counts");
+    DL_CK(W.offset.reserve(4 * size_t(ne)), "alloc offsets");
+    DL_CK(W.scan_tmp.reserve(scan_tmp_bytes(ne)), "alloc scan");
+    DL_CK(W.small.reserve(256), "alloc");
+    unsigned long long* d_total64 = W.small.as<unsigned long long>();
+    uint32_t* d_total32 = reinterpret_cast<uint32_t*>(W.small.as<char>() + 64);
+    DL_CK(cudaMemsetAsync(d_total64, 0, 8, s), "memset");
+    const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
+    ProjectOut po{W.rec.as<float4>(), W.count.as<uint32_t>(), d_total64};
+    DL_CK(launch_project(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, s), "project");
+    DL_CK(launch_exclusive_scan(W.count.as<uint32_t>(), W.offset.as<uint32_t>(), ne, d_total32,
+                                W.scan_tmp.p, s),
+          "scan");
+    DL_CK(mark(2), "event");
+    DL_CK(cudaMemcpyAsync(W.h_total, d_total64, 8, cudaMemcpyDeviceToHost, s), "copy total");
+    DL_CK(cudaStreamSynchronize(s), "sync");
+    const unsigned long long nkeys = *W.h_total;
+    if (nkeys >= (1ull << 31) - 1)
+        return fail(ctx, DL_ERR_CAPACITY, "frame needs %llu tile keys (limit 2^31-1)", nkeys);
+
+    // ---- tile keys and depth sort ----
+    const int64_t nk = int64_t(nkeys);
+    for (int i = 0; i < 2; ++i) {
+        DL_CK(W.keys[i].reserve(8 * size_t(nk > 0 ? nk : 1)), "alloc keys");
+        DL_CK(W.vals[i].reserve(4 * size_t(nk > 0 ? nk : 1)), "alloc vals");
+    }
+    DL_CK(W.radix_tmp.reserve(radix_tmp_bytes(nk)), "alloc radix");
+    DL_CK(W.ranges.reserve(8 * size_t(nv) * size_t(ntiles)), "alloc ranges");
+    DL_CK(mark(3), "event");
+    DL_CK(launch_emit_keys(pp, nv, W.rec.as<float4>(), W.count.as<uint32_t>(),
+                           W.offset.as<uint32_t>(), W.keys[0].as<unsigned long long>(),
+                           W.vals[0].as<uint32_t>(), s),
+          "emit keys");
+    DL_CK(mark(4), "event");
+    const int sort_bits = 28 + bits_for(int64_t(nv) * ntiles);
+    int alt = 0;
+    DL_CK(radix_sort_pairs(W.keys[0].as<unsigned long long>(), W.vals[0].as<uint32_t>(),
+                           W.keys[1].as<unsigned long long>(), W.vals[1].as<uint32_t>(), nk,
+                           sort_bits, W.radix_tmp.p, &alt, s),
+          "sort");
+    unsigned long long* keys = W.keys[alt].as<unsigned long long>();
+    uint32_t* vals = W.vals[alt].as<uint32_t>();
+    DL_CK(mark(5), "event");
+    DL_CK(cudaMemsetAsync(W.ranges.p, 0, 8 * size_t(nv) * size_t(ntiles), s), "memset");
+    DL_CK(launch_key_ranges(keys, nk, 28, W.ranges.as<uint2>(), s), "ranges");
+    DL_CK(mark(6), "event");
+    unsigned long long* pairs = timing ? W.pairs.as<unsigned long long>() : nullptr;
+
+    // ---- compositing ----
+    CompositeParams cp{};
+    cp.n = S.n;
+    cp.width = w;
+    cp.height = h;
+    cp.half_w = pp.half_w;
+    cp.half_h = pp.half_h;
+    cp.tile_w = tw;
+    cp.tile_h = th;
+    cp.ntx = pp.ntx;
+    cp.ntiles = int32_t(ntiles);
+    const size_t out_bytes = 12 * size_t(w) * size_t(h);
+    float* dst = out;
+    if (!out_on_device) {
+        DL_CK(W.out.reserve(out_bytes), "alloc out");
+        dst = W.out.as<float>();
+    }
+    if (mode == DL_STANDARD) {
+        DL_CK(W.Mm.reserve(12 * size_t(nv) * size_t(w) * size_t(h)), "alloc M_m");
+        DL_CK(launch_composite_full(cp, nv, W.ranges.as<uint2>(), vals, W.rec.as<float4>(),
+                                    W.Mm.as<float>(), pairs, s),
+              "composite full");
+        DL_CK(mark(7), "event");
+        DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), W.Mm.as<float>(), dst, s),
+              "interweave");
+    } else {
+        DL_CK(launch_composite_rays(cp, G->work.as<int4>(), G->n_work, G->grouped.as<int4>(),
+                                    W.ranges.as<uint2>(), vals, W.rec.as<float4>(), dst, pairs, s),
+              "composite rays");
+        DL_CK(mark(7), "event");
+    }
+    DL_CK(mark(8), "event");
+    if (!out_on_device)
+        DL_CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, s), "copy frame");
+
+    dl_frame_stats& fs = ctx->stats;
+    fs = dl_frame_stats{};
+    fs.n_keys = nk;
+    fs.n_rays = mode == DL_STANDARD ? int64_t(nv) * w * h : R->n_rays;
+    fs.tile_w = tw;
+    fs.tile_h = th;
+    fs.sort_bits = sort_bits;
+    // store_cams, project, 3 scan, emit, 3 per radix pass, ranges, composite
+    // (+ interweave)
+    fs.n_launches = int32_t((nv + kCamBatch - 1) / kCamBatch) + 1 + 3 + 1 +
+                    3 * ((nk > 1) ? (sort_bits + 7) / 8 : 0) + (nk > 0 ? 1 : 0) +
+                    (mode == DL_STANDARD ? 2 : (G->n_work > 0 ? 1 : 0));
+    if (timing) {
+        PendingFrame& pf = W.pending.back();
+        pf.n_keys = fs.n_keys;
+        pf.n_rays = fs.n_rays;
+        pf.launches = fs.n_launches;
+    }
+    W.last_bytes = W.footprint();
+    if (!out_on_device) DL_CK(cudaStreamSynchronize(s), "sync");
+    return DL_OK;
+}
+
+}  // extern "C"

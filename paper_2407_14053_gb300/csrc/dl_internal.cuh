@@ -1,0 +1,146 @@
+// Internal declarations shared by the CUDA translation units of libdirectl.
+// Nothing here crosses the C ABI (include/directl.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace dl {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+// Display constants as the kernels see them.  t3q, lq, kq are the Q32
+// fixed-point 3 tan(alpha), L_x and K_offset; win_dx / win_dy the row and
+// column extents of the repurposing search range (Sec. 5, Eq. (14)).
+struct DisplayQ {
+    int32_t w, h, nv, pw;
+    int64_t t3q, lq, kq;
+    int32_t win_dx, win_dy;
+    int32_t slant_neg;
+    int32_t n_areas;
+    int64_t area_min;
+};
+
+// One view's camera: world->camera rotation (row-major), translation, centre.
+struct Cam {
+    float r[9];
+    float t[3];
+    float c[3];
+};
+
+// Cameras of a frame reach the device as a kernel parameter of a one-block
+// copy kernel (stream-ordered, nothing to keep alive on the host).
+constexpr int kCamBatch = 128;
+struct CamBatch {
+    Cam cam[kCamBatch];
+};
+
+// Projection constants of a frame.
+struct ProjectParams {
+    int64_t n;            // Gaussians
+    int32_t sh_degree;
+    int32_t width, height;
+    float focal;
+    float half_w, half_h;  // principal point (w/2, h/2)
+    float lim_x, lim_y;    // 1.3 tan(fov/2) clamps of the EWA Jacobian
+    int32_t tile_w, tile_h, ntx, nty;
+};
+
+// Per (view, Gaussian) record written by the projection, 3 x float4:
+//  q0 = (u - w/2, v - h/2, A, B)
+//  q1 = (C, log2(opacity), r, g)
+//  q2 = (b, depth, rect_x, rect_y)   rect_x = tx0 | tx1 << 16 (bit pattern)
+// with log2 alpha = A dx^2 + B dx dy + C dy^2 + log2(opacity) at pixel offset
+// (dx, dy) from the mean (A, B, C are -log2(e)/2 times the conic's xx, 2xy, yy).
+struct ProjectOut {
+    float4* rec;       // nv * n * 3
+    uint32_t* count;   // nv * n tiles touched (0 = culled)
+    unsigned long long* total;  // sum of count (atomic)
+};
+
+template <typename T>
+struct GaussiansView {
+    const float* mean;
+    const T* log_scale;
+    const T* rot;
+    const T* opacity_logit;
+    const T* sh;
+};
+
+// ---- a1..a3: display tables (display.cu) --------------------------------
+cudaError_t launch_view_map(const DisplayQ& q, uint16_t* V, cudaStream_t s);
+cudaError_t launch_repurpose(const DisplayQ& q, const uint16_t* V, uint32_t* src, int identity,
+                             cudaStream_t s);
+// Ray table: fills ray_of (3wh), ray_view/ray_pix (n_rays), ray_slot (3 n_rays).
+// Temporary buffers come from `tmp` (>= ray_table_tmp_bytes(q)).
+size_t ray_table_tmp_bytes(const DisplayQ& q);
+cudaError_t launch_ray_table(const DisplayQ& q, const uint16_t* V, const uint32_t* src,
+                             uint32_t* ray_of, void* tmp, uint32_t* d_n_new, cudaStream_t s);
+cudaError_t launch_ray_attributes(const DisplayQ& q, const uint16_t* V, const uint32_t* ray_of,
+                                  const void* tmp, uint32_t* ray_view, uint32_t* ray_pix,
+                                  int32_t* ray_slot, int64_t n_rays, cudaStream_t s);
+// Group keys of rays for a compositing tile shape: key = v*ntiles + tile,
+// value = ray id (a stable sort then keeps ray order inside a group).
+cudaError_t launch_ray_group_keys(const uint32_t* ray_view, const uint32_t* ray_pix, int64_t n_rays,
+                                  int32_t tile_w, int32_t tile_h, int32_t ntx, int32_t ntiles,
+                                  unsigned long long* keys, uint32_t* vals, cudaStream_t s);
+// (view, row, col) int32 triplets of every ray.
+cudaError_t launch_rays_export(const uint32_t* ray_view, const uint32_t* ray_pix, int64_t n_rays,
+                               int32_t* out, cudaStream_t s);
+// Gathers per grouped ray {pixel, slot0, slot1, slot2}.
+cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_pix,
+                                    const int32_t* ray_slot, int64_t n_rays, int4* grouped,
+                                    cudaStream_t s);
+
+// ---- a5/a6: projection, key emission (project.cu) ------------------------
+// dtype: 0 f32, 1 bf16, 2 f16
+// Copies up to kCamBatch cameras from a kernel parameter into device memory.
+cudaError_t launch_store_cams(const CamBatch& b, int32_t n, Cam* dst, cudaStream_t s);
+cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectParams& p,
+                           const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s);
+cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* rec,
+                             const uint32_t* count, const uint32_t* offset,
+                             unsigned long long* keys, uint32_t* vals, cudaStream_t s);
+
+// ---- scan / radix sort / ranges (sort.cu) ---------------------------------
+size_t scan_tmp_bytes(int64_t n);
+// out[i] = sum_{j<i} in[j]; *d_total (device) = sum of all.
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total,
+                                  void* tmp, cudaStream_t s);
+size_t radix_tmp_bytes(int64_t n);
+// Sorts (keys, vals) by the low `bits` key bits, stable.  Ping-pongs between
+// (keys, vals) and (keys_alt, vals_alt); returns in *result_in_alt whether
+// the sorted data ended in the alt buffers.
+cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
+                             uint32_t* vals_alt, int64_t n, int bits, void* tmp,
+                             int* result_in_alt, cudaStream_t s);
+// ranges[g] = [first, last) index of keys whose key >> shift == g.  ranges must
+// be zeroed first.
+cudaError_t launch_key_ranges(const unsigned long long* keys, int64_t n, int shift, uint2* ranges,
+                              cudaStream_t s);
+
+// ---- a7..a9: compositing (composite.cu) -----------------------------------
+struct CompositeParams {
+    int64_t n;        // Gaussians per view
+    int32_t width, height;
+    float half_w, half_h;
+    int32_t tile_w, tile_h, ntx, ntiles;
+};
+// DirectL: work items {group, begin, end, -} over grouped rays.
+// pairs (optional, 2 x u64): evaluated and composited (ray, Gaussian) pairs.
+cudaError_t launch_composite_rays(const CompositeParams& p, const int4* work, int64_t n_work,
+                                  const int4* grouped, const uint2* ranges, const uint32_t* vals,
+                                  const float4* rec, float* out, unsigned long long* pairs,
+                                  cudaStream_t s);
+// Standard paradigm: every pixel of every view into Mm (nv x h x w x 3).
+cudaError_t launch_composite_full(const CompositeParams& p, int32_t nv, const uint2* ranges,
+                                  const uint32_t* vals, const float4* rec, float* Mm,
+                                  unsigned long long* pairs, cudaStream_t s);
+// Alg. 1 sampling step at native resolution.
+cudaError_t launch_interweave(int32_t w, int32_t h, int32_t nv, const uint16_t* V, const float* Mm,
+                              float* out, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace dl

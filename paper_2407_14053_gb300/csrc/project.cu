@@ -1,0 +1,281 @@
+// Multi-view 3DGS projection (Sec. 3.3, Eqs. (8)-(10)) and tile-key emission.
+//
+// One thread per Gaussian reads its attributes once (FP32 means; scale,
+// rotation, opacity and SH in FP32/BF16/FP16), builds Sigma = R S S^T R^T once
+// and then projects it into every view: camera transform, EWA 2D covariance
+// Sigma' = J W Sigma W^T J^T + 0.3 I, conic, SH colour for the view's
+// direction, and the tile rectangle that holds every pixel where alpha can
+// reach 1/255.  All arithmetic is FP32.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "dl_internal.cuh"
+
+namespace dl {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ float to_f(T x);
+template <>
+__device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half x) { return __half2float(x); }
+
+// Real spherical-harmonic normalisations (closed forms in the comments).
+constexpr float kY00 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kY1 = 0.48860251190291992f;    // sqrt(3 / (4 pi))
+constexpr float kY2a = 1.0925484305920792f;    // sqrt(15 / pi) / 2
+constexpr float kY2b = 0.31539156525252005f;   // sqrt(5 / pi) / 4
+constexpr float kY2c = 0.54627421529603959f;   // sqrt(15 / pi) / 4
+constexpr float kY3a = 0.59004358992664352f;   // sqrt(35 / (2 pi)) / 4
+constexpr float kY3b = 2.8906114426405538f;    // sqrt(105 / pi) / 2
+constexpr float kY3c = 0.45704579946446572f;   // sqrt(21 / (2 pi)) / 4
+constexpr float kY3d = 0.37317633259011540f;   // sqrt(7 / pi) / 4
+constexpr float kY3e = 1.4453057213202769f;    // sqrt(105 / pi) / 4
+constexpr float kLog2e = 1.4426950408889634f;
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = kY00;
+    if (DEG >= 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+    }
+    if (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;
+        Y[5] = -kY2a * y * z;
+        Y[6] = kY2b * (2.f * zz - xx - yy);
+        Y[7] = -kY2a * x * z;
+        Y[8] = kY2c * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -kY3a * y * (3.f * xx - yy);
+            Y[10] = kY3b * x * y * z;
+            Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+            Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+            Y[14] = kY3e * z * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T, int DEG>
+__global__ void __launch_bounds__(256) project_kernel(GaussiansView<T> G, ProjectParams p,
+                                                      const Cam* __restrict__ cams, int32_t nv,
+                                                      ProjectOut out) {
+    constexpr int NC = (DEG + 1) * (DEG + 1);
+    const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    unsigned long long my_total = 0;
+    if (g < p.n) {
+        const float mx = G.mean[3 * g], my = G.mean[3 * g + 1], mz = G.mean[3 * g + 2];
+        // Sigma = R S S^T R^T (Eq. (8)), R from the normalised quaternion
+        float qw = to_f(G.rot[4 * g]), qx = to_f(G.rot[4 * g + 1]);
+        float qy = to_f(G.rot[4 * g + 2]), qz = to_f(G.rot[4 * g + 3]);
+        const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+        const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz),
+                    R02 = 2.f * (qx * qz + qw * qy);
+        const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz),
+                    R12 = 2.f * (qy * qz - qw * qx);
+        const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx),
+                    R22 = 1.f - 2.f * (qx * qx + qy * qy);
+        const float s0 = __expf(2.f * to_f(G.log_scale[3 * g]));
+        const float s1 = __expf(2.f * to_f(G.log_scale[3 * g + 1]));
+        const float s2 = __expf(2.f * to_f(G.log_scale[3 * g + 2]));
+        const float S00 = R00 * R00 * s0 + R01 * R01 * s1 + R02 * R02 * s2;
+        const float S01 = R00 * R10 * s0 + R01 * R11 * s1 + R02 * R12 * s2;
+        const float S02 = R00 * R20 * s0 + R01 * R21 * s1 + R02 * R22 * s2;
+        const float S11 = R10 * R10 * s0 + R11 * R11 * s1 + R12 * R12 * s2;
+        const float S12 = R10 * R20 * s0 + R11 * R21 * s1 + R12 * R22 * s2;
+        const float S22 = R20 * R20 * s0 + R21 * R21 * s1 + R22 * R22 * s2;
+        const float logit = to_f(G.opacity_logit[g]);
+        const float opac = 1.f / (1.f + __expf(-logit));
+        const float log2o = log2f(opac);
+        const bool visible_alpha = opac * 255.f > 1.f;
+        const float K = visible_alpha ? 2.f * logf(255.f * opac) : 0.f;
+        float sh[NC][3];
+#pragma unroll
+        for (int i = 0; i < NC; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[i][c] = to_f(G.sh[(g * NC + i) * 3 + c]);
+
+        for (int32_t v = 0; v < nv; ++v) {
+            const Cam& cam = cams[v];
+            const int64_t e = int64_t(v) * p.n + g;
+            const float tx = cam.r[0] * mx + cam.r[1] * my + cam.r[2] * mz + cam.t[0];
+            const float ty = cam.r[3] * mx + cam.r[4] * my + cam.r[5] * mz + cam.t[1];
+            const float tz = cam.r[6] * mx + cam.r[7] * my + cam.r[8] * mz + cam.t[2];
+            uint32_t cnt = 0;
+            if (tz > 0.2f && visible_alpha) {
+                // EWA (Eq. (9)): T = J W, Sigma' = T Sigma T^T + 0.3 I
+                const float iz = 1.f / tz;
+                const float xz = fminf(fmaxf(tx * iz, -p.lim_x), p.lim_x);
+                const float yz = fminf(fmaxf(ty * iz, -p.lim_y), p.lim_y);
+                const float fz = p.focal * iz;
+                const float j02 = -fz * xz, j12 = -fz * yz;
+                const float T00 = fz * cam.r[0] + j02 * cam.r[6];
+                const float T01 = fz * cam.r[1] + j02 * cam.r[7];
+                const float T02 = fz * cam.r[2] + j02 * cam.r[8];
+                const float T10 = fz * cam.r[3] + j12 * cam.r[6];
+                const float T11 = fz * cam.r[4] + j12 * cam.r[7];
+                const float T12 = fz * cam.r[5] + j12 * cam.r[8];
+                const float a0 = T00 * S00 + T01 * S01 + T02 * S02;
+                const float a1 = T00 * S01 + T01 * S11 + T02 * S12;
+                const float a2 = T00 * S02 + T01 * S12 + T02 * S22;
+                const float b0 = T10 * S00 + T11 * S01 + T12 * S02;
+                const float b1 = T10 * S01 + T11 * S11 + T12 * S12;
+                const float b2 = T10 * S02 + T11 * S12 + T12 * S22;
+                const float cxx = a0 * T00 + a1 * T01 + a2 * T02 + 0.3f;
+                const float cxy = a0 * T10 + a1 * T11 + a2 * T12;
+                const float cyy = b0 * T10 + b1 * T11 + b2 * T12 + 0.3f;
+                const float det = cxx * cyy - cxy * cxy;
+                if (det > 0.f) {
+                    const float uc = p.focal * tx * iz, vc = p.focal * ty * iz;
+                    // pixels where alpha >= 1/255 lie in the ellipse
+                    // d^T Sigma'^-1 d <= 2 ln(255 o); its bounding box:
+                    const float rx = sqrtf(K * cxx) * 1.0001f + 1e-3f;
+                    const float ry = sqrtf(K * cyy) * 1.0001f + 1e-3f;
+                    const float c_lo = ceilf(uc + p.half_w - rx), c_hi = floorf(uc + p.half_w + rx);
+                    const float r_lo = ceilf(vc + p.half_h - ry), r_hi = floorf(vc + p.half_h + ry);
+                    if (c_hi >= 0.f && r_hi >= 0.f && c_lo <= float(p.width - 1) &&
+                        r_lo <= float(p.height - 1) && c_lo <= c_hi && r_lo <= r_hi) {
+                        const int ic0 = int(fmaxf(c_lo, 0.f)), ic1 = int(fminf(c_hi, float(p.width - 1)));
+                        const int ir0 = int(fmaxf(r_lo, 0.f)), ir1 = int(fminf(r_hi, float(p.height - 1)));
+                        const int tx0 = ic0 / p.tile_w, tx1 = ic1 / p.tile_w;
+                        const int ty0 = ir0 / p.tile_h, ty1 = ir1 / p.tile_h;
+                        cnt = uint32_t(tx1 - tx0 + 1) * uint32_t(ty1 - ty0 + 1);
+                        const float id = 1.f / det;
+                        // colour: SH at dir = normalise(mu - camera centre)
+                        float dx = mx - cam.c[0], dy = my - cam.c[1], dz = mz - cam.c[2];
+                        const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+                        dx *= dn; dy *= dn; dz *= dn;
+                        float Y[16];
+                        sh_basis<DEG>(dx, dy, dz, Y);
+                        float col[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float acc = 0.f;
+#pragma unroll
+                            for (int i = 0; i < NC; ++i) acc = fmaf(Y[i], sh[i][c], acc);
+                            col[c] = fmaxf(acc + 0.5f, 0.f);
+                        }
+                        float4* rec = out.rec + 3 * e;
+                        rec[0] = make_float4(uc, vc, -0.5f * kLog2e * cyy * id, kLog2e * cxy * id);
+                        rec[1] = make_float4(-0.5f * kLog2e * cxx * id, log2o, col[0], col[1]);
+                        rec[2] = make_float4(col[2], tz, __uint_as_float(uint32_t(tx0) | (uint32_t(tx1) << 16)),
+                                             __uint_as_float(uint32_t(ty0) | (uint32_t(ty1) << 16)));
+                    }
+                }
+            }
+            out.count[e] = cnt;
+            my_total += cnt;
+        }
+    }
+    // block sum of the tile counts -> one 64-bit atomic per block
+    __shared__ unsigned long long s_part[8];
+    my_total = warp_sum(my_total);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = my_total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += s_part[w];
+        if (t) atomicAdd(out.total, t);
+    }
+}
+
+// Key of a (view, tile, Gaussian) overlap: (view*ntiles + tile) << 28 | depth
+// key, the depth key being the float bits of z minus those of 0.2 (z > 0.2,
+// so the difference is positive and ordered like z; 28 bits reach z = 2^29).
+__global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
+                                 const uint32_t* __restrict__ count,
+                                 const uint32_t* __restrict__ offset,
+                                 unsigned long long* __restrict__ keys,
+                                 uint32_t* __restrict__ vals) {
+    const int64_t total = int64_t(nv) * p.n;
+    const int ntiles = p.ntx * p.nty;
+    const uint32_t zbits0 = __float_as_uint(0.2f);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t cnt = count[e];
+        if (!cnt) continue;
+        const float4 q2 = rec[3 * e + 2];
+        const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
+        const int tx0 = rx & 0xFFFF, tx1 = rx >> 16, ty0 = ry & 0xFFFF, ty1 = ry >> 16;
+        uint32_t dk = __float_as_uint(q2.y) - zbits0;
+        if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
+        const int64_t v = e / p.n;
+        const uint32_t gidx = uint32_t(e - v * p.n);
+        uint32_t o = offset[e];
+        const unsigned long long vbase = (unsigned long long)(v * ntiles);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                const unsigned long long grp = vbase + unsigned(ty * p.ntx + tx);
+                keys[o] = (grp << 28) | dk;
+                vals[o] = gidx;
+                ++o;
+            }
+    }
+}
+
+__global__ void store_cams_kernel(CamBatch b, int32_t n, Cam* __restrict__ dst) {
+    const int i = threadIdx.x;
+    if (i < n) dst[i] = b.cam[i];
+}
+
+}  // namespace
+
+cudaError_t launch_store_cams(const CamBatch& b, int32_t n, Cam* dst, cudaStream_t s) {
+    store_cams_kernel<<<1, kCamBatch, 0, s>>>(b, n, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_project_t(const void* const* attrs, const ProjectParams& p,
+                                    const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s) {
+    GaussiansView<T> G;
+    G.mean = static_cast<const float*>(attrs[0]);
+    G.log_scale = static_cast<const T*>(attrs[1]);
+    G.rot = static_cast<const T*>(attrs[2]);
+    G.opacity_logit = static_cast<const T*>(attrs[3]);
+    G.sh = static_cast<const T*>(attrs[4]);
+    const int block = 256;
+    const int64_t grid = (p.n + block - 1) / block;
+    switch (p.sh_degree) {
+        case 0: project_kernel<T, 0><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
+        case 1: project_kernel<T, 1><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
+        case 2: project_kernel<T, 2><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
+        default: project_kernel<T, 3><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectParams& p,
+                           const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s) {
+    if (dtype == 1) return launch_project_t<__nv_bfloat16>(attrs, p, cams, nv, out, s);
+    if (dtype == 2) return launch_project_t<__half>(attrs, p, cams, nv, out, s);
+    return launch_project_t<float>(attrs, p, cams, nv, out, s);
+}
+
+cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* rec,
+                             const uint32_t* count, const uint32_t* offset,
+                             unsigned long long* keys, uint32_t* vals, cudaStream_t s) {
+    const int64_t total = int64_t(nv) * p.n;
+    int64_t grid = (total + 255) / 256;
+    const int64_t cap = int64_t(num_sms()) * 32;
+    if (grid > cap) grid = cap;
+    emit_keys_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, rec, count, offset, keys,
+                                                                   vals);
+    return cudaGetLastError();
+}
+
+}  // namespace dl

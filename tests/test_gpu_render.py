@@ -1,0 +1,213 @@
+"""GPU parity of rendered light-field frames against the FP64 oracle.
+
+A GPU value is accepted when it lies within the tolerance of the oracle's
+value or of one of the oracle's alternative results at FP32-resolution ties
+(depth near-ties, alpha within 1e-6 of 1/255, T within 1e-8 of 1e-4).
+Tolerances: 2e-3 per channel for FP32 attributes; for BF16 storage 2e-3
+against the oracle run on the BF16-rounded attributes and 8e-3 against the
+original FP32 attributes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-3
+TOL_BF16_VS_FP32 = 8e-3
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    from paper_2407_14053_gb300 import Renderer
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def _accept(got, ref, tol):
+    lo, hi = ref["lo"] - tol, ref["hi"] + tol
+    ok = (got >= lo) & (got <= hi)
+    plain = np.abs(got - ref["value"])
+    return ok, float(plain.max()) if plain.size else 0.0, int((~ok).sum())
+
+
+def _frame(renderer, sid, did, L0, mode):
+    out = renderer.render(sid, did, L0, mode)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _sources(renderer, did, d, mode):
+    V = oracle.view_map(d)
+    if mode == "standard" or (mode == "directl" and d.repurpose == 0):
+        return V, None
+    if mode == "required_only":
+        return V, None
+    return V, oracle.repurpose(d, V)
+
+
+@pytest.mark.parametrize("mode", ["directl", "standard", "required_only"])
+def test_tiny_full_frame(renderer, mode):
+    wl = W.WORKLOADS["tiny"]
+    scene = W.make_scene(wl.scene)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(wl.display)
+    L0 = W.light_field_centre(wl.camera_distance, 3.0)
+    img = _frame(renderer, sid, did, L0, mode).reshape(-1)
+    V, src = _sources(renderer, did, wl.display, mode)
+    sub = np.arange(img.size)
+    ref = oracle.render_subpixels(oracle.Scene(scene), wl.display, L0, sub, V, src)
+    ok, maxerr, nbad = _accept(img, ref, TOL)
+    assert nbad == 0, f"{nbad} subpixels outside tolerance; max |err| {maxerr:.3g}"
+    assert np.abs(img).max() > 0.1
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+def test_identity_repurposing_matches_standard(renderer):
+    wl = W.WORKLOADS["tiny"]
+    scene = W.make_scene(wl.scene)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(wl.display.replace(repurpose=0))
+    L0 = W.light_field_centre(wl.camera_distance, -2.0)
+    a = _frame(renderer, sid, did, L0, "directl")
+    b = _frame(renderer, sid, did, L0, "standard")
+    assert np.abs(a - b).max() <= 1e-6
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+@pytest.mark.parametrize("mode", ["directl", "standard"])
+def test_1080p_sampled(renderer, mode):
+    wl = W.WORKLOADS["1080p"]
+    scene = W.make_scene(wl.scene)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(wl.display)
+    L0 = W.light_field_centre(wl.camera_distance, 4.0)
+    img = _frame(renderer, sid, did, L0, mode).reshape(-1)
+    sub = W.sample_subpixels(wl.display, 2048, windows=2, window_px=16, seed=11)
+    V, src = _sources(renderer, did, wl.display, mode)
+    ref = oracle.render_subpixels(oracle.Scene(scene), wl.display, L0, sub, V, src)
+    ok, maxerr, nbad = _accept(img[sub], ref, TOL)
+    assert nbad == 0, f"{nbad} of {sub.size} subpixels outside tolerance; max |err| {maxerr:.3g}"
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+@pytest.mark.parametrize("mode", ["directl", "standard"])
+def test_4k_bf16_sampled(renderer, mode):
+    wl = W.WORKLOADS["4k"]
+    scene = W.make_scene(wl.scene)
+    sid = renderer.load_gaussians(scene, "bf16")
+    did = renderer.set_display(wl.display)
+    L0 = W.light_field_centre(wl.camera_distance, -4.0)
+    img = _frame(renderer, sid, did, L0, mode).reshape(-1)
+    sub = W.sample_subpixels(wl.display, 1024, windows=1, window_px=16, seed=12)
+    V, src = _sources(renderer, did, wl.display, mode)
+    deq = oracle.render_subpixels(oracle.Scene(W.quantise_storage(scene, "bf16")), wl.display, L0,
+                                  sub, V, src)
+    ok, maxerr, nbad = _accept(img[sub], deq, TOL)
+    assert nbad == 0, f"vs dequantised oracle: {nbad} outside 2e-3; max |err| {maxerr:.3g}"
+    full = oracle.render_subpixels(oracle.Scene(scene), wl.display, L0, sub, V, src)
+    ok, maxerr32, nbad = _accept(img[sub], full, TOL_BF16_VS_FP32)
+    print(f"4k bf16 {mode}: max |err| vs dequantised {maxerr:.2e}, vs FP32 attributes {maxerr32:.2e}")
+    assert nbad == 0, f"vs FP32 oracle: {nbad} outside 8e-3; max |err| {maxerr32:.3g}"
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+def _tiny_case(n=400, seed=21, **disp):
+    d = W.Display(**{**dict(width=96, height=54, num_views=9, pitch_lx=5.3, tan_slant=1 / 6,
+                            view_span_deg=30.0), **disp})
+    scene = W.make_scene(W.SceneSpec(n, 2, "uniform", "f32", seed=seed))
+    return d, scene
+
+
+@pytest.mark.parametrize("mode,tile", [("directl", (8, 8)), ("directl", (16, 16)),
+                                       ("directl", (32, 128)), ("directl", (256, 256)),
+                                       ("standard", (8, 8)), ("standard", (32, 32)),
+                                       ("standard", (16, 32)), ("required_only", (64, 16))])
+def test_tile_shapes(renderer, mode, tile):
+    d, scene = _tiny_case()
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 1.0)
+    renderer.set_tile(mode, *tile)
+    try:
+        img = _frame(renderer, sid, did, L0, mode).reshape(-1)
+    finally:
+        renderer.set_tile(mode, *{"directl": (64, 64)}.get(mode, (16, 16)))
+    V, src = _sources(renderer, did, d, mode)
+    ref = oracle.render_subpixels(oracle.Scene(scene), d, L0, np.arange(img.size), V, src)
+    ok, maxerr, nbad = _accept(img, ref, TOL)
+    assert nbad == 0, f"{nbad} outside tolerance; max |err| {maxerr:.3g}"
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+@pytest.mark.parametrize("case", ["ragged", "one_view", "one_gaussian", "behind", "neg_slant"])
+def test_edge_cases(renderer, case):
+    kw = {}
+    n = 400
+    if case == "ragged":
+        kw = dict(width=37, height=23)
+    elif case == "one_view":
+        kw = dict(num_views=1, view_span_deg=0.0)
+    elif case == "one_gaussian":
+        n = 1
+    elif case == "neg_slant":
+        kw = dict(tan_slant=-0.21, offset_k=3.3)
+    d, scene = _tiny_case(n=n, **kw)
+    if case == "one_gaussian":
+        scene["mean"][:] = 0.0
+        scene["log_scale"][:] = -2.0
+        scene["opacity_logit"][:] = 2.0
+    if case == "behind":
+        scene["mean"][:, 2] = -4.5      # every mean behind the cameras (z < -4)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 0.0)
+    for mode in ("directl", "standard"):
+        img = _frame(renderer, sid, did, L0, mode).reshape(-1)
+        if case == "behind":
+            assert not img.any()
+            continue
+        V, src = _sources(renderer, did, d, mode)
+        ref = oracle.render_subpixels(oracle.Scene(scene), d, L0, np.arange(img.size), V, src)
+        ok, maxerr, nbad = _accept(img, ref, TOL)
+        assert nbad == 0, f"{case}/{mode}: {nbad} outside tolerance; max |err| {maxerr:.3g}"
+        if case == "one_gaussian":
+            assert img.max() > 0.1
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+def test_host_output_matches_device_output(renderer):
+    d, scene = _tiny_case()
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 2.5)
+    dev = _frame(renderer, sid, did, L0, "directl")
+    host = torch.empty((d.height, d.width, 3), dtype=torch.float32).pin_memory()
+    renderer.render_to_host(sid, did, L0, host, "directl")
+    assert np.array_equal(host.numpy(), dev)
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+def test_invalid_arguments_are_reported(renderer):
+    from paper_2407_14053_gb300 import DirectLError
+    with pytest.raises(DirectLError):
+        renderer.set_display(W.Display(0, 10, 45, 5.3, 0.1))
+    with pytest.raises(DirectLError):
+        renderer.set_display(W.Display(10, 10, 45, -1.0, 0.1))
+    with pytest.raises(DirectLError):
+        renderer.set_tile("standard", 64, 64)
+    d, scene = _tiny_case(n=10)
+    did = renderer.set_display(d)
+    with pytest.raises(DirectLError):
+        renderer.render(12345, did, np.eye(4))
+    renderer.free_display(did)
