@@ -358,7 +358,10 @@ size_t dtype_size(int32_t dt) { return dt == DL_F32 ? 4 : 2; }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();  // leave no sticky error for the next launch check
+        ms = 0.f;
+    }
     return ms;
 }
 
@@ -756,6 +759,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
     ProjectOut po{W.rec.as<float4>(), W.count.as<uint32_t>(), d_total64};
     DL_CK(launch_project(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, s), "project");
+    DL_CK(mark(1), "event");
     DL_CK(launch_exclusive_scan(W.count.as<uint32_t>(), W.offset.as<uint32_t>(), ne, d_total32,
                                 W.scan_tmp.p, s),
           "scan");

@@ -211,3 +211,29 @@ def test_invalid_arguments_are_reported(renderer):
     with pytest.raises(DirectLError):
         renderer.render(12345, did, np.eye(4))
     renderer.free_display(did)
+
+
+def test_stage_timing_and_pair_counters(renderer):
+    d, scene = _tiny_case()
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 0.5)
+    ref = _frame(renderer, sid, did, L0, "directl")
+    renderer.enable_stage_timing(True)
+    renderer.stage_totals()
+    try:
+        for mode in ("directl", "standard", "directl"):
+            img = _frame(renderer, sid, did, L0, mode)
+        tot, n = renderer.stage_totals()
+    finally:
+        renderer.enable_stage_timing(False)
+    assert n == 3
+    parts = sum(tot[k] for k in ("ms_project", "ms_scan", "ms_sync", "ms_emit", "ms_sort",
+                                 "ms_ranges", "ms_composite", "ms_interweave"))
+    assert tot["ms_total"] > 0 and abs(parts - tot["ms_total"]) <= 1e-3 * max(tot["ms_total"], 1.0) + 0.05
+    assert tot["pairs_evaluated"] >= tot["pairs_blended"] > 0
+    assert tot["n_launches"] > 3 * 10
+    # timing changes nothing in the image
+    assert np.array_equal(img, ref)
+    renderer.free_display(did)
+    renderer.free_scene(sid)
