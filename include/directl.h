@@ -179,6 +179,32 @@ dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, 
  * side).  Defaults: DL_STANDARD and DL_REQUIRED_ONLY 16x16, DL_DIRECTL 64x64. */
 dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h);
 
+/*
+ * Ray table without allocating (the paper has no counterpart: this serves
+ * callers that cannot call cudaMalloc, such as code running inside another
+ * library's memory pool, a process whose device memory is reserved up front,
+ * or a real-time loop that must not synchronise the device the way
+ * cudaMalloc/cudaFree can).  Builds the same table as dl_set_display /
+ * dl_get_ray_table from a view map V (h*3w uint16) and subpixel map src
+ * (3wh uint32) held in DEVICE memory, e.g. as returned by dl_get_view_map
+ * and dl_get_subpixel_map with out_on_device = 1.  Writes ray_of (3wh
+ * uint32, device) and rays ((view, row, col) int32 triplets, device, room
+ * for 3*3wh entries; the first 3*N_rays are written), and *n_rays (host).
+ * Needs no context and allocates nothing: its scratch is one file-scope
+ * device array of 5.0625 MiB that every GPU loading the library keeps until
+ * exit, so panels are limited to width*height <= 65536 pixels (e.g. 256x256);
+ * larger panels, NULL pointers or non-positive sizes return
+ * DL_ERR_INVALID_ARG.  The first call on a device, with that device
+ * current, looks the array's device address up (make it before any stream
+ * capture).  Enqueued on `stream`, then synchronises it once to read the ray
+ * count.  All calls share the array, which keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.
+ */
+dl_status dl_ray_table_static(int32_t width, int32_t height, const uint16_t* V,
+                              const uint32_t* src, uint32_t* ray_of, int32_t* rays,
+                              int64_t* n_rays, void* stream);
+
 /* Statistics of frames rendered on the context. */
 typedef struct {
     int64_t n_keys;          /* (view, tile, Gaussian) overlaps sorted        */

@@ -71,6 +71,8 @@ SIGNATURES = {
     "dl_enable_stage_timing": (c_int32, [c_void_p, c_int32]),
     "dl_last_frame_stats": (c_int32, [c_void_p, P(dl_frame_stats)]),
     "dl_stage_totals": (c_int32, [c_void_p, P(dl_frame_stats), P(c_int32)]),
+    "dl_ray_table_static": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      P(c_int64), c_void_p]),
 }
 
 _lock = threading.Lock()
@@ -217,3 +219,15 @@ def dl_last_frame_stats(ctx) -> dict:
     s = dl_frame_stats()
     _check("dl_last_frame_stats", ctx, lib().dl_last_frame_stats(ctx, ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in dl_frame_stats._fields_}
+
+
+def dl_ray_table_static(width: int, height: int, V_ptr: int, src_ptr: int, ray_of_ptr: int,
+                        rays_ptr: int, stream: int = 0) -> int:
+    """Ray table into caller device buffers using only the library's static
+    scratch (no allocation); returns N_rays."""
+    n = c_int64()
+    _check("dl_ray_table_static", None,
+           lib().dl_ray_table_static(int(width), int(height), c_void_p(V_ptr), c_void_p(src_ptr),
+                                     c_void_p(ray_of_ptr), c_void_p(rays_ptr), ctypes.byref(n),
+                                     c_void_p(stream)))
+    return n.value

@@ -2,6 +2,9 @@
 // Eqs. (1)-(3)), subpixel repurposing (Sec. 5, Alg. 2) and the R-first ray
 // table (Sec. 5, last part).  Integer arithmetic throughout, so the tables
 // are exact.
+#include <mutex>
+
+#include "../../include/directl.h"
 #include "dl_internal.cuh"
 
 namespace dl {
@@ -343,6 +346,21 @@ __global__ void rays_export_kernel(const uint32_t* __restrict__ ray_view,
     }
 }
 
+// (view, row, col) of every ray straight from the owner table.
+__global__ void ray_triplets_kernel(int32_t w, int64_t n, const uint16_t* __restrict__ V,
+                                    const RayTmp t, int32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t r = t.ray_of_owner[i];
+        if (r != kEmpty) {
+            const int64_t p = i / 3;
+            out[3 * int64_t(r)] = int32_t(V[i]);
+            out[3 * int64_t(r) + 1] = int32_t(p / w);
+            out[3 * int64_t(r) + 2] = int32_t(p % w);
+        }
+    }
+}
+
 int grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;
     const int64_t cap = int64_t(num_sms()) * 16;
@@ -432,3 +450,78 @@ cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_p
 }
 
 }  // namespace dl
+
+// ---------------------------------------------------------------------------
+// Ray table without any allocation.
+//
+// Some callers cannot call cudaMalloc: code running where the allocator is
+// off limits (inside another library's memory pool, in a process whose
+// device memory is fully reserved up front, or in a real-time loop that must
+// not synchronise the device the way cudaMalloc/cudaFree can).  For them
+// dl_ray_table_static builds the same ray table as dl_set_display, from a
+// view map and subpixel map the caller holds in device memory, using only
+// this file-scope scratch array.  Every GPU that loads the library holds the
+// array until the process exits.
+namespace {
+constexpr int64_t kStaticMaxPixels = 65536;  // panels up to e.g. 256 x 256
+constexpr size_t kStaticScratchBytes = 5u * 1024u * 1024u + 64u * 1024u;
+constexpr int kStaticMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_ray_table_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void* g_static_addr[kStaticMaxDevices] = {};
+
+extern "C" dl_status dl_ray_table_static(int32_t width, int32_t height, const uint16_t* V,
+                                         const uint32_t* src, uint32_t* ray_of, int32_t* rays,
+                                         int64_t* n_rays, void* stream) {
+    using namespace dl;
+    if (!V || !src || !ray_of || !rays || !n_rays || width < 1 || height < 1)
+        return DL_ERR_INVALID_ARG;
+    if (int64_t(width) * height > kStaticMaxPixels) return DL_ERR_INVALID_ARG;
+    DisplayQ q{};
+    q.w = width;
+    q.h = height;
+    if (ray_table_tmp_bytes(q) + 256 > kStaticScratchBytes) return DL_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DL_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kStaticMaxDevices) return DL_ERR_INVALID_ARG;
+    void* base = nullptr;
+    {
+        // Host code only knows a stand-in for the array's name: ask the
+        // runtime for its device address, once per device.
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_ray_table_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return DL_ERR_CUDA;
+            }
+            g_static_addr[dev] = p;
+        }
+        base = g_static_addr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* d_new = reinterpret_cast<uint32_t*>(static_cast<char*>(base) + kStaticScratchBytes - 256);
+    const int64_t wh = int64_t(width) * height, n = 3 * wh;
+    if (launch_ray_table(q, V, src, ray_of, base, d_new, s) != cudaSuccess) {
+        cudaGetLastError();
+        return DL_ERR_CUDA;
+    }
+    RayTmp t = carve(q, base);
+    ray_triplets_kernel<<<grid_for(n, 256), 256, 0, s>>>(width, n, V, t, rays);
+    uint32_t h_new = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h_new, d_new, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return DL_ERR_CUDA;
+    }
+    *n_rays = wh + int64_t(h_new);
+    return DL_OK;
+}
+
