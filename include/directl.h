@@ -148,9 +148,10 @@ dl_status dl_get_subpixel_map(dl_ctx* ctx, int32_t display_id, uint32_t* out,
                               int32_t out_on_device, void* stream);
 /* Ray table: ray_of[(x*w + y)*3 + k] = ray id of the subpixel (3wh
  * entries); rays[3*r .. 3*r+2] = (view, row, col) of ray r (N_rays*3
- * entries).  Rays 0..wh-1 belong to the R subpixels in row-major order; the
- * rest follow in order of first use by G, then B subpixels.  Either output
- * may be NULL. */
+ * entries).  Rays are numbered in order of first use by the R subpixels
+ * (row-major), then the G, then the B subpixels, so rays 0..wh-1 are the R
+ * subpixels' rays whenever the three channels of every pixel show different
+ * views.  Either output may be NULL. */
 dl_status dl_get_ray_table(dl_ctx* ctx, int32_t display_id, uint32_t* ray_of, int32_t* rays,
                            int32_t out_on_device, void* stream);
 
@@ -191,7 +192,7 @@ dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h)
  * uint32, device) and rays ((view, row, col) int32 triplets, device, room
  * for 3*3wh entries; the first 3*N_rays are written), and *n_rays (host).
  * Needs no context and allocates nothing: its scratch is one file-scope
- * device array of 5.0625 MiB that every GPU loading the library keeps until
+ * device array of 6.5 MiB that every GPU loading the library keeps until
  * exit, so panels are limited to width*height <= 65536 pixels (e.g. 256x256);
  * larger panels, NULL pointers or non-positive sizes return
  * DL_ERR_INVALID_ARG.  The first call on a device, with that device
@@ -205,6 +206,31 @@ dl_status dl_ray_table_static(int32_t width, int32_t height, const uint16_t* V,
                               const uint32_t* src, uint32_t* ray_of, int32_t* rays,
                               int64_t* n_rays, void* stream);
 
+/* Options of a context (dl_set_option).
+ * DL_OPT_SORT_MODE: how each (view, tile) list of Gaussians gets its depth
+ *   order.  DL_SORT_AUTO (default): keys are binned straight into their tile
+ *   and every compositing block sorts its own list in shared memory, unless a
+ *   list is longer than 16384 keys, in which case the frame uses one global
+ *   stable LSD radix sort of (view, tile, depth) keys.  DL_SORT_RADIX: always
+ *   the global radix sort.  DL_SORT_BINNED: always binned; a frame with a
+ *   longer list fails with DL_ERR_CAPACITY.  Both give the same image. */
+enum { DL_OPT_SORT_MODE = 1, DL_OPT_EVAL_DIRECTL = 2, DL_OPT_EVAL_STANDARD = 3,
+       DL_OPT_WARP_LIST_CAP = 4 };
+enum { DL_SORT_AUTO = 0, DL_SORT_RADIX = 1, DL_SORT_BINNED = 2 };
+/* DL_OPT_EVAL_DIRECTL / DL_OPT_EVAL_STANDARD: how a warp evaluates a tile's
+ * Gaussians on the binned path.  DL_EVAL_DIRECT: every lane walks the
+ * culled list for its own ray.  DL_EVAL_TRANSPOSED: each lane holds one
+ * Gaussian and tests it against all of the warp's unfinished rays, then each
+ * lane blends its own candidates in order.  Defaults: transposed for
+ * DL_DIRECTL and DL_REQUIRED_ONLY, direct for DL_STANDARD.  Same image
+ * either way. */
+enum { DL_EVAL_DIRECT = 0, DL_EVAL_TRANSPOSED = 1 };
+/* DL_OPT_WARP_LIST_CAP: on the binned DL_DIRECTL / DL_REQUIRED_ONLY path,
+ * tile lists of up to this many keys (512 or 1024) are composited by one warp
+ * each; longer lists by a thread block.  0 sends every list to thread
+ * blocks.  Default 512.  Same image either way. */
+dl_status dl_set_option(dl_ctx* ctx, int32_t option, int64_t value);
+
 /* Statistics of frames rendered on the context. */
 typedef struct {
     int64_t n_keys;          /* (view, tile, Gaussian) overlaps sorted        */
@@ -215,6 +241,9 @@ typedef struct {
     int32_t tile_w, tile_h;
     int32_t sort_bits;       /* key bits the radix sort ordered              */
     int32_t n_launches;      /* kernels the frame launched                   */
+    int64_t lists_small;     /* tile lists composited by the small class     */
+    int64_t lists_large;     /* tile lists composited by the large class     */
+    int64_t max_list;        /* longest tile list (keys)                     */
     float ms_project, ms_scan, ms_sync, ms_emit, ms_sort, ms_ranges, ms_composite,
         ms_interweave, ms_total; /* stage durations (CUDA events)        */
 } dl_frame_stats;

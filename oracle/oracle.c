@@ -225,8 +225,12 @@ int or_repurpose(const or_display* p, const uint16_t* V, uint32_t* src) {
 /* ------------------------------------------------------------------------ */
 
 /* The rows of R~_rays follow the R subpixels in row-major order, so the first
- * wh rays are the rays of the R subpixels.  Reading: the remaining rays follow
- * in order of first use by the G subpixels (row-major), then the B subpixels. */
+ * rays are the rays of the R subpixels (wh of them whenever the three
+ * channels of every pixel show different views).  Reading: every ray is
+ * numbered in order of first use, scanning the R subpixels (row-major), then
+ * the G subpixels, then the B subpixels.  (When N_v < L_x two channels of a
+ * pixel can show one view; Alg. 2 can then give one ray's channel to two
+ * subpixels, and two R subpixels may share a ray.) */
 int or_ray_table(const or_display* p, const uint16_t* V, const uint32_t* src,
                  uint32_t* ray_of, int32_t* ray_v, int32_t* ray_r, int32_t* ray_c,
                  int64_t* n_rays) {
@@ -253,16 +257,12 @@ int or_ray_table(const or_display* p, const uint16_t* V, const uint32_t* src,
                 uint64_t hsh = ((uint64_t)key * 0x9E3779B97F4A7C15ull) & (cap - 1);
                 while (keys[hsh] != -1 && keys[hsh] != key) hsh = (hsh + 1) & (cap - 1);
                 if (keys[hsh] == -1) {
-                    if (k == 0 && count != x * w + y) { rc = -4; break; } /* R rays must be distinct */
                     keys[hsh] = key;
                     vals[hsh] = (uint32_t)count;
                     ray_v[count] = (int32_t)v;
                     ray_r[count] = (int32_t)xs;
                     ray_c[count] = (int32_t)ys;
                     count++;
-                } else if (k == 0) {
-                    rc = -4;
-                    break;
                 }
                 ray_of[i] = vals[hsh];
             }

@@ -25,6 +25,9 @@ DL_ERR_CAPACITY = -7
 
 DL_F32, DL_BF16, DL_F16 = 0, 1, 2
 DL_DIRECTL, DL_STANDARD, DL_REQUIRED_ONLY = 0, 1, 2
+DL_OPT_SORT_MODE, DL_OPT_EVAL_DIRECTL, DL_OPT_EVAL_STANDARD, DL_OPT_WARP_LIST_CAP = 1, 2, 3, 4
+DL_SORT_AUTO, DL_SORT_RADIX, DL_SORT_BINNED = 0, 1, 2
+DL_EVAL_DIRECT, DL_EVAL_TRANSPOSED = 0, 1
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -45,7 +48,8 @@ class dl_display_params(ctypes.Structure):
 class dl_frame_stats(ctypes.Structure):
     _fields_ = [("n_keys", c_int64), ("n_rays", c_int64), ("pairs_evaluated", c_int64),
                 ("pairs_blended", c_int64), ("tile_w", c_int32), ("tile_h", c_int32),
-                ("sort_bits", c_int32), ("n_launches", c_int32)] + [
+                ("sort_bits", c_int32), ("n_launches", c_int32), ("lists_small", c_int64),
+                ("lists_large", c_int64), ("max_list", c_int64)] + [
         (f, ctypes.c_float) for f in ("ms_project", "ms_scan", "ms_sync", "ms_emit", "ms_sort",
                                       "ms_ranges", "ms_composite", "ms_interweave", "ms_total")]
 
@@ -71,6 +75,7 @@ SIGNATURES = {
     "dl_enable_stage_timing": (c_int32, [c_void_p, c_int32]),
     "dl_last_frame_stats": (c_int32, [c_void_p, P(dl_frame_stats)]),
     "dl_stage_totals": (c_int32, [c_void_p, P(dl_frame_stats), P(c_int32)]),
+    "dl_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
     "dl_ray_table_static": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                       P(c_int64), c_void_p]),
 }
@@ -202,6 +207,10 @@ def dl_query_footprint(ctx, scene_id: int, display_id: int, mode: int) -> int:
 
 def dl_set_tile(ctx, mode: int, tile_w: int, tile_h: int) -> None:
     _check("dl_set_tile", ctx, lib().dl_set_tile(ctx, int(mode), int(tile_w), int(tile_h)))
+
+
+def dl_set_option(ctx, option: int, value: int) -> None:
+    _check("dl_set_option", ctx, lib().dl_set_option(ctx, int(option), int(value)))
 
 
 def dl_enable_stage_timing(ctx, enable: bool) -> None:

@@ -55,14 +55,15 @@ struct Scene {
 
 struct TileGroups {
     int32_t tw = 0, th = 0, ntx = 0, nty = 0, ntiles = 0;
-    int64_t n_work = 0;
-    DevBuf grouped, work;
+    int64_t n_work = 0;   // <= 128-ray chunks (global radix path)
+    int64_t n_gwork = 0;  // groups holding rays (binned path)
+    DevBuf grouped, work, gwork;
 };
 
 struct RaySet {
     bool built = false;
     int64_t n_rays = 0;
-    DevBuf src, ray_of, ray_view, ray_pix, ray_slot;
+    DevBuf src, ray_of, ray_view, ray_pix;
     std::map<int64_t, std::unique_ptr<TileGroups>> groups;
 };
 
@@ -83,12 +84,13 @@ struct PendingFrame {
     StageEvents* ev;
     int64_t n_keys, n_rays;
     int32_t launches;
+    int64_t lists_small, lists_large, max_list;
 };
 
 struct Workspace {
     DevBuf cams, rec, count, offset, scan_tmp, keys[2], vals[2], ranges, radix_tmp, Mm, out, small,
-        pairs;
-    unsigned long long* h_total = nullptr;  // pinned
+        pairs, gcount, gstart, gfill, lists, gscan_tmp, raycol;
+    unsigned long long* h_total = nullptr;  // pinned, 256 bytes (copy of `small`)
     size_t last_bytes = 0;
     std::vector<StageEvents*> ev_free;
     std::vector<PendingFrame> pending;
@@ -103,7 +105,8 @@ struct Workspace {
     }
     size_t footprint() const {
         size_t b = cams.bytes + rec.bytes + count.bytes + offset.bytes + scan_tmp.bytes + ranges.bytes +
-                   radix_tmp.bytes + Mm.bytes + out.bytes + small.bytes;
+                   radix_tmp.bytes + Mm.bytes + out.bytes + small.bytes + gcount.bytes + gstart.bytes +
+                   gfill.bytes + lists.bytes + gscan_tmp.bytes + raycol.bytes;
         for (int i = 0; i < 2; ++i) b += keys[i].bytes + vals[i].bytes;
         return b;
     }
@@ -119,6 +122,9 @@ struct dl_ctx {
     std::map<int32_t, std::unique_ptr<dl::Display>> displays;
     dl::Workspace ws;
     int32_t tile[3][2] = {{64, 64}, {16, 16}, {16, 16}};
+    int32_t sort_mode = DL_SORT_AUTO;
+    int32_t eval_transposed[3] = {1, 0, 1};  // per mode
+    int32_t warp_cap = 512;
     bool timing = false;
     dl_frame_stats stats{};
 };
@@ -215,20 +221,18 @@ dl_status build_rayset(dl_ctx* ctx, Display& D, RaySet& R, bool identity, cudaSt
     DevBuf tmp;
     DL_CK(tmp.reserve(ray_table_tmp_bytes(q)), "alloc ray-table scratch");
     DL_CK(ctx->ws.small.reserve(256), "alloc small");
-    uint32_t* d_new = ctx->ws.small.as<uint32_t>();
+    uint32_t* d_n = ctx->ws.small.as<uint32_t>();
     DL_CK(launch_ray_table(q, D.V.as<uint16_t>(), R.src.as<uint32_t>(), R.ray_of.as<uint32_t>(),
-                           tmp.p, d_new, s),
+                           tmp.p, d_n, s),
           "ray table");
-    uint32_t h_new = 0;
-    DL_CK(cudaMemcpyAsync(&h_new, d_new, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "copy");
+    uint32_t h_n = 0;
+    DL_CK(cudaMemcpyAsync(&h_n, d_n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "copy");
     DL_CK(cudaStreamSynchronize(s), "sync");
-    R.n_rays = int64_t(q.w) * q.h + h_new;
+    R.n_rays = int64_t(h_n);
     DL_CK(R.ray_view.reserve(4 * size_t(R.n_rays)), "alloc rays");
     DL_CK(R.ray_pix.reserve(4 * size_t(R.n_rays)), "alloc rays");
-    DL_CK(R.ray_slot.reserve(12 * size_t(R.n_rays)), "alloc rays");
-    DL_CK(launch_ray_attributes(q, D.V.as<uint16_t>(), R.ray_of.as<uint32_t>(), tmp.p,
-                                R.ray_view.as<uint32_t>(), R.ray_pix.as<uint32_t>(),
-                                R.ray_slot.as<int32_t>(), R.n_rays, s),
+    DL_CK(launch_ray_attributes(q, D.V.as<uint16_t>(), tmp.p, R.ray_view.as<uint32_t>(),
+                                R.ray_pix.as<uint32_t>(), s),
           "ray attributes");
     DL_CK(cudaStreamSynchronize(s), "sync");
     R.groups.clear();
@@ -237,6 +241,21 @@ dl_status build_rayset(dl_ctx* ctx, Display& D, RaySet& R, bool identity, cudaSt
 }
 
 constexpr int kRaysPerBlock = 128;
+// Tile lists of up to kSmallCap keys are sorted in a small shared-memory
+// buffer; longer ones up to kLargeCap in one sized to the longest list; a
+// frame with a longer list (or one whose buffer would not fit in shared
+// memory) falls back to the global radix sort.
+constexpr int kSmallCap = 1024;
+constexpr int kLargeCap = 16384;
+
+size_t max_smem_optin(int device) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        cudaGetLastError();
+        v = 48 * 1024;
+    }
+    return size_t(v);
+}
 
 // Rays of a ray set grouped by (view, tile) for one tile shape, and the work
 // list of the DirectL compositing kernel (chunks of <= 128 rays).
@@ -268,16 +287,15 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
           "group keys");
     int alt = 0;
     DL_CK(radix_sort_pairs(k0.as<unsigned long long>(), v0.as<uint32_t>(),
-                           k1.as<unsigned long long>(), v1.as<uint32_t>(), nr, bits_for(ngroups),
+                           k1.as<unsigned long long>(), v1.as<uint32_t>(), nr, bits_for(ngroups) + 16,
                            rtmp.p, &alt, s),
           "group sort");
     unsigned long long* ks = alt ? k1.as<unsigned long long>() : k0.as<unsigned long long>();
     uint32_t* vs = alt ? v1.as<uint32_t>() : v0.as<uint32_t>();
     DL_CK(cudaMemsetAsync(ranges.p, 0, 8 * size_t(ngroups), s), "memset");
-    DL_CK(launch_key_ranges(ks, nr, 0, ranges.as<uint2>(), s), "group ranges");
-    DL_CK(G->grouped.reserve(16 * size_t(nr)), "alloc");
-    DL_CK(launch_ray_group_gather(vs, R.ray_pix.as<uint32_t>(), R.ray_slot.as<int32_t>(), nr,
-                                  G->grouped.as<int4>(), s),
+    DL_CK(launch_key_ranges(ks, nr, 16, ranges.as<uint2>(), ngroups, s), "group ranges");
+    DL_CK(G->grouped.reserve(8 * size_t(nr)), "alloc");
+    DL_CK(launch_ray_group_gather(vs, R.ray_pix.as<uint32_t>(), nr, G->grouped.as<int2>(), s),
           "group gather");
     std::vector<uint2> h_ranges(static_cast<size_t>(ngroups));
     DL_CK(cudaMemcpyAsync(h_ranges.data(), ranges.p, 8 * size_t(ngroups), cudaMemcpyDeviceToHost, s),
@@ -294,6 +312,16 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
     DL_CK(G->work.reserve(16 * std::max<size_t>(work.size(), 1)), "alloc");
     if (!work.empty())
         DL_CK(cudaMemcpyAsync(G->work.p, work.data(), 16 * work.size(), cudaMemcpyHostToDevice, s),
+              "copy");
+    std::vector<int4> gwork;
+    for (int64_t g = 0; g < ngroups; ++g) {
+        const uint2 r = h_ranges[size_t(g)];
+        if (r.y > r.x) gwork.push_back(make_int4(int(g), int(r.x), int(r.y), 0));
+    }
+    G->n_gwork = int64_t(gwork.size());
+    DL_CK(G->gwork.reserve(16 * std::max<size_t>(gwork.size(), 1)), "alloc");
+    if (!gwork.empty())
+        DL_CK(cudaMemcpyAsync(G->gwork.p, gwork.data(), 16 * gwork.size(), cudaMemcpyHostToDevice, s),
               "copy");
     DL_CK(cudaStreamSynchronize(s), "sync");
     *out = G.get();
@@ -398,7 +426,7 @@ dl_status dl_create(dl_ctx** out, int32_t device) {
     dl_ctx* c = new (std::nothrow) dl_ctx();
     if (!c) return DL_ERR_OOM;
     c->device = device;
-    if (cudaMallocHost(&c->ws.h_total, sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMallocHost(&c->ws.h_total, 256) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return DL_ERR_OOM;
@@ -593,6 +621,34 @@ dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h)
     return DL_OK;
 }
 
+dl_status dl_set_option(dl_ctx* ctx, int32_t option, int64_t value) {
+    if (!ctx) return DL_ERR_INVALID_ARG;
+    if (option == DL_OPT_SORT_MODE) {
+        if (value < DL_SORT_AUTO || value > DL_SORT_BINNED)
+            return fail(ctx, DL_ERR_INVALID_ARG, "sort mode %lld", (long long)value);
+        ctx->sort_mode = int32_t(value);
+        return DL_OK;
+    }
+    if (option == DL_OPT_WARP_LIST_CAP) {
+        if (value != 0 && value != 512 && value != 1024)
+            return fail(ctx, DL_ERR_INVALID_ARG, "warp list capacity %lld", (long long)value);
+        ctx->warp_cap = int32_t(value);
+        return DL_OK;
+    }
+    if (option == DL_OPT_EVAL_DIRECTL || option == DL_OPT_EVAL_STANDARD) {
+        if (value != DL_EVAL_DIRECT && value != DL_EVAL_TRANSPOSED)
+            return fail(ctx, DL_ERR_INVALID_ARG, "evaluation strategy %lld", (long long)value);
+        if (option == DL_OPT_EVAL_DIRECTL) {
+            ctx->eval_transposed[DL_DIRECTL] = int32_t(value);
+            ctx->eval_transposed[DL_REQUIRED_ONLY] = int32_t(value);
+        } else {
+            ctx->eval_transposed[DL_STANDARD] = int32_t(value);
+        }
+        return DL_OK;
+    }
+    return fail(ctx, DL_ERR_INVALID_ARG, "unknown option %d", option);
+}
+
 dl_status dl_enable_stage_timing(dl_ctx* ctx, int32_t enable) {
     dl_status st = check_ctx(ctx);
     if (st) return st;
@@ -634,6 +690,9 @@ dl_status dl_stage_totals(dl_ctx* ctx, dl_frame_stats* sum, int32_t* n_frames) {
         t.n_keys += f.n_keys;
         t.n_rays += f.n_rays;
         t.n_launches += f.launches;
+        t.lists_small += f.lists_small;
+        t.lists_large += f.lists_large;
+        t.max_list = std::max(t.max_list, f.max_list);
         W.ev_free.push_back(f.ev);
     }
     *n_frames = int32_t(W.pending.size());
@@ -696,7 +755,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         }
         E = W.ev_free.back();
         W.ev_free.pop_back();
-        W.pending.push_back(PendingFrame{E, 0, 0, 0});
+        W.pending.push_back(PendingFrame{E, 0, 0, 0, 0, 0, 0});
     }
     auto mark = [&](int i) -> cudaError_t {
         return timing ? cudaEventRecord(E->e[i], s) : cudaSuccess;
@@ -748,57 +807,62 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     const int64_t ntiles = int64_t(pp.ntx) * pp.nty;
     const int64_t ne = int64_t(nv) * S.n;
     if (ne >= (int64_t(1) << 31)) return fail(ctx, DL_ERR_CAPACITY, "views x Gaussians >= 2^31");
+    const int64_t ngroups = int64_t(nv) * ntiles;
+    if (ngroups >= (int64_t(1) << 31) - 1) return fail(ctx, DL_ERR_CAPACITY, "too many tiles");
     DL_CK(W.rec.reserve(48 * size_t(ne)), "alloc records");
     DL_CK(W.count.reserve(4 * size_t(ne)), "alloc counts");
-    DL_CK(W.offset.reserve(4 * size_t(ne)), "alloc offsets");
-    DL_CK(W.scan_tmp.reserve(scan_tmp_bytes(ne)), "alloc scan");
+    DL_CK(W.gcount.reserve(4 * size_t(ngroups + 1)), "alloc group counts");
+    DL_CK(W.gstart.reserve(4 * size_t(ngroups + 1)), "alloc group starts");
+    DL_CK(W.gscan_tmp.reserve(scan_tmp_bytes(ngroups + 1)), "alloc scan");
     DL_CK(W.small.reserve(256), "alloc");
     unsigned long long* d_total64 = W.small.as<unsigned long long>();
     uint32_t* d_total32 = reinterpret_cast<uint32_t*>(W.small.as<char>() + 64);
-    DL_CK(cudaMemsetAsync(d_total64, 0, 8, s), "memset");
+    uint32_t* d_meta = reinterpret_cast<uint32_t*>(W.small.as<char>() + 128);
+    DL_CK(cudaMemsetAsync(W.small.p, 0, 256, s), "memset");
+    DL_CK(cudaMemsetAsync(W.gcount.p, 0, 4 * size_t(ngroups + 1), s), "memset");
     const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
-    ProjectOut po{W.rec.as<float4>(), W.count.as<uint32_t>(), d_total64};
+    ProjectOut po{W.rec.as<float4>(), W.count.as<uint32_t>(), d_total64, W.gcount.as<uint32_t>()};
     DL_CK(launch_project(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, s), "project");
     DL_CK(mark(1), "event");
-    DL_CK(launch_exclusive_scan(W.count.as<uint32_t>(), W.offset.as<uint32_t>(), ne, d_total32,
-                                W.scan_tmp.p, s),
-          "scan");
+    // group starts (one extra entry: gstart[ngroups] = number of keys) and the
+    // split of the compositing work by list length
+    DL_CK(launch_exclusive_scan(W.gcount.as<uint32_t>(), W.gstart.as<uint32_t>(), ngroups + 1,
+                                d_total32, W.gscan_tmp.p, s),
+          "group scan");
+    const int4* gwork = mode == DL_STANDARD ? nullptr : G->gwork.as<int4>();
+    const int64_t n_work = mode == DL_STANDARD ? ngroups : G->n_gwork;
+    DL_CK(W.lists.reserve(8 * size_t(std::max<int64_t>(n_work, 1))), "alloc lists");
+    int32_t* small_list = W.lists.as<int32_t>();
+    int32_t* large_list = small_list + std::max<int64_t>(n_work, 1);
+    // DirectL: lists up to warp_list_cap() keys go to the warp-per-group
+    // kernel, longer ones to the block kernel; standard: small / large block
+    // classes.
+    const bool warp_path = mode != DL_STANDARD && ctx->warp_cap > 0;
+    const uint32_t split = warp_path ? uint32_t(ctx->warp_cap) : uint32_t(kSmallCap);
+    DL_CK(launch_partition(gwork, n_work, W.gstart.as<uint32_t>(), split, small_list, large_list,
+                           d_meta, s),
+          "partition");
     DL_CK(mark(2), "event");
-    DL_CK(cudaMemcpyAsync(W.h_total, d_total64, 8, cudaMemcpyDeviceToHost, s), "copy total");
+    DL_CK(cudaMemcpyAsync(W.h_total, W.small.p, 256, cudaMemcpyDeviceToHost, s), "copy totals");
     DL_CK(cudaStreamSynchronize(s), "sync");
-    const unsigned long long nkeys = *W.h_total;
+    const unsigned long long nkeys = W.h_total[0];
+    const uint32_t* h_meta = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(W.h_total) + 128);
+    const int64_t n_small = h_meta[0], n_large = h_meta[1];
+    const int64_t max_len = h_meta[2];
     if (nkeys >= (1ull << 31) - 1)
         return fail(ctx, DL_ERR_CAPACITY, "frame needs %llu tile keys (limit 2^31-1)", nkeys);
-
-    // ---- tile keys and depth sort ----
     const int64_t nk = int64_t(nkeys);
-    for (int i = 0; i < 2; ++i) {
-        DL_CK(W.keys[i].reserve(8 * size_t(nk > 0 ? nk : 1)), "alloc keys");
-        DL_CK(W.vals[i].reserve(4 * size_t(nk > 0 ? nk : 1)), "alloc vals");
-    }
-    DL_CK(W.radix_tmp.reserve(radix_tmp_bytes(nk)), "alloc radix");
-    DL_CK(W.ranges.reserve(8 * size_t(nv) * size_t(ntiles)), "alloc ranges");
-    DL_CK(mark(3), "event");
-    DL_CK(launch_emit_keys(pp, nv, W.rec.as<float4>(), W.count.as<uint32_t>(),
-                           W.offset.as<uint32_t>(), W.keys[0].as<unsigned long long>(),
-                           W.vals[0].as<uint32_t>(), s),
-          "emit keys");
-    DL_CK(mark(4), "event");
-    const int sort_bits = 28 + bits_for(int64_t(nv) * ntiles);
-    int alt = 0;
-    DL_CK(radix_sort_pairs(W.keys[0].as<unsigned long long>(), W.vals[0].as<uint32_t>(),
-                           W.keys[1].as<unsigned long long>(), W.vals[1].as<uint32_t>(), nk,
-                           sort_bits, W.radix_tmp.p, &alt, s),
-          "sort");
-    unsigned long long* keys = W.keys[alt].as<unsigned long long>();
-    uint32_t* vals = W.vals[alt].as<uint32_t>();
-    DL_CK(mark(5), "event");
-    DL_CK(cudaMemsetAsync(W.ranges.p, 0, 8 * size_t(nv) * size_t(ntiles), s), "memset");
-    DL_CK(launch_key_ranges(keys, nk, 28, W.ranges.as<uint2>(), s), "ranges");
-    DL_CK(mark(6), "event");
+    int cap_large = warp_path ? 2 * ctx->warp_cap : 1;
+    while (cap_large < max_len) cap_large <<= 1;
+    const int binned_threads = mode == DL_STANDARD ? tw * th : kBinnedThreads;
+    bool binned = ctx->sort_mode != DL_SORT_RADIX && max_len <= kLargeCap &&
+                  binned_smem_bytes(std::max(cap_large, kSmallCap), binned_threads) <=
+                      max_smem_optin(ctx->device);
+    if (ctx->sort_mode == DL_SORT_BINNED && !binned)
+        return fail(ctx, DL_ERR_CAPACITY, "a tile list holds %lld keys (binned limit %d)",
+                    (long long)max_len, kLargeCap);
     unsigned long long* pairs = timing ? W.pairs.as<unsigned long long>() : nullptr;
 
-    // ---- compositing ----
     CompositeParams cp{};
     cp.n = S.n;
     cp.width = w;
@@ -815,20 +879,110 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         DL_CK(W.out.reserve(out_bytes), "alloc out");
         dst = W.out.as<float>();
     }
+    float* Mm = nullptr;
+    float* raycol = nullptr;
     if (mode == DL_STANDARD) {
         DL_CK(W.Mm.reserve(12 * size_t(nv) * size_t(w) * size_t(h)), "alloc M_m");
-        DL_CK(launch_composite_full(cp, nv, W.ranges.as<uint2>(), vals, W.rec.as<float4>(),
-                                    W.Mm.as<float>(), pairs, s),
-              "composite full");
-        DL_CK(mark(7), "event");
-        DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), W.Mm.as<float>(), dst, s),
-              "interweave");
+        Mm = W.Mm.as<float>();
     } else {
-        DL_CK(launch_composite_rays(cp, G->work.as<int4>(), G->n_work, G->grouped.as<int4>(),
-                                    W.ranges.as<uint2>(), vals, W.rec.as<float4>(), dst, pairs, s),
-              "composite rays");
-        DL_CK(mark(7), "event");
+        DL_CK(W.raycol.reserve(12 * size_t(R->n_rays > 0 ? R->n_rays : 1)), "alloc ray colours");
+        raycol = W.raycol.as<float>();
     }
+    int sort_bits = 0;
+    int launches = int32_t((nv + kCamBatch - 1) / kCamBatch) + 1 + 3 + (n_work > 0 ? 1 : 0);
+    DL_CK(W.keys[0].reserve(8 * size_t(nk > 0 ? nk : 1)), "alloc keys");
+    if (binned) {
+        // ---- binned keys, sorted per tile in shared memory while compositing ----
+        DL_CK(W.gfill.reserve(4 * size_t(ngroups)), "alloc");
+        DL_CK(cudaMemsetAsync(W.gfill.p, 0, 4 * size_t(ngroups), s), "memset");
+        DL_CK(mark(3), "event");
+        DL_CK(launch_emit_binned(pp, nv, W.rec.as<float4>(), W.count.as<uint32_t>(),
+                                 W.gstart.as<uint32_t>(), W.gfill.as<uint32_t>(),
+                                 W.keys[0].as<unsigned long long>(), s),
+              "emit binned");
+        DL_CK(mark(4), "event");
+        DL_CK(mark(5), "event");
+        DL_CK(mark(6), "event");
+        const unsigned long long* keys = W.keys[0].as<unsigned long long>();
+        if (mode == DL_STANDARD) {
+            DL_CK(launch_composite_full_binned(cp, small_list, n_small, kSmallCap,
+                                               W.gstart.as<uint32_t>(), keys, W.rec.as<float4>(), Mm,
+                                               pairs, ctx->eval_transposed[mode], s),
+                  "composite full (small lists)");
+            DL_CK(launch_composite_full_binned(cp, large_list, n_large, cap_large,
+                                               W.gstart.as<uint32_t>(), keys, W.rec.as<float4>(), Mm,
+                                               pairs, ctx->eval_transposed[mode], s),
+                  "composite full (large lists)");
+        } else {
+            if (warp_path) {
+                DL_CK(launch_composite_rays_warp(cp, ctx->warp_cap, G->gwork.as<int4>(), small_list,
+                                                 n_small, G->grouped.as<int2>(),
+                                                 W.gstart.as<uint32_t>(), keys, W.rec.as<float4>(),
+                                                 raycol, pairs, s),
+                      "composite rays (warp per group)");
+            } else {
+                DL_CK(launch_composite_rays_binned(cp, G->gwork.as<int4>(), small_list, n_small,
+                                                   kSmallCap, G->grouped.as<int2>(),
+                                                   W.gstart.as<uint32_t>(), keys, W.rec.as<float4>(),
+                                                   raycol, pairs, ctx->eval_transposed[mode], s),
+                      "composite rays (small lists)");
+            }
+            DL_CK(launch_composite_rays_binned(cp, G->gwork.as<int4>(), large_list, n_large, cap_large,
+                                               G->grouped.as<int2>(), W.gstart.as<uint32_t>(), keys,
+                                               W.rec.as<float4>(), raycol, pairs,
+                                               ctx->eval_transposed[mode], s),
+                  "composite rays (large lists)");
+        }
+        launches += 1 + (n_small > 0 ? 1 : 0) + (n_large > 0 ? 1 : 0);
+    } else {
+        // ---- global tile keys and a stable LSD radix sort ----
+        DL_CK(W.offset.reserve(4 * size_t(ne)), "alloc offsets");
+        DL_CK(W.scan_tmp.reserve(scan_tmp_bytes(ne)), "alloc scan");
+        DL_CK(W.keys[1].reserve(8 * size_t(nk > 0 ? nk : 1)), "alloc keys");
+        for (int i = 0; i < 2; ++i) DL_CK(W.vals[i].reserve(4 * size_t(nk > 0 ? nk : 1)), "alloc vals");
+        DL_CK(W.radix_tmp.reserve(radix_tmp_bytes(nk)), "alloc radix");
+        DL_CK(W.ranges.reserve(8 * size_t(ngroups)), "alloc ranges");
+        DL_CK(mark(3), "event");
+        DL_CK(launch_exclusive_scan(W.count.as<uint32_t>(), W.offset.as<uint32_t>(), ne, nullptr,
+                                    W.scan_tmp.p, s),
+              "scan");
+        DL_CK(launch_emit_keys(pp, nv, W.rec.as<float4>(), W.count.as<uint32_t>(),
+                               W.offset.as<uint32_t>(), W.keys[0].as<unsigned long long>(),
+                               W.vals[0].as<uint32_t>(), s),
+              "emit keys");
+        DL_CK(mark(4), "event");
+        sort_bits = 28 + bits_for(ngroups);
+        int alt = 0;
+        DL_CK(radix_sort_pairs(W.keys[0].as<unsigned long long>(), W.vals[0].as<uint32_t>(),
+                               W.keys[1].as<unsigned long long>(), W.vals[1].as<uint32_t>(), nk,
+                               sort_bits, W.radix_tmp.p, &alt, s),
+              "sort");
+        unsigned long long* keys = W.keys[alt].as<unsigned long long>();
+        uint32_t* vals = W.vals[alt].as<uint32_t>();
+        DL_CK(mark(5), "event");
+        DL_CK(cudaMemsetAsync(W.ranges.p, 0, 8 * size_t(ngroups), s), "memset");
+        DL_CK(launch_key_ranges(keys, nk, 28, W.ranges.as<uint2>(), ngroups, s), "ranges");
+        DL_CK(mark(6), "event");
+        if (mode == DL_STANDARD) {
+            DL_CK(launch_composite_full(cp, nv, W.ranges.as<uint2>(), vals, W.rec.as<float4>(), Mm,
+                                        pairs, s),
+                  "composite full");
+        } else {
+            DL_CK(launch_composite_rays(cp, G->work.as<int4>(), G->n_work, G->grouped.as<int2>(),
+                                        W.ranges.as<uint2>(), vals, W.rec.as<float4>(), raycol, pairs,
+                                        s),
+                  "composite rays");
+        }
+        launches += 3 + 1 + 3 * ((nk > 1) ? (sort_bits + 7) / 8 : 0) + (nk > 0 ? 1 : 0) +
+                    (mode == DL_STANDARD ? 1 : (G->n_work > 0 ? 1 : 0));
+    }
+    DL_CK(mark(7), "event");
+    if (mode == DL_STANDARD) {
+        DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), Mm, dst, s), "interweave");
+    } else {
+        DL_CK(launch_reorder(R->ray_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst, s), "reorder");
+    }
+    launches += 1;
     DL_CK(mark(8), "event");
     if (!out_on_device)
         DL_CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, s), "copy frame");
@@ -840,16 +994,18 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     fs.tile_w = tw;
     fs.tile_h = th;
     fs.sort_bits = sort_bits;
-    // store_cams, project, 3 scan, emit, 3 per radix pass, ranges, composite
-    // (+ interweave)
-    fs.n_launches = int32_t((nv + kCamBatch - 1) / kCamBatch) + 1 + 3 + 1 +
-                    3 * ((nk > 1) ? (sort_bits + 7) / 8 : 0) + (nk > 0 ? 1 : 0) +
-                    (mode == DL_STANDARD ? 2 : (G->n_work > 0 ? 1 : 0));
+    fs.n_launches = launches;
+    fs.lists_small = n_small;
+    fs.lists_large = n_large;
+    fs.max_list = max_len;
     if (timing) {
         PendingFrame& pf = W.pending.back();
         pf.n_keys = fs.n_keys;
         pf.n_rays = fs.n_rays;
         pf.launches = fs.n_launches;
+        pf.lists_small = fs.lists_small;
+        pf.lists_large = fs.lists_large;
+        pf.max_list = fs.max_list;
     }
     W.last_bytes = W.footprint();
     if (!out_on_device) DL_CK(cudaStreamSynchronize(s), "sync");

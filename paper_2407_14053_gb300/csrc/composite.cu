@@ -2,34 +2,71 @@
 // the standard paradigm's interweave (Alg. 1).
 //
 // Both compositing kernels stream one (view, tile) list of depth-sorted
-// Gaussian records through shared memory in batches; every thread composites
-// its own ray against the whole batch and the block stops as soon as every
-// ray's transmittance would fall below 1e-4 (block-wide vote).
+// Gaussian records through shared memory in batches.  Each warp first tests
+// 32 records at a time against the bounding box of its own rays (one ballot)
+// and then composites only the records whose alpha >= 1/255 box touches it,
+// in list order, so the per-ray sequence of composited Gaussians is exactly
+// the depth-sorted one.  A block stops once every ray's transmittance would
+// fall below 1e-4 (block-wide vote).
 //  - composite_rays_kernel (DirectL): one block per work item, i.e. up to
-//    kRayThreads required rays of one (view, tile); each ray writes only the
-//    subpixels it feeds (Sec. 4 step (3), the channel reorder folded in).
+//    kRayThreads required rays of one (view, tile), ordered along a Morton
+//    curve so that a warp's rays are close together; each ray writes its
+//    colour, and reorder_kernel gathers the encoded image by the ray table
+//    (Sec. 4 step (3): the channel reorder by precomputed indices).
 //  - composite_full_kernel (standard paradigm): one block per (view, tile),
 //    one thread per pixel, every pixel of every view into M_m.
+#include <climits>
+
 #include "dl_internal.cuh"
 
 namespace dl {
 namespace {
 
 constexpr int kRayThreads = 128;
+constexpr float kLog2MinAlpha = -7.99435343685886f;  // log2(1/255)
 
 struct Acc {
     float T, c0, c1, c2;
     uint32_t blended;
 };
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Asynchronous 16-byte global -> shared copies (Ampere-and-later cp.async),
+// used to fetch the next batch of records while the current one is blended.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// log2 alpha = A dx^2 + B dx dy + C dy^2 + log2 o at pixel offset (dx, dy)
+// from the record's mean.  Every caller evaluates exactly this expression, so
+// a pre-test and the blend below always agree bit for bit.
+__device__ __forceinline__ float log2_alpha(float px, float py, float u, float v, float A, float B,
+                                            float C, float L) {
+    const float dx = px - u, dy = py - v;
+    return fmaf(A * dx, dx, fmaf(B * dx, dy, fmaf(C * dy, dy, L)));
+}
+
 // One record against one ray.  Returns false once the ray is finished.
-// log2 alpha = A dx^2 + B dx dy + C dy^2 + log2 o; alpha = min(0.99, 2^that);
-// skip alpha < 1/255; stop before T would drop below 1e-4.
+// alpha = min(0.99, 2^log2_alpha); skip alpha < 1/255 (tested first on
+// log2 alpha, then on alpha itself); stop before T would drop below 1e-4.
 __device__ __forceinline__ bool blend(Acc& a, float px, float py, const float4& q0,
                                       const float4& q1, float b) {
-    const float dx = px - q0.x, dy = py - q0.y;
-    const float l2 = fmaf(q0.z * dx, dx, fmaf(q0.w * dx, dy, fmaf(q1.x * dy, dy, q1.y)));
-    const float alpha = fminf(0.99f, exp2f(l2));
+    const float l2 = log2_alpha(px, py, q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
+    if (l2 < kLog2MinAlpha) return true;
+    const float alpha = fminf(0.99f, ex2_approx(l2));
     if (alpha < (1.0f / 255.0f)) return true;
     const float Tn = a.T * (1.f - alpha);
     if (Tn < 1e-4f) return false;
@@ -57,21 +94,149 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
     }
 }
 
+// Transposed evaluation of up to 32 records (indices wbuf[0..n)) for the
+// warp's rays: each lane holds one record, tests it against every ray that is
+// still compositing (ray position by shuffle, one ballot per ray), and keeps
+// the mask of records that may reach alpha >= 1/255 for its own ray.  Then
+// every lane blends its own candidates in list order.  Finished rays drop out
+// of the ray loop, so they cost nothing.
+__device__ __forceinline__ void warp_group(Acc& a, bool& done, uint32_t& evals, float px, float py,
+                                           const int* wbuf, int n, const float4* s0,
+                                           const float4* s1, const float4* s2) {
+    const int lane = threadIdx.x & 31;
+    const int j = lane < n ? wbuf[lane] : -1;
+    float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f, L = -1e30f;
+    if (j >= 0) {
+        const float4 q0 = s0[j];
+        const float2 q1 = *reinterpret_cast<const float2*>(s1 + j);
+        u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y;
+    }
+    unsigned act = __ballot_sync(0xffffffffu, !done);
+    unsigned mine = 0;
+    while (act) {
+        const int r = __ffs(act) - 1;
+        act &= act - 1;
+        const float rx = __shfl_sync(0xffffffffu, px, r);
+        const float ry = __shfl_sync(0xffffffffu, py, r);
+        const bool pass = log2_alpha(rx, ry, u, v, A, B, C, L) >= kLog2MinAlpha;
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (lane == r) mine = m;
+    }
+    if (!done) evals += uint32_t(n);
+    while (mine && !done) {
+        const int sidx = __ffs(mine) - 1;
+        mine &= mine - 1;
+        const int jj = wbuf[sidx];
+        if (!blend(a, px, py, s0[jj], s1[jj], s2[jj].x)) done = true;
+    }
+}
+
+// Composites a shared-memory batch of nb records for this lane's ray.  Records
+// whose pixel box misses the warp's box [bx0,bx1] x [by0,by1] are dropped; the
+// rest are compacted, in list order, into the warp's buffer (64 ints) and
+// evaluated 32 at a time.
+__device__ __forceinline__ void warp_batch(Acc& a, bool& done, uint32_t& evals, float px, float py,
+                                           int bx0, int bx1, int by0, int by1, const float4* s0,
+                                           const float4* s1, const float4* s2, int nb, int* wbuf) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1;
+    int cnt = 0;
+    for (int j0 = 0; j0 < nb; j0 += 32) {
+        if (__all_sync(0xffffffffu, done)) return;
+        bool hit = false;
+        if (j0 + lane < nb) {
+            const float4 q2 = s2[j0 + lane];
+            const uint32_t rc = __float_as_uint(q2.z), rr = __float_as_uint(q2.w);
+            hit = int(rc & 0xFFFFu) <= bx1 && int(rc >> 16) >= bx0 && int(rr & 0xFFFFu) <= by1 &&
+                  int(rr >> 16) >= by0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) wbuf[cnt + __popc(m & lt)] = j0 + lane;
+        cnt += __popc(m);
+        __syncwarp();
+        if (cnt >= 32) {
+            warp_group(a, done, evals, px, py, wbuf, 32, s0, s1, s2);
+            __syncwarp();
+            const int rest = cnt - 32;
+            const int t = lane < rest ? wbuf[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) wbuf[lane] = t;
+            __syncwarp();
+            cnt = rest;
+        }
+    }
+    if (cnt > 0 && !__all_sync(0xffffffffu, done)) {
+        warp_group(a, done, evals, px, py, wbuf, cnt, s0, s1, s2);
+    }
+    __syncwarp();
+}
+
+// Direct evaluation: every lane walks the culled records in list order and
+// evaluates each one for its own ray (record fields by shared-memory broadcast).
+__device__ __forceinline__ void warp_batch_direct(Acc& a, bool& done, uint32_t& evals, float px,
+                                                  float py, int bx0, int bx1, int by0, int by1,
+                                                  const float4* s0, const float4* s1,
+                                                  const float4* s2, int nb) {
+    const int lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < nb; j0 += 32) {
+        if (__all_sync(0xffffffffu, done)) return;
+        bool hit = false;
+        if (j0 + lane < nb) {
+            const float4 q2 = s2[j0 + lane];
+            const uint32_t rc = __float_as_uint(q2.z), rr = __float_as_uint(q2.w);
+            hit = int(rc & 0xFFFFu) <= bx1 && int(rc >> 16) >= bx0 && int(rr & 0xFFFFu) <= by1 &&
+                  int(rr >> 16) >= by0;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        while (m) {
+            const int j = j0 + __ffs(m) - 1;
+            m &= m - 1;
+            if (!done) {
+                ++evals;
+                if (!blend(a, px, py, s0[j], s1[j], s2[j].x)) done = true;
+            }
+        }
+    }
+}
+
+template <bool TRANSPOSED>
+__device__ __forceinline__ void eval_batch(Acc& a, bool& done, uint32_t& evals, float px, float py,
+                                           int bx0, int bx1, int by0, int by1, const float4* s0,
+                                           const float4* s1, const float4* s2, int nb, int* wbuf) {
+    if (TRANSPOSED)
+        warp_batch(a, done, evals, px, py, bx0, bx1, by0, by1, s0, s1, s2, nb, wbuf);
+    else
+        warp_batch_direct(a, done, evals, px, py, bx0, bx1, by0, by1, s0, s1, s2, nb);
+}
+
+__device__ __forceinline__ void warp_box(bool active, int col, int row, int& bx0, int& bx1, int& by0,
+                                         int& by1) {
+    bx0 = __reduce_min_sync(0xffffffffu, active ? col : INT_MAX);
+    bx1 = __reduce_max_sync(0xffffffffu, active ? col : INT_MIN);
+    by0 = __reduce_min_sync(0xffffffffu, active ? row : INT_MAX);
+    by1 = __reduce_max_sync(0xffffffffu, active ? row : INT_MIN);
+}
+
 __global__ void __launch_bounds__(kRayThreads)
 composite_rays_kernel(CompositeParams p, const int4* __restrict__ work,
-                      const int4* __restrict__ grouped, const uint2* __restrict__ ranges,
+                      const int2* __restrict__ grouped, const uint2* __restrict__ ranges,
                       const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
-                      float* __restrict__ out, unsigned long long* __restrict__ pairs) {
+                      float* __restrict__ raycol, unsigned long long* __restrict__ pairs) {
     __shared__ float4 s0[kRayThreads];
     __shared__ float4 s1[kRayThreads];
-    __shared__ float s2[kRayThreads];
+    __shared__ float4 s2[kRayThreads];
+    __shared__ int wbuf_all[kRayThreads / 32][64];
+    int* wbuf = wbuf_all[threadIdx.x >> 5];
     const int4 wi = work[blockIdx.x];
     const int v = wi.x / p.ntiles;
     const int rid = wi.y + int(threadIdx.x);
     const bool active = rid < wi.z;
-    const int4 ray = active ? grouped[rid] : make_int4(0, -1, -1, -1);
-    const float px = float(uint32_t(ray.x) & 0xFFFFu) - p.half_w;
-    const float py = float(uint32_t(ray.x) >> 16) - p.half_h;
+    const int2 ray = active ? grouped[rid] : make_int2(0, -1);
+    const int col = int(uint32_t(ray.x) & 0xFFFFu), row = int(uint32_t(ray.x) >> 16);
+    const float px = float(col) - p.half_w;
+    const float py = float(row) - p.half_h;
+    int bx0, bx1, by0, by1;
+    warp_box(active, col, row, bx0, bx1, by0, by1);
     const uint2 rg = ranges[wi.x];
     const int64_t vbase = int64_t(v) * p.n;
     Acc a{1.f, 0.f, 0.f, 0.f, 0u};
@@ -83,28 +248,19 @@ composite_rays_kernel(CompositeParams p, const int4* __restrict__ work,
             const int64_t e = vbase + vals[i];
             s0[threadIdx.x] = rec[3 * e];
             s1[threadIdx.x] = rec[3 * e + 1];
-            s2[threadIdx.x] = rec[3 * e + 2].x;
+            s2[threadIdx.x] = rec[3 * e + 2];
         }
         __syncthreads();
         const int nb = int(rg.y - b < kRayThreads ? rg.y - b : kRayThreads);
-        if (!done) {
-            int j = 0;
-            for (; j < nb; ++j) {
-                if (!blend(a, px, py, s0[j], s1[j], s2[j])) {
-                    done = true;
-                    ++j;
-                    break;
-                }
-            }
-            evals += uint32_t(j);
-        }
+        warp_batch_direct(a, done, evals, px, py, bx0, bx1, by0, by1, s0, s1, s2, nb);
         if (__syncthreads_count(done) == int(blockDim.x)) break;
     }
     if (pairs) count_pairs(pairs, evals, a.blended);
     if (active) {
-        if (ray.y >= 0) out[ray.y] = a.c0;
-        if (ray.z >= 0) out[ray.z] = a.c1;
-        if (ray.w >= 0) out[ray.w] = a.c2;
+        float* o = raycol + 3 * int64_t(ray.y);
+        o[0] = a.c0;
+        o[1] = a.c1;
+        o[2] = a.c2;
     }
 }
 
@@ -116,7 +272,8 @@ __global__ void composite_full_kernel(CompositeParams p, const uint2* __restrict
     const int nthr = blockDim.x;
     float4* s0 = sm;
     float4* s1 = sm + nthr;
-    float* s2 = reinterpret_cast<float*>(sm + 2 * nthr);
+    float4* s2 = sm + 2 * nthr;
+    int* wbuf = reinterpret_cast<int*>(sm + 3 * nthr) + 64 * (threadIdx.x >> 5);
     const int group = blockIdx.x;
     const int v = group / p.ntiles;
     const int tile = group - v * p.ntiles;
@@ -125,6 +282,8 @@ __global__ void composite_full_kernel(CompositeParams p, const uint2* __restrict
     const int row = ty * p.tile_h + int(threadIdx.x) / p.tile_w;
     const bool inside = col < p.width && row < p.height;
     const float px = float(col) - p.half_w, py = float(row) - p.half_h;
+    int bx0, bx1, by0, by1;
+    warp_box(inside, col, row, bx0, bx1, by0, by1);
     const uint2 rg = ranges[group];
     const int64_t vbase = int64_t(v) * p.n;
     Acc a{1.f, 0.f, 0.f, 0.f, 0u};
@@ -136,21 +295,11 @@ __global__ void composite_full_kernel(CompositeParams p, const uint2* __restrict
             const int64_t e = vbase + vals[i];
             s0[threadIdx.x] = rec[3 * e];
             s1[threadIdx.x] = rec[3 * e + 1];
-            s2[threadIdx.x] = rec[3 * e + 2].x;
+            s2[threadIdx.x] = rec[3 * e + 2];
         }
         __syncthreads();
         const int nb = int(rg.y - b < uint32_t(nthr) ? rg.y - b : uint32_t(nthr));
-        if (!done) {
-            int j = 0;
-            for (; j < nb; ++j) {
-                if (!blend(a, px, py, s0[j], s1[j], s2[j])) {
-                    done = true;
-                    ++j;
-                    break;
-                }
-            }
-            evals += uint32_t(j);
-        }
+        warp_batch_direct(a, done, evals, px, py, bx0, bx1, by0, by1, s0, s1, s2, nb);
         if (__syncthreads_count(done) == nthr) break;
     }
     if (pairs) count_pairs(pairs, evals, a.blended);
@@ -160,6 +309,618 @@ __global__ void composite_full_kernel(CompositeParams p, const uint2* __restrict
         o[1] = a.c1;
         o[2] = a.c2;
     }
+}
+
+// ---------------------------------------------------------- binned path ---
+// Ascending bitonic sort of P (a power of two) unique keys in shared memory.
+__device__ void bitonic_sort(unsigned long long* s, int P) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+                const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                const int hi = lo + j;
+                const bool up = (lo & k) == 0;
+                const unsigned long long a = s[lo], b = s[hi];
+                if ((a > b) == up) {
+                    s[lo] = b;
+                    s[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Exclusive scan, in place, of n <= blockDim.x * 64 counters in shared memory.
+__device__ void block_scan_counts(uint32_t* c, int n) {
+    __shared__ uint32_t s_w[32];
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int per = (n + nthr - 1) / nthr;
+    const int b0 = tid * per;
+    uint32_t sum = 0;
+    for (int i = b0; i < b0 + per && i < n; ++i) sum += c[i];
+    const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t x = lane < nw ? s_w[lane] : 0;
+        uint32_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < nw) s_w[lane] = xi - x;
+    }
+    __syncthreads();
+    uint32_t run = s_w[wid] + inc - sum;
+    for (int i = b0; i < b0 + per && i < n; ++i) {
+        const uint32_t v = c[i];
+        c[i] = run;
+        run += v;
+    }
+    __syncthreads();
+}
+
+constexpr int kBucketSortLimit = 64;  // largest bucket sorted by one thread
+
+// Sorts the group's keys (depth << 32 | Gaussian, all distinct) into sk:
+// a counting sort on the depth bucket floor((d - dmin) NB / (dmax - dmin + 1))
+// (monotone in d), then an insertion sort inside every bucket.  If a bucket
+// holds more than kBucketSortLimit keys (many equal depths), the whole list
+// is bitonic-sorted instead.  KPT > 0: the block holds the keys in registers
+// (len <= KPT * blockDim.x, one coalesced load); KPT == 0: the keys are read
+// from global memory once per pass.  sk holds next_pow2(len) keys; cnt holds
+// cap + 2 counters, cap >= len being the class capacity (a power of two).
+template <int KPT>
+__device__ void block_sort(const unsigned long long* __restrict__ keys, uint32_t start, int len,
+                           int cap, unsigned long long* sk, uint32_t* cnt) {
+    __shared__ uint32_t s_lo, s_hi, s_big;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    constexpr int R = KPT > 0 ? KPT : 1;
+    unsigned long long kr[R];
+    if (tid == 0) {
+        s_lo = 0xFFFFFFFFu;
+        s_hi = 0u;
+        s_big = 0u;
+    }
+    __syncthreads();
+    if (len <= 1) {
+        if (len == 1 && tid == 0) sk[0] = keys[start];
+        __syncthreads();
+        return;
+    }
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    if (KPT > 0) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int i = j * nthr + tid;
+            kr[j] = i < len ? keys[start + i] : ~0ull;
+            if (i < len) {
+                lo = min(lo, uint32_t(kr[j] >> 32));
+                hi = max(hi, uint32_t(kr[j] >> 32));
+            }
+        }
+    } else {
+        for (int i = tid; i < len; i += nthr) {
+            const uint32_t d = uint32_t(keys[start + i] >> 32);
+            lo = min(lo, d);
+            hi = max(hi, d);
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((tid & 31) == 0) {
+        atomicMin(&s_lo, lo);
+        atomicMax(&s_hi, hi);
+    }
+    int NB = 1;
+    while (NB < len) NB <<= 1;
+    NB = NB >> 1;
+    if (NB > cap / 2) NB = cap / 2;
+    if (NB < 1) NB = 1;
+    uint32_t* bstart = cnt;               // NB + 1
+    uint32_t* bfill = cnt + cap / 2 + 1;  // NB
+    for (int i = tid; i <= NB; i += nthr) bstart[i] = 0u;
+    for (int i = tid; i < NB; i += nthr) bfill[i] = 0u;
+    __syncthreads();
+    const uint32_t dmin = s_lo;
+    const float scale = float(NB) / (float(s_hi - s_lo) + 1.0f);
+    auto bucket = [&](unsigned long long k) {
+        return min(NB - 1, int(float(uint32_t(k >> 32) - dmin) * scale));
+    };
+    if (KPT > 0) {
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if (j * nthr + tid < len) atomicAdd(&bstart[bucket(kr[j])], 1u);
+    } else {
+        for (int i = tid; i < len; i += nthr) atomicAdd(&bstart[bucket(keys[start + i])], 1u);
+    }
+    __syncthreads();
+    block_scan_counts(bstart, NB);
+    if (tid == 0) bstart[NB] = uint32_t(len);
+    __syncthreads();
+    if (KPT > 0) {
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if (j * nthr + tid < len) {
+                const int b = bucket(kr[j]);
+                sk[bstart[b] + atomicAdd(&bfill[b], 1u)] = kr[j];
+            }
+    } else {
+        for (int i = tid; i < len; i += nthr) {
+            const unsigned long long k = keys[start + i];
+            const int b = bucket(k);
+            sk[bstart[b] + atomicAdd(&bfill[b], 1u)] = k;
+        }
+    }
+    __syncthreads();
+    for (int b = tid; b < NB; b += nthr)
+        if (bstart[b + 1] - bstart[b] > uint32_t(kBucketSortLimit)) s_big = 1u;
+    __syncthreads();
+    if (s_big) {
+        int P = 1;
+        while (P < len) P <<= 1;
+        for (int i = len + tid; i < P; i += nthr) sk[i] = ~0ull;
+        __syncthreads();
+        bitonic_sort(sk, P);
+    } else {
+        for (int b = tid; b < NB; b += nthr) {
+            const int b0 = int(bstart[b]), b1 = int(bstart[b + 1]);
+            for (int i = b0 + 1; i < b1; ++i) {
+                const unsigned long long k = sk[i];
+                int j = i - 1;
+                while (j >= b0 && sk[j] > k) {
+                    sk[j + 1] = sk[j];
+                    --j;
+                }
+                sk[j + 1] = k;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Streams the sorted list's records through two shared-memory batches of
+// blockDim.x records (cp.async prefetch of batch b+1 while batch b is
+// blended) until every ray of the block is finished.
+template <bool TRANSPOSED>
+__device__ __forceinline__ void stream_list(const unsigned long long* sk, int len, int64_t vbase,
+                                            const float4* __restrict__ rec, float4* buf, int* wbuf,
+                                            Acc& a, bool& done, uint32_t& evals, float px, float py,
+                                            int bx0, int bx1, int by0, int by1) {
+    const int nthr = blockDim.x, t = threadIdx.x;
+    // single shared batch: load, barrier, blend, vote
+    for (int b = 0; b < len; b += nthr) {
+        const int i = b + t;
+        if (i < len) {
+            const int64_t e = vbase + uint32_t(sk[i]);
+            buf[t] = rec[3 * e];
+            buf[nthr + t] = rec[3 * e + 1];
+            buf[2 * nthr + t] = rec[3 * e + 2];
+        }
+        __syncthreads();
+        const int nb = len - b < nthr ? len - b : nthr;
+        eval_batch<TRANSPOSED>(a, done, evals, px, py, bx0, bx1, by0, by1, buf, buf + nthr,
+                               buf + 2 * nthr, nb, wbuf);
+        if (__syncthreads_count(done) == nthr) break;
+    }
+}
+
+// Variant of stream_list with two batches: cp.async fetches batch b+1 while
+// batch b is blended.
+template <bool TRANSPOSED>
+__device__ __forceinline__ void stream_list_db(const unsigned long long* sk, int len, int64_t vbase,
+                                               const float4* __restrict__ rec, float4* buf,
+                                               int* wbuf, Acc& a, bool& done, uint32_t& evals,
+                                               float px, float py, int bx0, int bx1, int by0,
+                                               int by1) {
+    const int nthr = blockDim.x, t = threadIdx.x;
+    const int nbatch = (len + nthr - 1) / nthr;
+    if (nbatch == 0) return;
+    auto issue = [&](int b) {
+        float4* dst = buf + (b & 1) * 3 * nthr;
+        const int i = b * nthr + t;
+        if (i < len) {
+            const int64_t e = vbase + uint32_t(sk[i]);
+            cp_async16(dst + t, rec + 3 * e);
+            cp_async16(dst + nthr + t, rec + 3 * e + 1);
+            cp_async16(dst + 2 * nthr + t, rec + 3 * e + 2);
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    for (int b = 0; b < nbatch; ++b) {
+        if (b + 1 < nbatch) issue(b + 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const float4* cur = buf + (b & 1) * 3 * nthr;
+        const int nb = len - b * nthr < nthr ? len - b * nthr : nthr;
+        eval_batch<TRANSPOSED>(a, done, evals, px, py, bx0, bx1, by0, by1, cur, cur + nthr,
+                               cur + 2 * nthr, nb, wbuf);
+        if (__syncthreads_count(done) == nthr) break;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+}
+
+// Shared memory of a binned block: keys (cap), bucket counters (cap + 2),
+// a record batch (3 x nthr float4), compaction buffers (64 ints per warp).
+struct BinnedSmem {
+    unsigned long long* sk;
+    uint32_t* cnt;
+    float4* buf;
+    int* wbuf;
+};
+
+__device__ __forceinline__ BinnedSmem carve_binned(unsigned char* base, int cap, int nthr) {
+    BinnedSmem m;
+    m.sk = reinterpret_cast<unsigned long long*>(base);
+    m.cnt = reinterpret_cast<uint32_t*>(base + 8 * size_t(cap));
+    const size_t off = (8 * size_t(cap) + 4 * size_t(cap + 2) + 15) & ~size_t(15);
+    m.buf = reinterpret_cast<float4*>(base + off);
+    m.wbuf = reinterpret_cast<int*>(m.buf + 3 * nthr) + 64 * (threadIdx.x >> 5);
+    return m;
+}
+
+template <bool TRANSPOSED, int KPT>
+__global__ void __launch_bounds__(kBinnedThreads)
+composite_rays_binned_kernel(CompositeParams p, const int4* __restrict__ gwork,
+                             const int32_t* __restrict__ list, int cap,
+                             const int2* __restrict__ grouped, const uint32_t* __restrict__ gstart,
+                             const unsigned long long* __restrict__ keys,
+                             const float4* __restrict__ rec, float* __restrict__ raycol,
+                             unsigned long long* __restrict__ pairs) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    const int nthr = blockDim.x;
+    const BinnedSmem S = carve_binned(smb, cap, nthr);
+    const int4 wi = gwork[list[blockIdx.x]];
+    const int v = wi.x / p.ntiles;
+    const uint32_t start = gstart[wi.x];
+    const int len = int(gstart[wi.x + 1] - start);
+    block_sort<KPT>(keys, start, len, cap, S.sk, S.cnt);
+    const int64_t vbase = int64_t(v) * p.n;
+    uint32_t evals = 0, blended = 0;
+    for (int r0 = wi.y; r0 < wi.z; r0 += nthr) {
+        const int rid = r0 + int(threadIdx.x);
+        const bool active = rid < wi.z;
+        const int2 ray = active ? grouped[rid] : make_int2(0, -1);
+        const int col = int(uint32_t(ray.x) & 0xFFFFu), row = int(uint32_t(ray.x) >> 16);
+        const float px = float(col) - p.half_w, py = float(row) - p.half_h;
+        int bx0, bx1, by0, by1;
+        warp_box(active, col, row, bx0, bx1, by0, by1);
+        Acc a{1.f, 0.f, 0.f, 0.f, 0u};
+        bool done = !active;
+        stream_list<TRANSPOSED>(S.sk, len, vbase, rec, S.buf, S.wbuf, a, done, evals, px, py, bx0,
+                                bx1, by0, by1);
+        if (active) {
+            float* o = raycol + 3 * int64_t(ray.y);
+            o[0] = a.c0;
+            o[1] = a.c1;
+            o[2] = a.c2;
+        }
+        blended += a.blended;
+    }
+    if (pairs) count_pairs(pairs, evals, blended);
+}
+
+template <bool TRANSPOSED, int KPT>
+__global__ void __launch_bounds__(1024)
+composite_full_binned_kernel(CompositeParams p, const int32_t* __restrict__ list, int cap,
+                             const uint32_t* __restrict__ gstart,
+                             const unsigned long long* __restrict__ keys,
+                             const float4* __restrict__ rec, float* __restrict__ Mm,
+                             unsigned long long* __restrict__ pairs) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    const int nthr = blockDim.x;
+    const BinnedSmem S = carve_binned(smb, cap, nthr);
+    const int group = list[blockIdx.x];
+    const int v = group / p.ntiles;
+    const int tile = group - v * p.ntiles;
+    const int tx = tile % p.ntx, ty = tile / p.ntx;
+    const int col = tx * p.tile_w + int(threadIdx.x) % p.tile_w;
+    const int row = ty * p.tile_h + int(threadIdx.x) / p.tile_w;
+    const bool inside = col < p.width && row < p.height;
+    const float px = float(col) - p.half_w, py = float(row) - p.half_h;
+    const uint32_t start = gstart[group];
+    const int len = int(gstart[group + 1] - start);
+    block_sort<KPT>(keys, start, len, cap, S.sk, S.cnt);
+    int bx0, bx1, by0, by1;
+    warp_box(inside, col, row, bx0, bx1, by0, by1);
+    const int64_t vbase = int64_t(v) * p.n;
+    Acc a{1.f, 0.f, 0.f, 0.f, 0u};
+    uint32_t evals = 0;
+    bool done = !inside;
+    stream_list<TRANSPOSED>(S.sk, len, vbase, rec, S.buf, S.wbuf, a, done, evals, px, py, bx0, bx1,
+                            by0, by1);
+    if (pairs) count_pairs(pairs, evals, a.blended);
+    if (inside) {
+        float* o = Mm + ((int64_t(v) * p.height + row) * p.width + col) * 3;
+        o[0] = a.c0;
+        o[1] = a.c1;
+        o[2] = a.c2;
+    }
+}
+
+// ------------------------------------------------- one warp per tile ----
+// DirectL tiles hold few rays (tens) and a few hundred Gaussians, so each
+// warp owns one (view, tile) group: it sorts the group's keys in its own
+// shared memory (warp-level bucket sort), streams the records in batches of
+// 32 with cp.async double buffering, and evaluates them transposed against
+// its rays.  Only __syncwarp is used, so warps never wait on each other.
+constexpr int kWarpsPerBlock = 4;
+
+template <int CAP>
+struct WarpSmem {
+    static constexpr int kBuckets = CAP / 2;
+    unsigned long long sk[CAP];
+    uint32_t bstart[kBuckets + 1];
+    uint32_t bfill[kBuckets];
+    float4 buf[2][3][32];
+};
+
+// Warp-level version of block_sort (len <= CAP).  Lists of up to 512 keys
+// are held in registers; longer ones are re-read from global memory per pass.
+template <int CAP>
+__device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t start, int len,
+                          WarpSmem<CAP>& W) {
+    const int lane = threadIdx.x & 31;
+    constexpr int kWarpBuckets = WarpSmem<CAP>::kBuckets;
+    constexpr int KPL = (CAP <= 512 ? CAP : 512) / 32;
+    unsigned long long kr[KPL];
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    const bool in_regs = len <= KPL * 32;
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+        const int i = j * 32 + lane;
+        kr[j] = i < len ? keys[start + i] : ~0ull;
+        if (i < len) {
+            lo = min(lo, uint32_t(kr[j] >> 32));
+            hi = max(hi, uint32_t(kr[j] >> 32));
+        }
+    }
+    for (int i = KPL * 32 + lane; i < len; i += 32) {
+        lo = min(lo, uint32_t(keys[start + i] >> 32));
+        hi = max(hi, uint32_t(keys[start + i] >> 32));
+    }
+    if (len <= 1) {
+        if (len == 1 && lane == 0) W.sk[0] = kr[0];
+        __syncwarp();
+        return;
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    int NB = 1;
+    while (NB < len) NB <<= 1;
+    NB >>= 1;
+    if (NB > kWarpBuckets) NB = kWarpBuckets;
+    for (int b = lane; b <= NB; b += 32) W.bstart[b] = 0u;
+    for (int b = lane; b < NB; b += 32) W.bfill[b] = 0u;
+    __syncwarp();
+    const float scale = float(NB) / (float(hi - lo) + 1.0f);
+    auto bucket = [&](unsigned long long k) {
+        return min(NB - 1, int(float(uint32_t(k >> 32) - lo) * scale));
+    };
+    if (in_regs) {
+#pragma unroll
+        for (int j = 0; j < KPL; ++j)
+            if (j * 32 + lane < len) atomicAdd(&W.bstart[bucket(kr[j])], 1u);
+    } else {
+        for (int i = lane; i < len; i += 32) atomicAdd(&W.bstart[bucket(keys[start + i])], 1u);
+    }
+    __syncwarp();
+    {  // exclusive scan of bstart[0..NB)
+        const int per = (NB + 31) / 32, b0 = lane * per;
+        uint32_t sum = 0;
+        for (int b = b0; b < b0 + per && b < NB; ++b) sum += W.bstart[b];
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        uint32_t run = inc - sum;
+        __syncwarp();
+        for (int b = b0; b < b0 + per && b < NB; ++b) {
+            const uint32_t c = W.bstart[b];
+            W.bstart[b] = run;
+            run += c;
+        }
+        if (lane == 0) W.bstart[NB] = uint32_t(len);
+    }
+    __syncwarp();
+    if (in_regs) {
+#pragma unroll
+        for (int j = 0; j < KPL; ++j)
+            if (j * 32 + lane < len) {
+                const int b = bucket(kr[j]);
+                W.sk[W.bstart[b] + atomicAdd(&W.bfill[b], 1u)] = kr[j];
+            }
+    } else {
+        for (int i = lane; i < len; i += 32) {
+            const unsigned long long k = keys[start + i];
+            const int b = bucket(k);
+            W.sk[W.bstart[b] + atomicAdd(&W.bfill[b], 1u)] = k;
+        }
+    }
+    __syncwarp();
+    bool big = false;
+    for (int b = lane; b < NB; b += 32)
+        big |= W.bstart[b + 1] - W.bstart[b] > uint32_t(kBucketSortLimit);
+    if (__any_sync(0xffffffffu, big)) {
+        int P = 1;
+        while (P < len) P <<= 1;
+        for (int i = len + lane; i < P; i += 32) W.sk[i] = ~0ull;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = lane; i < (P >> 1); i += 32) {
+                    const int a = ((i & ~(jj - 1)) << 1) | (i & (jj - 1));
+                    const int c = a + jj;
+                    const bool up = (a & k) == 0;
+                    const unsigned long long x = W.sk[a], y = W.sk[c];
+                    if ((x > y) == up) {
+                        W.sk[a] = y;
+                        W.sk[c] = x;
+                    }
+                }
+                __syncwarp();
+            }
+    } else {
+        for (int b = lane; b < NB; b += 32) {
+            const int b0 = int(W.bstart[b]), b1 = int(W.bstart[b + 1]);
+            for (int i = b0 + 1; i < b1; ++i) {
+                const unsigned long long k = W.sk[i];
+                int j = i - 1;
+                while (j >= b0 && W.sk[j] > k) {
+                    W.sk[j + 1] = W.sk[j];
+                    --j;
+                }
+                W.sk[j + 1] = k;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Streams the warp's sorted list in batches of 32 records (cp.async double
+// buffering) and composites them, transposed, for the warp's rays.
+template <int CAP>
+__device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t vbase,
+                                            const float4* __restrict__ rec, Acc& a, bool& done,
+                                            uint32_t& evals, float px, float py, int bx0, int bx1,
+                                            int by0, int by1) {
+    const int lane = threadIdx.x & 31;
+    const int nbatch = (len + 31) / 32;
+    if (nbatch == 0) return;
+    auto issue = [&](int b) {
+        const int i = b * 32 + lane;
+        if (i < len) {
+            const int64_t e = vbase + uint32_t(W.sk[i]);
+            cp_async16(&W.buf[b & 1][0][lane], rec + 3 * e);
+            cp_async16(&W.buf[b & 1][1][lane], rec + 3 * e + 1);
+            cp_async16(&W.buf[b & 1][2][lane], rec + 3 * e + 2);
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    for (int b = 0; b < nbatch; ++b) {
+        if (b + 1 < nbatch) issue(b + 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        const float4* c0 = W.buf[b & 1][0];
+        const float4* c1 = W.buf[b & 1][1];
+        const float4* c2 = W.buf[b & 1][2];
+        const int n = len - b * 32 < 32 ? len - b * 32 : 32;
+        bool hit = false;
+        float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f, L = -1e30f;
+        if (lane < n) {
+            const float4 q2 = c2[lane];
+            const uint32_t rc = __float_as_uint(q2.z), rr = __float_as_uint(q2.w);
+            hit = int(rc & 0xFFFFu) <= bx1 && int(rc >> 16) >= bx0 && int(rr & 0xFFFFu) <= by1 &&
+                  int(rr >> 16) >= by0;
+            if (hit) {
+                const float4 q0 = c0[lane];
+                const float2 q1 = *reinterpret_cast<const float2*>(c1 + lane);
+                u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y;
+            }
+        }
+        if (__any_sync(0xffffffffu, hit)) {
+            unsigned act = __ballot_sync(0xffffffffu, !done);
+            unsigned mine = 0;
+            while (act) {
+                const int r = __ffs(act) - 1;
+                act &= act - 1;
+                const float rx = __shfl_sync(0xffffffffu, px, r);
+                const float ry = __shfl_sync(0xffffffffu, py, r);
+                const bool pass = log2_alpha(rx, ry, u, v, A, B, C, L) >= kLog2MinAlpha;
+                const unsigned m = __ballot_sync(0xffffffffu, pass);
+                if (lane == r) mine = m;
+            }
+            if (!done) evals += uint32_t(n);
+            while (mine && !done) {
+                const int sidx = __ffs(mine) - 1;
+                mine &= mine - 1;
+                if (!blend(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
+            }
+        }
+        __syncwarp();
+        if (__all_sync(0xffffffffu, done)) break;
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ gwork,
+                           const int32_t* __restrict__ list, int64_t n_list,
+                           const int2* __restrict__ grouped, const uint32_t* __restrict__ gstart,
+                           const unsigned long long* __restrict__ keys,
+                           const float4* __restrict__ rec, float* __restrict__ raycol,
+                           unsigned long long* __restrict__ pairs) {
+    extern __shared__ __align__(16) unsigned char wsm_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP>& W = reinterpret_cast<WarpSmem<CAP>*>(wsm_raw)[warp];
+    const int64_t item = int64_t(blockIdx.x) * kWarpsPerBlock + warp;
+    uint32_t evals = 0, blended = 0;
+    if (item < n_list) {
+        const int4 wi = gwork[list[item]];
+        const int v = wi.x / p.ntiles;
+        const uint32_t start = gstart[wi.x];
+        const int len = int(gstart[wi.x + 1] - start);
+        warp_sort(keys, start, len, W);
+        const int64_t vbase = int64_t(v) * p.n;
+        for (int r0 = wi.y; r0 < wi.z; r0 += 32) {
+            const int rid = r0 + lane;
+            const bool active = rid < wi.z;
+            const int2 ray = active ? grouped[rid] : make_int2(0, -1);
+            const int col = int(uint32_t(ray.x) & 0xFFFFu), row = int(uint32_t(ray.x) >> 16);
+            const float px = float(col) - p.half_w, py = float(row) - p.half_h;
+            int bx0, bx1, by0, by1;
+            warp_box(active, col, row, bx0, bx1, by0, by1);
+            Acc a{1.f, 0.f, 0.f, 0.f, 0u};
+            bool done = !active;
+            warp_stream(W, len, vbase, rec, a, done, evals, px, py, bx0, bx1, by0, by1);
+            if (active) {
+                float* o = raycol + 3 * int64_t(ray.y);
+                o[0] = a.c0;
+                o[1] = a.c1;
+                o[2] = a.c2;
+            }
+            blended += a.blended;
+        }
+    }
+    if (pairs) count_pairs(pairs, evals, blended);
+}
+
+__global__ void partition_kernel(const int4* __restrict__ gwork, int64_t n_work,
+                                 const uint32_t* __restrict__ gstart, uint32_t small_cap,
+                                 int32_t* __restrict__ small_list, int32_t* __restrict__ large_list,
+                                 uint32_t* __restrict__ meta) {
+    for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < n_work;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t g = gwork ? gwork[w].x : w;
+        const uint32_t len = gstart[g + 1] - gstart[g];
+        if (len <= small_cap) small_list[atomicAdd(meta, 1u)] = int32_t(w);
+        else large_list[atomicAdd(meta + 1, 1u)] = int32_t(w);
+        atomicMax(meta + 2, len);
+    }
+}
+
+__global__ void reorder_kernel(const uint32_t* __restrict__ ray_of, const float* __restrict__ raycol,
+                               int64_t n, float* __restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = raycol[3 * int64_t(ray_of[i]) + (i % 3)];
 }
 
 // M_e[x, y, k] = M_m[V(x, 3y + k), x, y, k] (Alg. 1, native resolution).
@@ -179,12 +940,12 @@ __global__ void interweave_kernel(int32_t w, int32_t h, const uint16_t* __restri
 }  // namespace
 
 cudaError_t launch_composite_rays(const CompositeParams& p, const int4* work, int64_t n_work,
-                                  const int4* grouped, const uint2* ranges, const uint32_t* vals,
-                                  const float4* rec, float* out, unsigned long long* pairs,
+                                  const int2* grouped, const uint2* ranges, const uint32_t* vals,
+                                  const float4* rec, float* raycol, unsigned long long* pairs,
                                   cudaStream_t s) {
     if (n_work <= 0) return cudaSuccess;
     composite_rays_kernel<<<unsigned(n_work), kRayThreads, 0, s>>>(p, work, grouped, ranges, vals,
-                                                                   rec, out, pairs);
+                                                                   rec, raycol, pairs);
     return cudaGetLastError();
 }
 
@@ -192,9 +953,100 @@ cudaError_t launch_composite_full(const CompositeParams& p, int32_t nv, const ui
                                   const uint32_t* vals, const float4* rec, float* Mm,
                                   unsigned long long* pairs, cudaStream_t s) {
     const int nthr = p.tile_w * p.tile_h;
-    const size_t smem = size_t(nthr) * (2 * sizeof(float4) + sizeof(float));
+    const size_t smem = size_t(nthr) * 3 * sizeof(float4) + size_t(nthr / 32) * 64 * sizeof(int);
     const int64_t blocks = int64_t(nv) * p.ntiles;
     composite_full_kernel<<<unsigned(blocks), nthr, smem, s>>>(p, ranges, vals, rec, Mm, pairs);
+    return cudaGetLastError();
+}
+
+size_t binned_smem_bytes(int cap, int nthr) {
+    const size_t off = (8 * size_t(cap) + 4 * size_t(cap + 2) + 15) & ~size_t(15);
+    return off + size_t(nthr) * 3 * sizeof(float4) + size_t(nthr / 32) * 64 * sizeof(int);
+}
+
+cudaError_t launch_composite_rays_binned(const CompositeParams& p, const int4* gwork,
+                                         const int32_t* list, int64_t n_list, int cap,
+                                         const int2* grouped, const uint32_t* gstart,
+                                         const unsigned long long* keys, const float4* rec,
+                                         float* raycol, unsigned long long* pairs, int transposed,
+                                         cudaStream_t s) {
+    if (n_list <= 0) return cudaSuccess;
+    const int nthr = kBinnedThreads;
+    const size_t smem = binned_smem_bytes(cap, nthr);
+    const bool regs = false;
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+        kernel<<<unsigned(n_list), nthr, smem, s>>>(p, gwork, list, cap, grouped, gstart, keys, rec,
+                                                    raycol, pairs);
+        return cudaGetLastError();
+    };
+    if (transposed) return regs ? go(composite_rays_binned_kernel<true, 8>)
+                                : go(composite_rays_binned_kernel<true, 0>);
+    return regs ? go(composite_rays_binned_kernel<false, 8>) : go(composite_rays_binned_kernel<false, 0>);
+}
+
+cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t* list,
+                                         int64_t n_list, int cap, const uint32_t* gstart,
+                                         const unsigned long long* keys, const float4* rec,
+                                         float* Mm, unsigned long long* pairs, int transposed,
+                                         cudaStream_t s) {
+    if (n_list <= 0) return cudaSuccess;
+    const int nthr = p.tile_w * p.tile_h;
+    const size_t smem = binned_smem_bytes(cap, nthr);
+    const bool regs = false;
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+        kernel<<<unsigned(n_list), nthr, smem, s>>>(p, list, cap, gstart, keys, rec, Mm, pairs);
+        return cudaGetLastError();
+    };
+    if (transposed) return regs ? go(composite_full_binned_kernel<true, 4>)
+                                : go(composite_full_binned_kernel<true, 0>);
+    return regs ? go(composite_full_binned_kernel<false, 4>) : go(composite_full_binned_kernel<false, 0>);
+}
+
+cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* gwork,
+                                       const int32_t* list, int64_t n_list, const int2* grouped,
+                                       const uint32_t* gstart, const unsigned long long* keys,
+                                       const float4* rec, float* raycol, unsigned long long* pairs,
+                                       cudaStream_t s) {
+    if (n_list <= 0) return cudaSuccess;
+    const int64_t blocks = (n_list + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    auto go = [&](auto kernel, size_t smem) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+        kernel<<<unsigned(blocks), kWarpsPerBlock * 32, smem, s>>>(p, gwork, list, n_list, grouped,
+                                                                   gstart, keys, rec, raycol, pairs);
+        return cudaGetLastError();
+    };
+    if (cap == 1024)
+        return go(composite_rays_warp_kernel<1024>, kWarpsPerBlock * sizeof(WarpSmem<1024>));
+    return go(composite_rays_warp_kernel<512>, kWarpsPerBlock * sizeof(WarpSmem<512>));
+}
+
+cudaError_t launch_partition(const int4* gwork, int64_t n_work, const uint32_t* gstart,
+                             uint32_t small_cap, int32_t* small_list, int32_t* large_list,
+                             uint32_t* meta, cudaStream_t s) {
+    if (n_work <= 0) return cudaSuccess;
+    int64_t grid = (n_work + 255) / 256;
+    const int64_t cap = int64_t(num_sms()) * 16;
+    if (grid > cap) grid = cap;
+    partition_kernel<<<unsigned(grid), 256, 0, s>>>(gwork, n_work, gstart, small_cap, small_list,
+                                                    large_list, meta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(const uint32_t* ray_of, const float* raycol, int64_t n, float* out,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t grid = (n + 255) / 256;
+    const int64_t cap = int64_t(num_sms()) * 32;
+    if (grid > cap) grid = cap;
+    reorder_kernel<<<unsigned(grid), 256, 0, s>>>(ray_of, raycol, n, out);
     return cudaGetLastError();
 }
 

@@ -190,20 +190,25 @@ __global__ void identity_src_kernel(int32_t w, int32_t h, uint32_t* __restrict__
 
 // ------------------------------------------------------------------ a3 ---
 // A ray (v, x', y') is identified by its owner: the subpixel (x', y', k0) of
-// the source pixel with the lowest channel k0 showing view v.
+// the source pixel with the lowest channel k0 showing view v.  Rays are
+// numbered in order of first use by the R subpixels (row-major), then G,
+// then B (Sec. 5: R~_rays follows the R subpixels): an owner's order key is
+// the first R pixel using it, else wh + the first G pixel, else 2wh + the
+// first B pixel, and its ray id is the rank of that key.
 struct RayTmp {
     uint32_t* owner;        // 3wh: owner subpixel of each subpixel's ray
     uint32_t* ray_of_owner; // 3wh: ray id per owner (kEmpty when not an owner)
-    uint32_t* first_g;      // 3wh: first G pixel index using the owner
+    uint32_t* first_r;      // 3wh: first R pixel index using the owner
+    uint32_t* first_g;      // 3wh
     uint32_t* first_b;      // 3wh
-    uint32_t* key_of;       // 3wh: order key of rays not used by R
-    uint32_t* flag;         // 2wh
-    uint32_t* rank;         // 2wh
+    uint32_t* key_of;       // 3wh: order key of each owner
+    uint32_t* flag;         // 3wh: 1 at every used order key
+    uint32_t* rank;         // 3wh + 1
     void* scan_tmp;
 };
 
 __host__ RayTmp carve(const DisplayQ& q, void* tmp) {
-    const size_t n = 3 * size_t(q.w) * q.h, n2 = 2 * size_t(q.w) * q.h;
+    const size_t n = 3 * size_t(q.w) * q.h;
     char* p = static_cast<char*>(tmp);
     RayTmp t;
     auto take = [&](size_t bytes) {
@@ -213,11 +218,12 @@ __host__ RayTmp carve(const DisplayQ& q, void* tmp) {
     };
     t.owner = reinterpret_cast<uint32_t*>(take(4 * n));
     t.ray_of_owner = reinterpret_cast<uint32_t*>(take(4 * n));
+    t.first_r = reinterpret_cast<uint32_t*>(take(4 * n));
     t.first_g = reinterpret_cast<uint32_t*>(take(4 * n));
     t.first_b = reinterpret_cast<uint32_t*>(take(4 * n));
     t.key_of = reinterpret_cast<uint32_t*>(take(4 * n));
-    t.flag = reinterpret_cast<uint32_t*>(take(4 * n2));
-    t.rank = reinterpret_cast<uint32_t*>(take(4 * n2 + 4));
+    t.flag = reinterpret_cast<uint32_t*>(take(4 * n));
+    t.rank = reinterpret_cast<uint32_t*>(take(4 * n + 4));
     t.scan_tmp = take(0);
     return t;
 }
@@ -236,34 +242,29 @@ __global__ void owner_kernel(int32_t w, int32_t h, int64_t n, const uint16_t* __
         while (k0 < 2 && V[3 * sp + k0] != v) ++k0;
         t.owner[i] = uint32_t(3 * sp + k0);
         t.ray_of_owner[i] = kEmpty;
+        t.first_r[i] = kEmpty;
         t.first_g[i] = kEmpty;
         t.first_b[i] = kEmpty;
         t.key_of[i] = kEmpty;
     }
 }
 
-__global__ void r_rays_kernel(int64_t wh, RayTmp t) {
-    for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < wh;
-         p += int64_t(gridDim.x) * blockDim.x)
-        t.ray_of_owner[t.owner[3 * p]] = uint32_t(p);
-}
-
 __global__ void first_use_kernel(int64_t wh, RayTmp t) {
     for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < wh;
          p += int64_t(gridDim.x) * blockDim.x) {
-        const uint32_t og = t.owner[3 * p + 1], ob = t.owner[3 * p + 2];
-        if (t.ray_of_owner[og] == kEmpty) atomicMin(&t.first_g[og], uint32_t(p));
-        if (t.ray_of_owner[ob] == kEmpty) atomicMin(&t.first_b[ob], uint32_t(p));
+        atomicMin(&t.first_r[t.owner[3 * p]], uint32_t(p));
+        atomicMin(&t.first_g[t.owner[3 * p + 1]], uint32_t(p));
+        atomicMin(&t.first_b[t.owner[3 * p + 2]], uint32_t(p));
     }
 }
 
-__global__ void mark_new_kernel(int64_t n, int64_t wh, RayTmp t) {
+__global__ void mark_keys_kernel(int64_t n, int64_t wh, RayTmp t) {
     for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n;
          o += int64_t(gridDim.x) * blockDim.x) {
-        if (t.ray_of_owner[o] != kEmpty) continue;
         uint32_t key = kEmpty;
-        if (t.first_g[o] != kEmpty) key = t.first_g[o];
-        else if (t.first_b[o] != kEmpty) key = uint32_t(wh) + t.first_b[o];
+        if (t.first_r[o] != kEmpty) key = t.first_r[o];
+        else if (t.first_g[o] != kEmpty) key = uint32_t(wh) + t.first_g[o];
+        else if (t.first_b[o] != kEmpty) key = uint32_t(2 * wh) + t.first_b[o];
         if (key != kEmpty) {
             t.key_of[o] = key;
             t.flag[key] = 1;
@@ -271,11 +272,11 @@ __global__ void mark_new_kernel(int64_t n, int64_t wh, RayTmp t) {
     }
 }
 
-__global__ void assign_new_kernel(int64_t n, int64_t wh, RayTmp t) {
+__global__ void assign_kernel(int64_t n, RayTmp t) {
     for (int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; o < n;
          o += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t key = t.key_of[o];
-        if (key != kEmpty) t.ray_of_owner[o] = uint32_t(wh) + t.rank[key];
+        if (key != kEmpty) t.ray_of_owner[o] = t.rank[key];
     }
 }
 
@@ -286,9 +287,8 @@ __global__ void ray_of_kernel(int64_t n, const RayTmp t, uint32_t* __restrict__ 
 }
 
 __global__ void ray_attr_kernel(int32_t w, int64_t n, const uint16_t* __restrict__ V,
-                                const uint32_t* __restrict__ ray_of, const RayTmp t,
-                                uint32_t* __restrict__ ray_view, uint32_t* __restrict__ ray_pix,
-                                int32_t* __restrict__ ray_slot) {
+                                const RayTmp t, uint32_t* __restrict__ ray_view,
+                                uint32_t* __restrict__ ray_pix) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t r = t.ray_of_owner[i];
@@ -297,14 +297,7 @@ __global__ void ray_attr_kernel(int32_t w, int64_t n, const uint16_t* __restrict
             ray_view[r] = V[i];
             ray_pix[r] = pack_px(p / w, p % w);
         }
-        ray_slot[3 * int64_t(ray_of[i]) + (i % 3)] = int32_t(i);
     }
-}
-
-__global__ void fill_i32_kernel(int32_t* p, int64_t n, int32_t v) {
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
-         i += int64_t(gridDim.x) * blockDim.x)
-        p[i] = v;
 }
 
 __global__ void group_keys_kernel(const uint32_t* __restrict__ ray_view,
@@ -317,20 +310,22 @@ __global__ void group_keys_kernel(const uint32_t* __restrict__ ray_view,
         const uint32_t px = ray_pix[r];
         const uint32_t row = px >> 16, col = px & 0xFFFF;
         const uint64_t g = uint64_t(ray_view[r]) * ntiles + (row / th) * ntx + (col / tw);
-        keys[r] = g;
+        // inside the tile, order rays along a Morton curve so that each warp's
+        // rays cover a compact patch
+        uint32_t x = col % tw, y = row % th, m = 0;
+        for (int b = 0; b < 8; ++b) m |= (((x >> b) & 1u) << (2 * b)) | (((y >> b) & 1u) << (2 * b + 1));
+        keys[r] = (g << 16) | m;
         vals[r] = uint32_t(r);
     }
 }
 
 __global__ void group_gather_kernel(const uint32_t* __restrict__ order,
-                                    const uint32_t* __restrict__ ray_pix,
-                                    const int32_t* __restrict__ ray_slot, int64_t n,
-                                    int4* __restrict__ grouped) {
+                                    const uint32_t* __restrict__ ray_pix, int64_t n,
+                                    int2* __restrict__ grouped) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n;
          j += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t r = order[j];
-        grouped[j] = make_int4(int(ray_pix[r]), ray_slot[3 * int64_t(r)],
-                               ray_slot[3 * int64_t(r) + 1], ray_slot[3 * int64_t(r) + 2]);
+        grouped[j] = make_int2(int(ray_pix[r]), int(r));
     }
 }
 
@@ -391,38 +386,34 @@ cudaError_t launch_repurpose(const DisplayQ& q, const uint16_t* V, uint32_t* src
 }
 
 size_t ray_table_tmp_bytes(const DisplayQ& q) {
-    const size_t n = 3 * size_t(q.w) * q.h, n2 = 2 * size_t(q.w) * q.h;
-    return 5 * ((4 * n + 255) & ~size_t(255)) + ((4 * n2 + 255) & ~size_t(255)) +
-           ((4 * n2 + 4 + 255) & ~size_t(255)) + scan_tmp_bytes(int64_t(n2)) + 256;
+    const size_t n = 3 * size_t(q.w) * q.h;
+    return 7 * ((4 * n + 255) & ~size_t(255)) + ((4 * n + 4 + 255) & ~size_t(255)) +
+           scan_tmp_bytes(int64_t(n)) + 256;
 }
 
 cudaError_t launch_ray_table(const DisplayQ& q, const uint16_t* V, const uint32_t* src,
-                             uint32_t* ray_of, void* tmp, uint32_t* d_n_new, cudaStream_t s) {
+                             uint32_t* ray_of, void* tmp, uint32_t* d_n_rays, cudaStream_t s) {
     const int64_t wh = int64_t(q.w) * q.h, n = 3 * wh;
     RayTmp t = carve(q, tmp);
-    cudaError_t e = cudaMemsetAsync(t.flag, 0, sizeof(uint32_t) * 2 * size_t(wh), s);
+    cudaError_t e = cudaMemsetAsync(t.flag, 0, sizeof(uint32_t) * size_t(n), s);
     if (e != cudaSuccess) return e;
     owner_kernel<<<grid_for(n, 256), 256, 0, s>>>(q.w, q.h, n, V, src, t);
-    r_rays_kernel<<<grid_for(wh, 256), 256, 0, s>>>(wh, t);
     first_use_kernel<<<grid_for(wh, 256), 256, 0, s>>>(wh, t);
-    mark_new_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, wh, t);
+    mark_keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, wh, t);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_exclusive_scan(t.flag, t.rank, 2 * wh, d_n_new, t.scan_tmp, s);
+    e = launch_exclusive_scan(t.flag, t.rank, n, d_n_rays, t.scan_tmp, s);
     if (e != cudaSuccess) return e;
-    assign_new_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, wh, t);
+    assign_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, t);
     ray_of_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, t, ray_of);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_attributes(const DisplayQ& q, const uint16_t* V, const uint32_t* ray_of,
-                                  const void* tmp, uint32_t* ray_view, uint32_t* ray_pix,
-                                  int32_t* ray_slot, int64_t n_rays, cudaStream_t s) {
+cudaError_t launch_ray_attributes(const DisplayQ& q, const uint16_t* V, const void* tmp,
+                                  uint32_t* ray_view, uint32_t* ray_pix, cudaStream_t s) {
     const int64_t n = 3 * int64_t(q.w) * q.h;
     RayTmp t = carve(q, const_cast<void*>(tmp));
-    fill_i32_kernel<<<grid_for(3 * n_rays, 256), 256, 0, s>>>(ray_slot, 3 * n_rays, -1);
-    ray_attr_kernel<<<grid_for(n, 256), 256, 0, s>>>(q.w, n, V, ray_of, t, ray_view, ray_pix,
-                                                      ray_slot);
+    ray_attr_kernel<<<grid_for(n, 256), 256, 0, s>>>(q.w, n, V, t, ray_view, ray_pix);
     return cudaGetLastError();
 }
 
@@ -441,11 +432,9 @@ cudaError_t launch_rays_export(const uint32_t* ray_view, const uint32_t* ray_pix
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_pix,
-                                    const int32_t* ray_slot, int64_t n_rays, int4* grouped,
-                                    cudaStream_t s) {
-    group_gather_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(order, ray_pix, ray_slot, n_rays,
-                                                               grouped);
+cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_pix, int64_t n_rays,
+                                    int2* grouped, cudaStream_t s) {
+    group_gather_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(order, ray_pix, n_rays, grouped);
     return cudaGetLastError();
 }
 
@@ -464,7 +453,7 @@ cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_p
 // array until the process exits.
 namespace {
 constexpr int64_t kStaticMaxPixels = 65536;  // panels up to e.g. 256 x 256
-constexpr size_t kStaticScratchBytes = 5u * 1024u * 1024u + 64u * 1024u;
+constexpr size_t kStaticScratchBytes = 6u * 1024u * 1024u + 512u * 1024u;
 constexpr int kStaticMaxDevices = 64;
 }  // namespace
 
@@ -506,22 +495,22 @@ extern "C" dl_status dl_ray_table_static(int32_t width, int32_t height, const ui
         base = g_static_addr[dev];
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    uint32_t* d_new = reinterpret_cast<uint32_t*>(static_cast<char*>(base) + kStaticScratchBytes - 256);
-    const int64_t wh = int64_t(width) * height, n = 3 * wh;
-    if (launch_ray_table(q, V, src, ray_of, base, d_new, s) != cudaSuccess) {
+    uint32_t* d_n = reinterpret_cast<uint32_t*>(static_cast<char*>(base) + kStaticScratchBytes - 256);
+    const int64_t n = 3 * int64_t(width) * height;
+    if (launch_ray_table(q, V, src, ray_of, base, d_n, s) != cudaSuccess) {
         cudaGetLastError();
         return DL_ERR_CUDA;
     }
     RayTmp t = carve(q, base);
     ray_triplets_kernel<<<grid_for(n, 256), 256, 0, s>>>(width, n, V, t, rays);
-    uint32_t h_new = 0;
+    uint32_t h_n = 0;
     if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(&h_new, d_new, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h_n, d_n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return DL_ERR_CUDA;
     }
-    *n_rays = wh + int64_t(h_new);
+    *n_rays = int64_t(h_n);
     return DL_OK;
 }
 

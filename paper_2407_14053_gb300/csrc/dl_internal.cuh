@@ -50,13 +50,15 @@ struct ProjectParams {
 // Per (view, Gaussian) record written by the projection, 3 x float4:
 //  q0 = (u - w/2, v - h/2, A, B)
 //  q1 = (C, log2(opacity), r, g)
-//  q2 = (b, depth, rect_x, rect_y)   rect_x = tx0 | tx1 << 16 (bit pattern)
+//  q2 = (b, depth, rect_c, rect_r)   pixel bounding box of alpha >= 1/255,
+//       rect_c = c0 | c1 << 16, rect_r = r0 | r1 << 16 (bit patterns)
 // with log2 alpha = A dx^2 + B dx dy + C dy^2 + log2(opacity) at pixel offset
 // (dx, dy) from the mean (A, B, C are -log2(e)/2 times the conic's xx, 2xy, yy).
 struct ProjectOut {
     float4* rec;       // nv * n * 3
     uint32_t* count;   // nv * n tiles touched (0 = culled)
     unsigned long long* total;  // sum of count (atomic)
+    uint32_t* gcount;  // optional: keys per (view, tile) group (atomic; zeroed by caller)
 };
 
 template <typename T>
@@ -72,26 +74,26 @@ struct GaussiansView {
 cudaError_t launch_view_map(const DisplayQ& q, uint16_t* V, cudaStream_t s);
 cudaError_t launch_repurpose(const DisplayQ& q, const uint16_t* V, uint32_t* src, int identity,
                              cudaStream_t s);
-// Ray table: fills ray_of (3wh), ray_view/ray_pix (n_rays), ray_slot (3 n_rays).
-// Temporary buffers come from `tmp` (>= ray_table_tmp_bytes(q)).
+// Ray table: fills ray_of (3wh) and *d_n_rays (device); rays are numbered in
+// order of first use by R, then G, then B subpixels.  Scratch comes from
+// `tmp` (>= ray_table_tmp_bytes(q)); launch_ray_attributes then reads the
+// same scratch to fill ray_view / ray_pix (n_rays each).
 size_t ray_table_tmp_bytes(const DisplayQ& q);
 cudaError_t launch_ray_table(const DisplayQ& q, const uint16_t* V, const uint32_t* src,
-                             uint32_t* ray_of, void* tmp, uint32_t* d_n_new, cudaStream_t s);
-cudaError_t launch_ray_attributes(const DisplayQ& q, const uint16_t* V, const uint32_t* ray_of,
-                                  const void* tmp, uint32_t* ray_view, uint32_t* ray_pix,
-                                  int32_t* ray_slot, int64_t n_rays, cudaStream_t s);
-// Group keys of rays for a compositing tile shape: key = v*ntiles + tile,
-// value = ray id (a stable sort then keeps ray order inside a group).
+                             uint32_t* ray_of, void* tmp, uint32_t* d_n_rays, cudaStream_t s);
+cudaError_t launch_ray_attributes(const DisplayQ& q, const uint16_t* V, const void* tmp,
+                                  uint32_t* ray_view, uint32_t* ray_pix, cudaStream_t s);
+// Group keys of rays for a compositing tile shape: key = (v*ntiles + tile) << 16
+// | Morton code of the pixel inside the tile; value = ray id.
 cudaError_t launch_ray_group_keys(const uint32_t* ray_view, const uint32_t* ray_pix, int64_t n_rays,
                                   int32_t tile_w, int32_t tile_h, int32_t ntx, int32_t ntiles,
                                   unsigned long long* keys, uint32_t* vals, cudaStream_t s);
 // (view, row, col) int32 triplets of every ray.
 cudaError_t launch_rays_export(const uint32_t* ray_view, const uint32_t* ray_pix, int64_t n_rays,
                                int32_t* out, cudaStream_t s);
-// Gathers per grouped ray {pixel, slot0, slot1, slot2}.
-cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_pix,
-                                    const int32_t* ray_slot, int64_t n_rays, int4* grouped,
-                                    cudaStream_t s);
+// Gathers per grouped ray {pixel, ray id}.
+cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_pix, int64_t n_rays,
+                                    int2* grouped, cudaStream_t s);
 
 // ---- a5/a6: projection, key emission (project.cu) ------------------------
 // dtype: 0 f32, 1 bf16, 2 f16
@@ -99,6 +101,11 @@ cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_p
 cudaError_t launch_store_cams(const CamBatch& b, int32_t n, Cam* dst, cudaStream_t s);
 cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectParams& p,
                            const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s);
+// Keys depth << 32 | Gaussian into their group's slice [gstart[g], gstart[g+1])
+// (gfill zeroed by the caller).
+cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const float4* rec,
+                               const uint32_t* count, const uint32_t* gstart, uint32_t* gfill,
+                               unsigned long long* keys, cudaStream_t s);
 cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* rec,
                              const uint32_t* count, const uint32_t* offset,
                              unsigned long long* keys, uint32_t* vals, cudaStream_t s);
@@ -115,10 +122,10 @@ size_t radix_tmp_bytes(int64_t n);
 cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, void* tmp,
                              int* result_in_alt, cudaStream_t s);
-// ranges[g] = [first, last) index of keys whose key >> shift == g.  ranges must
-// be zeroed first.
+// ranges[g] = [first, last) index of keys whose key >> shift == g < n_groups.
+// ranges must be zeroed first.
 cudaError_t launch_key_ranges(const unsigned long long* keys, int64_t n, int shift, uint2* ranges,
-                              cudaStream_t s);
+                              int64_t n_groups, cudaStream_t s);
 
 // ---- a7..a9: compositing (composite.cu) -----------------------------------
 struct CompositeParams {
@@ -129,14 +136,51 @@ struct CompositeParams {
 };
 // DirectL: work items {group, begin, end, -} over grouped rays.
 // pairs (optional, 2 x u64): evaluated and composited (ray, Gaussian) pairs.
+// raycol: 3 floats per ray id.
 cudaError_t launch_composite_rays(const CompositeParams& p, const int4* work, int64_t n_work,
-                                  const int4* grouped, const uint2* ranges, const uint32_t* vals,
-                                  const float4* rec, float* out, unsigned long long* pairs,
+                                  const int2* grouped, const uint2* ranges, const uint32_t* vals,
+                                  const float4* rec, float* raycol, unsigned long long* pairs,
                                   cudaStream_t s);
+// Encoded image from ray colours (Sec. 4 step (3), Sec. 6: the channel
+// reorder by precomputed indices): out[i] = raycol[3 ray_of[i] + i mod 3].
+cudaError_t launch_reorder(const uint32_t* ray_of, const float* raycol, int64_t n_subpixels,
+                           float* out, cudaStream_t s);
 // Standard paradigm: every pixel of every view into Mm (nv x h x w x 3).
 cudaError_t launch_composite_full(const CompositeParams& p, int32_t nv, const uint2* ranges,
                                   const uint32_t* vals, const float4* rec, float* Mm,
                                   unsigned long long* pairs, cudaStream_t s);
+// Binned paths: each block sorts its group's keys in shared memory (bucket
+// counting sort, up to `cap` keys, a power of two) and then composites in that
+// order; `transposed` selects the evaluation strategy.
+// `list` selects the blocks' work entries (size class), gwork holds
+// {group, ray begin, ray end, -} per DirectL group with rays.
+constexpr int kBinnedThreads = 128;
+size_t binned_smem_bytes(int cap_p, int nthr);
+cudaError_t launch_composite_rays_binned(const CompositeParams& p, const int4* gwork,
+                                         const int32_t* list, int64_t n_list, int cap_p,
+                                         const int2* grouped, const uint32_t* gstart,
+                                         const unsigned long long* keys, const float4* rec,
+                                         float* raycol, unsigned long long* pairs, int transposed,
+                                         cudaStream_t s);
+cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t* list,
+                                         int64_t n_list, int cap_p, const uint32_t* gstart,
+                                         const unsigned long long* keys, const float4* rec,
+                                         float* Mm, unsigned long long* pairs, int transposed,
+                                         cudaStream_t s);
+// DirectL groups whose lists hold at most `cap` (512 or 1024) keys: one warp
+// per group (warp-level sort, cp.async batches of 32, transposed evaluation).
+cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* gwork,
+                                       const int32_t* list, int64_t n_list, const int2* grouped,
+                                       const uint32_t* gstart, const unsigned long long* keys,
+                                       const float4* rec, float* raycol, unsigned long long* pairs,
+                                       cudaStream_t s);
+// Splits work entries by their group's key count: <= small_cap -> small
+// list, else large list; meta = {n_small, n_large, max count}.  gwork NULL:
+// the entries are the groups 0..n_work-1 themselves.
+cudaError_t launch_partition(const int4* gwork, int64_t n_work, const uint32_t* gstart,
+                             uint32_t small_cap, int32_t* small_list, int32_t* large_list,
+                             uint32_t* meta, cudaStream_t s);
+
 // Alg. 1 sampling step at native resolution.
 cudaError_t launch_interweave(int32_t w, int32_t h, int32_t nv, const uint16_t* V, const float* Mm,
                               float* out, cudaStream_t s);

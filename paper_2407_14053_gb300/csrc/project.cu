@@ -154,6 +154,14 @@ __global__ void __launch_bounds__(256) project_kernel(GaussiansView<T> G, Projec
                         const int tx0 = ic0 / p.tile_w, tx1 = ic1 / p.tile_w;
                         const int ty0 = ir0 / p.tile_h, ty1 = ir1 / p.tile_h;
                         cnt = uint32_t(tx1 - tx0 + 1) * uint32_t(ty1 - ty0 + 1);
+                        const uint32_t rect_c = uint32_t(ic0) | (uint32_t(ic1) << 16);
+                        const uint32_t rect_r = uint32_t(ir0) | (uint32_t(ir1) << 16);
+                        if (out.gcount) {  // keys per (view, tile) group
+                            const uint32_t vb = uint32_t(v) * uint32_t(p.ntx * p.nty);
+                            for (int ty = ty0; ty <= ty1; ++ty)
+                                for (int tx = tx0; tx <= tx1; ++tx)
+                                    atomicAdd(out.gcount + vb + uint32_t(ty * p.ntx + tx), 1u);
+                        }
                         const float id = 1.f / det;
                         // colour: SH at dir = normalise(mu - camera centre)
                         float dx = mx - cam.c[0], dy = my - cam.c[1], dz = mz - cam.c[2];
@@ -172,8 +180,7 @@ __global__ void __launch_bounds__(256) project_kernel(GaussiansView<T> G, Projec
                         float4* rec = out.rec + 3 * e;
                         rec[0] = make_float4(uc, vc, -0.5f * kLog2e * cyy * id, kLog2e * cxy * id);
                         rec[1] = make_float4(-0.5f * kLog2e * cxx * id, log2o, col[0], col[1]);
-                        rec[2] = make_float4(col[2], tz, __uint_as_float(uint32_t(tx0) | (uint32_t(tx1) << 16)),
-                                             __uint_as_float(uint32_t(ty0) | (uint32_t(ty1) << 16)));
+                        rec[2] = make_float4(col[2], tz, __uint_as_float(rect_c), __uint_as_float(rect_r));
                     }
                 }
             }
@@ -210,7 +217,8 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
         if (!cnt) continue;
         const float4 q2 = rec[3 * e + 2];
         const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
-        const int tx0 = rx & 0xFFFF, tx1 = rx >> 16, ty0 = ry & 0xFFFF, ty1 = ry >> 16;
+        const int tx0 = int(rx & 0xFFFF) / p.tile_w, tx1 = int(rx >> 16) / p.tile_w;
+        const int ty0 = int(ry & 0xFFFF) / p.tile_h, ty1 = int(ry >> 16) / p.tile_h;
         uint32_t dk = __float_as_uint(q2.y) - zbits0;
         if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
         const int64_t v = e / p.n;
@@ -223,6 +231,37 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
                 keys[o] = (grp << 28) | dk;
                 vals[o] = gidx;
                 ++o;
+            }
+    }
+}
+
+// Binned emission: every (view, tile, Gaussian) key goes straight into its
+// group's slice of the key array (slot from an atomic cursor); the order
+// inside a group is fixed later by sorting the unique keys depth << 32 | index.
+__global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
+                                   const uint32_t* __restrict__ count,
+                                   const uint32_t* __restrict__ gstart, uint32_t* __restrict__ gfill,
+                                   unsigned long long* __restrict__ keys) {
+    const int64_t total = int64_t(nv) * p.n;
+    const int ntiles = p.ntx * p.nty;
+    const uint32_t zbits0 = __float_as_uint(0.2f);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        if (!count[e]) continue;
+        const float4 q2 = rec[3 * e + 2];
+        const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
+        const int tx0 = int(rx & 0xFFFF) / p.tile_w, tx1 = int(rx >> 16) / p.tile_w;
+        const int ty0 = int(ry & 0xFFFF) / p.tile_h, ty1 = int(ry >> 16) / p.tile_h;
+        uint32_t dk = __float_as_uint(q2.y) - zbits0;
+        if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
+        const int64_t v = e / p.n;
+        const uint32_t gidx = uint32_t(e - v * p.n);
+        const unsigned long long key = ((unsigned long long)dk << 32) | gidx;
+        const uint32_t vb = uint32_t(v) * uint32_t(ntiles);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                const uint32_t grp = vb + uint32_t(ty * p.ntx + tx);
+                keys[gstart[grp] + atomicAdd(gfill + grp, 1u)] = key;
             }
     }
 }
@@ -264,6 +303,18 @@ cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectPar
     if (dtype == 1) return launch_project_t<__nv_bfloat16>(attrs, p, cams, nv, out, s);
     if (dtype == 2) return launch_project_t<__half>(attrs, p, cams, nv, out, s);
     return launch_project_t<float>(attrs, p, cams, nv, out, s);
+}
+
+cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const float4* rec,
+                               const uint32_t* count, const uint32_t* gstart, uint32_t* gfill,
+                               unsigned long long* keys, cudaStream_t s) {
+    const int64_t total = int64_t(nv) * p.n;
+    int64_t grid = (total + 255) / 256;
+    const int64_t cap = int64_t(num_sms()) * 32;
+    if (grid > cap) grid = cap;
+    emit_binned_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, rec, count, gstart, gfill,
+                                                                     keys);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* rec,

@@ -242,10 +242,11 @@ radix_downsweep_kernel(const unsigned long long* __restrict__ kin, const uint32_
 }
 
 __global__ void key_ranges_kernel(const unsigned long long* __restrict__ keys, int64_t n,
-                                  int shift, uint2* __restrict__ ranges) {
+                                  int shift, uint2* __restrict__ ranges, int64_t n_groups) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
         const unsigned long long g = keys[i] >> shift;
+        if (g >= (unsigned long long)n_groups) continue;  // never produced; not followed
         if (i == 0 || (keys[i - 1] >> shift) != g) ranges[g].x = uint32_t(i);
         if (i == n - 1 || (keys[i + 1] >> shift) != g) ranges[g].y = uint32_t(i + 1);
     }
@@ -326,12 +327,12 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* vals, unsigned 
 }
 
 cudaError_t launch_key_ranges(const unsigned long long* keys, int64_t n, int shift, uint2* ranges,
-                              cudaStream_t s) {
+                              int64_t n_groups, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t grid = (n + 255) / 256;
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
-    key_ranges_kernel<<<unsigned(grid), 256, 0, s>>>(keys, n, shift, ranges);
+    key_ranges_kernel<<<unsigned(grid), 256, 0, s>>>(keys, n, shift, ranges, n_groups);
     return cudaGetLastError();
 }
 

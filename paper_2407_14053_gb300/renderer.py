@@ -122,6 +122,22 @@ class Renderer:
                           out.data_ptr(), 0, _stream())
         return out
 
+    def set_sort_mode(self, mode: str) -> None:
+        """'auto', 'radix' or 'binned' (see DL_OPT_SORT_MODE)."""
+        B.dl_set_option(self.ctx, B.DL_OPT_SORT_MODE,
+                        {"auto": B.DL_SORT_AUTO, "radix": B.DL_SORT_RADIX, "binned": B.DL_SORT_BINNED}[mode])
+
+    def set_eval(self, mode: str, strategy: str) -> None:
+        """Evaluation strategy ('direct' or 'transposed') of 'directl' (and
+        'required_only') or of 'standard'."""
+        opt = B.DL_OPT_EVAL_STANDARD if mode == "standard" else B.DL_OPT_EVAL_DIRECTL
+        B.dl_set_option(self.ctx, opt, {"direct": B.DL_EVAL_DIRECT,
+                                        "transposed": B.DL_EVAL_TRANSPOSED}[strategy])
+
+    def set_warp_cap(self, cap: int) -> None:
+        """Longest tile list (512 or 1024 keys; 0 = none) one warp composites."""
+        B.dl_set_option(self.ctx, B.DL_OPT_WARP_LIST_CAP, int(cap))
+
     def enable_stage_timing(self, on: bool = True) -> None:
         B.dl_enable_stage_timing(self.ctx, on)
 

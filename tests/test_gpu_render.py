@@ -232,8 +232,62 @@ def test_stage_timing_and_pair_counters(renderer):
                                  "ms_ranges", "ms_composite", "ms_interweave"))
     assert tot["ms_total"] > 0 and abs(parts - tot["ms_total"]) <= 1e-3 * max(tot["ms_total"], 1.0) + 0.05
     assert tot["pairs_evaluated"] >= tot["pairs_blended"] > 0
-    assert tot["n_launches"] > 3 * 10
+    assert tot["n_launches"] >= 3 * 6
     # timing changes nothing in the image
     assert np.array_equal(img, ref)
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+@pytest.mark.parametrize("mode", ["directl", "standard"])
+def test_sort_modes_give_identical_frames(renderer, mode):
+    # binned keys sorted per tile in shared memory vs one global radix sort:
+    # the same depth order reaches every ray, so the frames match bit for bit
+    d, scene = _tiny_case(n=1500, seed=5)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, -1.5)
+    frames = {}
+    try:
+        for sm in ("radix", "binned", "auto"):
+            renderer.set_sort_mode(sm)
+            frames[sm] = _frame(renderer, sid, did, L0, mode)
+    finally:
+        renderer.set_sort_mode("auto")
+    assert np.array_equal(frames["radix"], frames["binned"])
+    assert np.array_equal(frames["auto"], frames["binned"])
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+@pytest.mark.parametrize("n,expect_binned", [(6000, True), (24000, False)])
+def test_long_tile_lists(renderer, n, expect_binned):
+    # a dense cluster puts thousands of Gaussians in one 64x64 tile: 6000 go
+    # through the large shared-memory class, 24000 exceed it and the frame
+    # falls back to the global radix sort
+    from paper_2407_14053_gb300 import DirectLError
+    d = W.Display(96, 64, 5, 5.3, 1 / 6, view_span_deg=8.0)
+    scene = W.make_scene(W.SceneSpec(n, 1, "uniform", "f32", seed=9))
+    scene["mean"] *= np.float32(0.08)
+    scene["log_scale"][:] = np.float32(-3.5)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 0.0)
+    img = _frame(renderer, sid, did, L0, "directl").reshape(-1)
+    renderer.set_sort_mode("binned")
+    try:
+        if expect_binned:
+            assert np.array_equal(_frame(renderer, sid, did, L0, "directl").reshape(-1), img)
+        else:
+            with pytest.raises(DirectLError):
+                renderer.render(sid, did, L0, "directl")
+    finally:
+        renderer.set_sort_mode("auto")
+    V = oracle.view_map(d)
+    src = oracle.repurpose(d, V)
+    sub = W.sample_subpixels(d, 300, windows=1, window_px=12, seed=2)
+    ref = oracle.render_subpixels(oracle.Scene(scene), d, L0, sub, V, src)
+    ok, maxerr, nbad = _accept(img[sub], ref, TOL)
+    assert nbad == 0, f"{nbad} outside tolerance; max |err| {maxerr:.3g}"
     renderer.free_display(did)
     renderer.free_scene(sid)

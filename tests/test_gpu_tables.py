@@ -54,6 +54,7 @@ def test_paper_panel_tables(renderer, name):
     dict(width=200, height=120, num_views=45, pitch_lx=8.1, tan_slant=0.18, offset_k=0.0, repurpose=0),
     dict(width=1, height=1, num_views=3, pitch_lx=3.0, tan_slant=0.0, offset_k=0.0),
     dict(width=333, height=7, num_views=100, pitch_lx=11.7, tan_slant=0.2, offset_k=-3.5, p_w=3),
+    dict(width=96, height=64, num_views=5, pitch_lx=5.3, tan_slant=1 / 6, offset_k=0.0),
 ])
 def test_edge_displays(renderer, kw):
     _check_tables(renderer, W.Display(**kw))

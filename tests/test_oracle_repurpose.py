@@ -116,3 +116,21 @@ def test_ray_table_r_first_and_unique():
     _, first = np.unique(extra, return_index=True)
     order = extra[np.sort(first)]
     assert np.array_equal(order, np.arange(h * w, rays.shape[0]))
+
+
+def test_ray_order_when_views_repeat_within_a_pixel():
+    # N_v < L_x: two channels of a pixel can show one view, so two R
+    # subpixels may share a ray; rays are still numbered by first use
+    # (R row-major, then G, then B) and every subpixel gets its own ray
+    d = W.Display(96, 64, 5, 5.3, 1 / 6, view_span_deg=8.0)
+    V, src, ray_of, rays = _tables(d)
+    h, w = d.height, d.width
+    seq = np.concatenate([ray_of[..., 0].ravel(), ray_of[..., 1].ravel(), ray_of[..., 2].ravel()])
+    _, first = np.unique(seq.astype(np.int64), return_index=True)
+    assert np.array_equal(seq[np.sort(first)], np.arange(rays.shape[0]))
+    v = V.reshape(h, w, 3).astype(np.int64)
+    r = rays[ray_of.astype(np.int64)]
+    assert np.array_equal(r[..., 0], v)
+    assert np.array_equal(r[..., 1], (src >> 16).astype(np.int64))
+    assert np.array_equal(r[..., 2], (src & 0xFFFF).astype(np.int64))
+    assert len(np.unique(ray_of[..., 0])) < h * w   # R subpixels do share rays here
