@@ -177,7 +177,7 @@ dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, 
                              size_t* bytes);
 
 /* Compositing tile shape of a mode (powers of two, 8..256 pixels each
- * side).  Defaults: DL_STANDARD and DL_REQUIRED_ONLY 16x16, DL_DIRECTL 64x64. */
+ * side).  Defaults: DL_STANDARD 16x16, DL_DIRECTL and DL_REQUIRED_ONLY 32x32. */
 dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h);
 
 /*

@@ -121,7 +121,7 @@ struct dl_ctx {
     std::map<int32_t, std::unique_ptr<dl::Scene>> scenes;
     std::map<int32_t, std::unique_ptr<dl::Display>> displays;
     dl::Workspace ws;
-    int32_t tile[3][2] = {{64, 64}, {16, 16}, {16, 16}};
+    int32_t tile[3][2] = {{32, 32}, {16, 16}, {32, 32}};
     int32_t sort_mode = DL_SORT_AUTO;
     int32_t eval_transposed[3] = {1, 0, 1};  // per mode
     int32_t warp_cap = 512;
@@ -482,6 +482,21 @@ dl_status dl_load_gaussians(dl_ctx* ctx, const dl_gaussians_desc* d, void* strea
         DL_CK(pt.b->reserve(pt.bytes), "alloc scene");
         DL_CK(cudaMemcpyAsync(pt.b->p, pt.src, pt.bytes, kind, s), "copy scene");
     }
+    if (sc->n > 1) {
+        // Morton order of the means (see scene.cu)
+        DevBuf tmp;
+        DL_CK(tmp.reserve(spatial_order_tmp_bytes(sc->n)), "alloc reorder scratch");
+        uint32_t* perm = nullptr;
+        DL_CK(launch_spatial_order(sc->mean.as<float>(), sc->n, tmp.p, &perm, s), "spatial order");
+        for (auto& pt : parts) {
+            DevBuf sorted;
+            DL_CK(sorted.reserve(pt.bytes), "alloc scene");
+            DL_CK(launch_gather_records(pt.b->p, sorted.p, perm, sc->n, pt.bytes / n, s), "gather");
+            std::swap(pt.b->p, sorted.p);
+            std::swap(pt.b->bytes, sorted.bytes);
+            DL_CK(cudaStreamSynchronize(s), "sync");
+        }
+    }
     if (!d->on_device) DL_CK(cudaStreamSynchronize(s), "sync");
     const int32_t id = ctx->next_id++;
     ctx->scenes[id] = std::move(sc);
@@ -831,17 +846,23 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
           "group scan");
     const int4* gwork = mode == DL_STANDARD ? nullptr : G->gwork.as<int4>();
     const int64_t n_work = mode == DL_STANDARD ? ngroups : G->n_gwork;
-    DL_CK(W.lists.reserve(8 * size_t(std::max<int64_t>(n_work, 1))), "alloc lists");
+    const size_t nw1 = size_t(std::max<int64_t>(n_work, 1));
+    DL_CK(W.lists.reserve(24 * nw1 + 16), "alloc lists");
     int32_t* small_list = W.lists.as<int32_t>();
-    int32_t* large_list = small_list + std::max<int64_t>(n_work, 1);
-    // DirectL: lists up to warp_list_cap() keys go to the warp-per-group
-    // kernel, longer ones to the block kernel; standard: small / large block
-    // classes.
+    int32_t* large_list = small_list + nw1;
+    int4* items = reinterpret_cast<int4*>(W.lists.as<char>() + 8 * nw1 + 15 - ((8 * nw1 + 15) % 16));
+    // DirectL: lists of up to warp_cap keys become warp items, longer ones go
+    // to the block kernel; standard: small / large block classes.
     const bool warp_path = mode != DL_STANDARD && ctx->warp_cap > 0;
-    const uint32_t split = warp_path ? uint32_t(ctx->warp_cap) : uint32_t(kSmallCap);
-    DL_CK(launch_partition(gwork, n_work, W.gstart.as<uint32_t>(), split, small_list, large_list,
-                           d_meta, s),
-          "partition");
+    if (warp_path) {
+        DL_CK(launch_partition_warp(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(ctx->warp_cap),
+                                    items, large_list, d_meta, s),
+              "partition");
+    } else {
+        DL_CK(launch_partition(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(kSmallCap), small_list,
+                               large_list, d_meta, s),
+              "partition");
+    }
     DL_CK(mark(2), "event");
     DL_CK(cudaMemcpyAsync(W.h_total, W.small.p, 256, cudaMemcpyDeviceToHost, s), "copy totals");
     DL_CK(cudaStreamSynchronize(s), "sync");
@@ -915,9 +936,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                   "composite full (large lists)");
         } else {
             if (warp_path) {
-                DL_CK(launch_composite_rays_warp(cp, ctx->warp_cap, G->gwork.as<int4>(), small_list,
-                                                 n_small, G->grouped.as<int2>(),
-                                                 W.gstart.as<uint32_t>(), keys, W.rec.as<float4>(),
+                DL_CK(launch_composite_rays_warp(cp, ctx->warp_cap, items, n_small, d_meta + 3,
+                                                 G->grouped.as<int2>(), keys, W.rec.as<float4>(),
                                                  raycol, pairs, s),
                       "composite rays (warp per group)");
             } else {

@@ -859,30 +859,50 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
     __syncwarp();
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Persistent: one resident warp per slot takes items until none is left; an
+// item is {group, first key, first ray, rays << 16 | keys}.  While one group
+// is composited, the next item is loaded and its keys and rays are
+// prefetched into L2.  *cursor must be 0 at launch.
 template <int CAP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ gwork,
-                           const int32_t* __restrict__ list, int64_t n_list,
-                           const int2* __restrict__ grouped, const uint32_t* __restrict__ gstart,
+composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ items, int64_t n_items,
+                           uint32_t* __restrict__ cursor, const int2* __restrict__ grouped,
                            const unsigned long long* __restrict__ keys,
                            const float4* __restrict__ rec, float* __restrict__ raycol,
                            unsigned long long* __restrict__ pairs) {
     extern __shared__ __align__(16) unsigned char wsm_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP>& W = reinterpret_cast<WarpSmem<CAP>*>(wsm_raw)[warp];
-    const int64_t item = int64_t(blockIdx.x) * kWarpsPerBlock + warp;
+    const int64_t n_warps = int64_t(gridDim.x) * kWarpsPerBlock;
+    int64_t item = int64_t(blockIdx.x) * kWarpsPerBlock + warp;
     uint32_t evals = 0, blended = 0;
-    if (item < n_list) {
-        const int4 wi = gwork[list[item]];
-        const int v = wi.x / p.ntiles;
-        const uint32_t start = gstart[wi.x];
-        const int len = int(gstart[wi.x + 1] - start);
-        warp_sort(keys, start, len, W);
+    int4 cur = item < n_items ? items[item] : make_int4(0, 0, 0, 0);
+    while (item < n_items) {
+        // next item: the first n_warps items are taken by warp id, the rest
+        // claimed from the cursor (groups differ widely in cost)
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(cursor, 1u);
+        const int64_t nxt = n_warps + int64_t(__shfl_sync(0xffffffffu, c, 0));
+        const int4 next = nxt < n_items ? items[nxt] : make_int4(0, 0, 0, 0);
+        const int group = cur.x;
+        const uint32_t start = uint32_t(cur.y);
+        const int rbeg = cur.z, nrays = int(uint32_t(cur.w) >> 16), len = cur.w & 0xFFFF;
+        const int v = group / p.ntiles;
+        warp_sort<CAP>(keys, start, len, W);
+        if (nxt < n_items) {  // warm L2 for the next group
+            const int nlen = next.w & 0xFFFF, nr = int(uint32_t(next.w) >> 16);
+            for (int i = lane * 16; i < nlen; i += 32 * 16) prefetch_l2(keys + uint32_t(next.y) + i);
+            for (int i = lane * 16; i < nr; i += 32 * 16) prefetch_l2(grouped + next.z + i);
+        }
         const int64_t vbase = int64_t(v) * p.n;
-        for (int r0 = wi.y; r0 < wi.z; r0 += 32) {
+        for (int r0 = 0; r0 < nrays; r0 += 32) {
             const int rid = r0 + lane;
-            const bool active = rid < wi.z;
-            const int2 ray = active ? grouped[rid] : make_int2(0, -1);
+            const bool active = rid < nrays;
+            const int2 ray = active ? grouped[rbeg + rid] : make_int2(0, -1);
             const int col = int(uint32_t(ray.x) & 0xFFFFu), row = int(uint32_t(ray.x) >> 16);
             const float px = float(col) - p.half_w, py = float(row) - p.half_h;
             int bx0, bx1, by0, by1;
@@ -898,8 +918,31 @@ composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ gwork,
             }
             blended += a.blended;
         }
+        item = nxt;
+        cur = next;
     }
     if (pairs) count_pairs(pairs, evals, blended);
+}
+
+// Items of the warp class: DirectL groups with at most `cap` keys and fewer
+// than 65536 rays become self-contained items; the rest go to the block
+// list (as gwork indices).  meta = {n_items, n_block, max keys}.
+__global__ void partition_warp_kernel(const int4* __restrict__ gwork, int64_t n_work,
+                                      const uint32_t* __restrict__ gstart, uint32_t cap,
+                                      int4* __restrict__ items, int32_t* __restrict__ block_list,
+                                      uint32_t* __restrict__ meta) {
+    for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < n_work;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        const int4 wi = gwork[w];
+        const uint32_t st = gstart[wi.x];
+        const uint32_t len = gstart[wi.x + 1] - st;
+        const uint32_t nr = uint32_t(wi.z - wi.y);
+        if (len <= cap && nr < 65536u)
+            items[atomicAdd(meta, 1u)] = make_int4(wi.x, int(st), wi.y, int((nr << 16) | len));
+        else
+            block_list[atomicAdd(meta + 1, 1u)] = int32_t(w);
+        atomicMax(meta + 2, len);
+    }
 }
 
 __global__ void partition_kernel(const int4* __restrict__ gwork, int64_t n_work,
@@ -1008,24 +1051,41 @@ cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t
     return regs ? go(composite_full_binned_kernel<false, 4>) : go(composite_full_binned_kernel<false, 0>);
 }
 
-cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* gwork,
-                                       const int32_t* list, int64_t n_list, const int2* grouped,
-                                       const uint32_t* gstart, const unsigned long long* keys,
-                                       const float4* rec, float* raycol, unsigned long long* pairs,
-                                       cudaStream_t s) {
-    if (n_list <= 0) return cudaSuccess;
-    const int64_t blocks = (n_list + kWarpsPerBlock - 1) / kWarpsPerBlock;
+cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* items,
+                                       int64_t n_items, uint32_t* cursor, const int2* grouped,
+                                       const unsigned long long* keys, const float4* rec,
+                                       float* raycol, unsigned long long* pairs, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+
     auto go = [&](auto kernel, size_t smem) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
-        kernel<<<unsigned(blocks), kWarpsPerBlock * 32, smem, s>>>(p, gwork, list, n_list, grouped,
-                                                                   gstart, keys, rec, raycol, pairs);
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerBlock * 32, smem);
+        if (e != cudaSuccess) return e;
+        int64_t blocks = int64_t(num_sms()) * (per_sm > 0 ? per_sm : 1);
+        const int64_t need = (n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        if (blocks > need) blocks = need;
+        kernel<<<unsigned(blocks), kWarpsPerBlock * 32, smem, s>>>(p, items, n_items, cursor, grouped,
+                                                                   keys, rec, raycol, pairs);
         return cudaGetLastError();
     };
     if (cap == 1024)
         return go(composite_rays_warp_kernel<1024>, kWarpsPerBlock * sizeof(WarpSmem<1024>));
     return go(composite_rays_warp_kernel<512>, kWarpsPerBlock * sizeof(WarpSmem<512>));
+}
+
+cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
+                                  uint32_t cap, int4* items, int32_t* block_list, uint32_t* meta,
+                                  cudaStream_t s) {
+    if (n_work <= 0) return cudaSuccess;
+    int64_t grid = (n_work + 255) / 256;
+    const int64_t lim = int64_t(num_sms()) * 16;
+    if (grid > lim) grid = lim;
+    partition_warp_kernel<<<unsigned(grid), 256, 0, s>>>(gwork, n_work, gstart, cap, items,
+                                                         block_list, meta);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_partition(const int4* gwork, int64_t n_work, const uint32_t* gstart,

@@ -70,6 +70,16 @@ struct GaussiansView {
     const T* sh;
 };
 
+// ---- scene layout (scene.cu) ----------------------------------------------
+// Morton order of the means: *perm (inside tmp) lists the source index of
+// each reordered Gaussian.
+size_t spatial_order_tmp_bytes(int64_t n);
+cudaError_t launch_spatial_order(const float* mean, int64_t n, void* tmp, uint32_t** perm,
+                                 cudaStream_t s);
+// dst record i = src record perm[i] (record_bytes even).
+cudaError_t launch_gather_records(const void* src, void* dst, const uint32_t* perm, int64_t n,
+                                  size_t record_bytes, cudaStream_t s);
+
 // ---- a1..a3: display tables (display.cu) --------------------------------
 cudaError_t launch_view_map(const DisplayQ& q, uint16_t* V, cudaStream_t s);
 cudaError_t launch_repurpose(const DisplayQ& q, const uint16_t* V, uint32_t* src, int identity,
@@ -168,12 +178,18 @@ cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t
                                          float* Mm, unsigned long long* pairs, int transposed,
                                          cudaStream_t s);
 // DirectL groups whose lists hold at most `cap` (512 or 1024) keys: one warp
-// per group (warp-level sort, cp.async batches of 32, transposed evaluation).
-cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* gwork,
-                                       const int32_t* list, int64_t n_list, const int2* grouped,
-                                       const uint32_t* gstart, const unsigned long long* keys,
-                                       const float4* rec, float* raycol, unsigned long long* pairs,
-                                       cudaStream_t s);
+// per group (warp-level sort, cp.async batches of 32, transposed evaluation),
+// persistent over self-contained items {group, first key, first ray,
+// rays << 16 | keys} made by launch_partition_warp (the other groups' gwork
+// indices go to block_list; meta = {n_items, n_block, max keys}).  The
+// compositing kernel claims items through *cursor, which must be 0.
+cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
+                                  uint32_t cap, int4* items, int32_t* block_list, uint32_t* meta,
+                                  cudaStream_t s);
+cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* items,
+                                       int64_t n_items, uint32_t* cursor, const int2* grouped,
+                                       const unsigned long long* keys, const float4* rec,
+                                       float* raycol, unsigned long long* pairs, cudaStream_t s);
 // Splits work entries by their group's key count: <= small_cap -> small
 // list, else large list; meta = {n_small, n_large, max count}.  gwork NULL:
 // the entries are the groups 0..n_work-1 themselves.

@@ -158,9 +158,21 @@ __global__ void __launch_bounds__(256) project_kernel(GaussiansView<T> G, Projec
                         const uint32_t rect_r = uint32_t(ir0) | (uint32_t(ir1) << 16);
                         if (out.gcount) {  // keys per (view, tile) group
                             const uint32_t vb = uint32_t(v) * uint32_t(p.ntx * p.nty);
-                            for (int ty = ty0; ty <= ty1; ++ty)
-                                for (int tx = tx0; tx <= tx1; ++tx)
-                                    atomicAdd(out.gcount + vb + uint32_t(ty * p.ntx + tx), 1u);
+                            const uint32_t g0 = vb + uint32_t(ty0 * p.ntx + tx0);
+                            // the warp's Gaussians are neighbours in space: when
+                            // every active lane covers the same single tile,
+                            // one lane adds for all of them
+                            const unsigned am = __activemask();
+                            const bool single = tx0 == tx1 && ty0 == ty1;
+                            const bool same = __all_sync(am, single) &&
+                                              __reduce_min_sync(am, g0) == __reduce_max_sync(am, g0);
+                            if (same) {
+                                if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(out.gcount + g0, __popc(am));
+                            } else {
+                                for (int ty = ty0; ty <= ty1; ++ty)
+                                    for (int tx = tx0; tx <= tx1; ++tx)
+                                        atomicAdd(out.gcount + vb + uint32_t(ty * p.ntx + tx), 1u);
+                            }
                         }
                         const float id = 1.f / det;
                         // colour: SH at dir = normalise(mu - camera centre)
@@ -258,10 +270,20 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
         const uint32_t gidx = uint32_t(e - v * p.n);
         const unsigned long long key = ((unsigned long long)dk << 32) | gidx;
         const uint32_t vb = uint32_t(v) * uint32_t(ntiles);
+        const int lane = threadIdx.x & 31;
+        const unsigned lt = (1u << lane) - 1u;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) {
+                // lanes of the warp on the same group take consecutive slots
+                // with one atomic
                 const uint32_t grp = vb + uint32_t(ty * p.ntx + tx);
-                keys[gstart[grp] + atomicAdd(gfill + grp, 1u)] = key;
+                const unsigned am = __activemask();
+                const unsigned peers = __match_any_sync(am, grp);
+                const int leader = __ffs(peers) - 1;
+                uint32_t base = 0;
+                if (lane == leader) base = atomicAdd(gfill + grp, uint32_t(__popc(peers)));
+                base = __shfl_sync(peers, base, leader);
+                keys[gstart[grp] + base + __popc(peers & lt)] = key;
             }
     }
 }

@@ -139,7 +139,7 @@ def test_tile_shapes(renderer, mode, tile):
     try:
         img = _frame(renderer, sid, did, L0, mode).reshape(-1)
     finally:
-        renderer.set_tile(mode, *{"directl": (64, 64)}.get(mode, (16, 16)))
+        renderer.set_tile(mode, *{"standard": (16, 16)}.get(mode, (32, 32)))
     V, src = _sources(renderer, did, d, mode)
     ref = oracle.render_subpixels(oracle.Scene(scene), d, L0, np.arange(img.size), V, src)
     ok, maxerr, nbad = _accept(img, ref, TOL)
