@@ -856,7 +856,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     const bool warp_path = mode != DL_STANDARD && ctx->warp_cap > 0;
     if (warp_path) {
         DL_CK(launch_partition_warp(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(ctx->warp_cap),
-                                    items, large_list, d_meta, s),
+                                    ctx->warp_cap < 1024 ? 1024u : 0u, items, large_list, d_meta, s),
               "partition");
     } else {
         DL_CK(launch_partition(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(kSmallCap), small_list,
@@ -869,11 +869,12 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     const unsigned long long nkeys = W.h_total[0];
     const uint32_t* h_meta = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(W.h_total) + 128);
     const int64_t n_small = h_meta[0], n_large = h_meta[1];
+    const int64_t n_mid = warp_path ? int64_t(h_meta[4]) : 0;  // 1024-key warp class
     const int64_t max_len = h_meta[2];
     if (nkeys >= (1ull << 31) - 1)
         return fail(ctx, DL_ERR_CAPACITY, "frame needs %llu tile keys (limit 2^31-1)", nkeys);
     const int64_t nk = int64_t(nkeys);
-    int cap_large = warp_path ? 2 * ctx->warp_cap : 1;
+    int cap_large = warp_path ? 2048 : 1;
     while (cap_large < max_len) cap_large <<= 1;
     const int binned_threads = mode == DL_STANDARD ? tw * th : kBinnedThreads;
     bool binned = ctx->sort_mode != DL_SORT_RADIX && max_len <= kLargeCap &&
@@ -940,6 +941,10 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                                                  G->grouped.as<int2>(), keys, W.rec.as<float4>(),
                                                  raycol, pairs, s),
                       "composite rays (warp per group)");
+                DL_CK(launch_composite_rays_warp(cp, 1024, items + (n_work - n_mid), n_mid,
+                                                 d_meta + 5, G->grouped.as<int2>(), keys,
+                                                 W.rec.as<float4>(), raycol, pairs, s),
+                      "composite rays (warp per group, 1024 keys)");
             } else {
                 DL_CK(launch_composite_rays_binned(cp, G->gwork.as<int4>(), small_list, n_small,
                                                    kSmallCap, G->grouped.as<int2>(),
@@ -953,7 +958,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                                                ctx->eval_transposed[mode], s),
                   "composite rays (large lists)");
         }
-        launches += 1 + (n_small > 0 ? 1 : 0) + (n_large > 0 ? 1 : 0);
+        launches += 1 + (n_small > 0 ? 1 : 0) + (n_mid > 0 ? 1 : 0) + (n_large > 0 ? 1 : 0);
     } else {
         // ---- global tile keys and a stable LSD radix sort ----
         DL_CK(W.offset.reserve(4 * size_t(ne)), "alloc offsets");
@@ -1015,7 +1020,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     fs.tile_h = th;
     fs.sort_bits = sort_bits;
     fs.n_launches = launches;
-    fs.lists_small = n_small;
+    fs.lists_small = n_small + n_mid;
     fs.lists_large = n_large;
     fs.max_list = max_len;
     if (timing) {

@@ -836,14 +836,26 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
         if (__any_sync(0xffffffffu, hit)) {
             unsigned act = __ballot_sync(0xffffffffu, !done);
             unsigned mine = 0;
-            while (act) {
-                const int r = __ffs(act) - 1;
+            while (act) {  // four rays per pass: independent chains
+                int r[4];
+                r[0] = __ffs(act) - 1;
                 act &= act - 1;
-                const float rx = __shfl_sync(0xffffffffu, px, r);
-                const float ry = __shfl_sync(0xffffffffu, py, r);
-                const bool pass = log2_alpha(rx, ry, u, v, A, B, C, L) >= kLog2MinAlpha;
-                const unsigned m = __ballot_sync(0xffffffffu, pass);
-                if (lane == r) mine = m;
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {  // repeats r[0] once act runs out
+                    r[k] = act ? __ffs(act) - 1 : r[0];
+                    act &= act - 1;
+                }
+                unsigned m[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float rx = __shfl_sync(0xffffffffu, px, r[k]);
+                    const float ry = __shfl_sync(0xffffffffu, py, r[k]);
+                    m[k] = __ballot_sync(0xffffffffu,
+                                         log2_alpha(rx, ry, u, v, A, B, C, L) >= kLog2MinAlpha);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (lane == r[k]) mine = m[k];
             }
             if (!done) evals += uint32_t(n);
             while (mine && !done) {
@@ -924,21 +936,26 @@ composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ items, in
     if (pairs) count_pairs(pairs, evals, blended);
 }
 
-// Items of the warp class: DirectL groups with at most `cap` keys and fewer
-// than 65536 rays become self-contained items; the rest go to the block
-// list (as gwork indices).  meta = {n_items, n_block, max keys}.
+// Items of the warp classes: DirectL groups with fewer than 65536 rays and
+// at most cap1 keys become self-contained items at the front of `items`,
+// those with cap1 < keys <= cap2 at the back (cap2 = 0: no second class); the
+// rest go to the block list (as gwork indices).
+// meta = {n_items1, n_block, max keys, -, n_items2}.
 __global__ void partition_warp_kernel(const int4* __restrict__ gwork, int64_t n_work,
-                                      const uint32_t* __restrict__ gstart, uint32_t cap,
-                                      int4* __restrict__ items, int32_t* __restrict__ block_list,
-                                      uint32_t* __restrict__ meta) {
+                                      const uint32_t* __restrict__ gstart, uint32_t cap1,
+                                      uint32_t cap2, int4* __restrict__ items,
+                                      int32_t* __restrict__ block_list, uint32_t* __restrict__ meta) {
     for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < n_work;
          w += int64_t(gridDim.x) * blockDim.x) {
         const int4 wi = gwork[w];
         const uint32_t st = gstart[wi.x];
         const uint32_t len = gstart[wi.x + 1] - st;
         const uint32_t nr = uint32_t(wi.z - wi.y);
-        if (len <= cap && nr < 65536u)
-            items[atomicAdd(meta, 1u)] = make_int4(wi.x, int(st), wi.y, int((nr << 16) | len));
+        const int4 it = make_int4(wi.x, int(st), wi.y, int((nr << 16) | len));
+        if (nr < 65536u && len <= cap1)
+            items[atomicAdd(meta, 1u)] = it;
+        else if (nr < 65536u && len <= cap2)
+            items[n_work - 1 - int64_t(atomicAdd(meta + 4, 1u))] = it;
         else
             block_list[atomicAdd(meta + 1, 1u)] = int32_t(w);
         atomicMax(meta + 2, len);
@@ -1077,13 +1094,13 @@ cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const 
 }
 
 cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
-                                  uint32_t cap, int4* items, int32_t* block_list, uint32_t* meta,
-                                  cudaStream_t s) {
+                                  uint32_t cap1, uint32_t cap2, int4* items, int32_t* block_list,
+                                  uint32_t* meta, cudaStream_t s) {
     if (n_work <= 0) return cudaSuccess;
     int64_t grid = (n_work + 255) / 256;
     const int64_t lim = int64_t(num_sms()) * 16;
     if (grid > lim) grid = lim;
-    partition_warp_kernel<<<unsigned(grid), 256, 0, s>>>(gwork, n_work, gstart, cap, items,
+    partition_warp_kernel<<<unsigned(grid), 256, 0, s>>>(gwork, n_work, gstart, cap1, cap2, items,
                                                          block_list, meta);
     return cudaGetLastError();
 }

@@ -177,15 +177,17 @@ cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t
                                          const unsigned long long* keys, const float4* rec,
                                          float* Mm, unsigned long long* pairs, int transposed,
                                          cudaStream_t s);
-// DirectL groups whose lists hold at most `cap` (512 or 1024) keys: one warp
-// per group (warp-level sort, cp.async batches of 32, transposed evaluation),
+// DirectL groups whose lists hold at most 512 or 1024 keys: one warp per
+// group (warp-level sort, cp.async batches of 32, transposed evaluation),
 // persistent over self-contained items {group, first key, first ray,
-// rays << 16 | keys} made by launch_partition_warp (the other groups' gwork
-// indices go to block_list; meta = {n_items, n_block, max keys}).  The
+// rays << 16 | keys} made by launch_partition_warp: groups of at most cap1
+// keys at the front of `items`, cap1 < keys <= cap2 at the back (from
+// items[n_work - 1] down), the other groups' gwork indices in block_list;
+// meta = {n_items1, n_block, max keys, cursor1, n_items2, cursor2}.  The
 // compositing kernel claims items through *cursor, which must be 0.
 cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
-                                  uint32_t cap, int4* items, int32_t* block_list, uint32_t* meta,
-                                  cudaStream_t s);
+                                  uint32_t cap1, uint32_t cap2, int4* items, int32_t* block_list,
+                                  uint32_t* meta, cudaStream_t s);
 cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* items,
                                        int64_t n_items, uint32_t* cursor, const int2* grouped,
                                        const unsigned long long* keys, const float4* rec,
