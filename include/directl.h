@@ -259,6 +259,81 @@ dl_status dl_last_frame_stats(dl_ctx* ctx, dl_frame_stats* out);
  * tile_w/tile_h/sort_bits are those of the last frame. */
 dl_status dl_stage_totals(dl_ctx* ctx, dl_frame_stats* sum, int32_t* n_frames);
 
+/* ---- Frame batches ---------------------------------------------------
+ * The paper renders one light-field frame at a time; it has no counterpart
+ * for this section, which serves many DirectL frames (any mix of scenes,
+ * displays, view counts and tile shapes) at once.
+ *
+ * A batch owns n_slots frame slots with fixed device capacities.  Every
+ * dl_batch_launch renders one DirectL frame (the frame of Sec. 5, the same
+ * image dl_render_frame gives) for each assigned slot without any host
+ * synchronisation: per slot the projection, group scan, key emission and
+ * list partition; then one persistent launch per compositing class over the
+ * tile lists of all slots together; then each slot's reorder into the
+ * caller's output.  So the sequence can be captured into a CUDA graph
+ * (dl_batch_capture) and replayed.
+ *
+ * Capacities of slot i come from plans[i]: that frame is rendered once
+ * through dl_render_frame (DL_DIRECTL, on `stream`, synchronously); its key
+ * count times `margin` (>= 1) is the slot's key capacity and its longest
+ * tile list times margin, rounded up to a power of two (2048..16384), the
+ * batch's long-list capacity.  Its views x Gaussians, (view, tile) groups,
+ * rays, tile lists and views are the slot's hard limits.  A launched frame
+ * whose keys exceed the key capacity, or that has a tile list longer than
+ * the long-list capacity, is not composited (its output is left as it was)
+ * and is reported by dl_batch_wait.
+ *
+ * Ownership and lifetime: the library owns the batch's memory; the caller
+ * owns each slot's output (device, h*w*3 FP32, the layout of
+ * dl_render_frame) and must keep it valid while launches that write it are
+ * in flight.  Assigned scenes and displays cannot be freed (DL_ERR_INVALID_ARG)
+ * and the context cannot be destroyed while a batch exists.  Calls on one
+ * batch are not thread-safe; the context's other calls may not run
+ * concurrently with them either.  dl_batch_assign, dl_batch_clear and
+ * dl_batch_set_pose wait for the batch's previous launch to finish (they
+ * rewrite the host staging that the launch uploads). */
+typedef struct dl_batch dl_batch;
+typedef struct {
+    int32_t scene_id, display_id;
+    int32_t tile_w, tile_h;  /* 0, 0: the context's DL_DIRECTL tile            */
+    double L0_c2w[16];       /* pose of the sizing frame (row-major 4x4)      */
+} dl_slot_plan;
+dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plans, double margin,
+                          void* stream, dl_batch** out);
+dl_status dl_batch_destroy(dl_batch* b);
+/* Assigns a frame to a slot.  tile_w, tile_h as in dl_slot_plan.
+ * DL_ERR_CAPACITY when the frame exceeds the slot's hard limits. */
+dl_status dl_batch_assign(dl_batch* b, int32_t slot, int32_t scene_id, int32_t display_id,
+                          int32_t tile_w, int32_t tile_h, float* out_dev);
+dl_status dl_batch_clear(dl_batch* b, int32_t slot);
+/* Light-field centre pose of the slot's next frame (row-major 4x4 c2w). */
+dl_status dl_batch_set_pose(dl_batch* b, int32_t slot, const double L0_c2w[16]);
+/* Enqueues one frame for every assigned slot on `stream`; replays the
+ * captured graph when the assignment has not changed since the capture. */
+dl_status dl_batch_launch(dl_batch* b, void* stream);
+/* Captures the launch sequence of the current assignment into a CUDA graph
+ * (stream capture on `stream`, which must not be the legacy default stream);
+ * nothing runs during the capture.  Any assignment change drops the graph. */
+dl_status dl_batch_capture(dl_batch* b, void* stream);
+/* Waits for the last launch.  status (optional, n_slots entries): 0 ok, bit 0
+ * key capacity exceeded, bit 1 a tile list longer than the long-list
+ * capacity (only for assigned slots).  Returns DL_ERR_CAPACITY when a slot
+ * failed. */
+dl_status dl_batch_wait(dl_batch* b, uint32_t* status);
+/* Device bytes the batch holds, and its long-list capacity. */
+dl_status dl_batch_info(dl_batch* b, size_t* bytes, int32_t* long_list_cap);
+
+/* Tile-shape autotuner (no counterpart in the paper): renders the DirectL
+ * frame of (scene, display, pose) with each candidate tile shape
+ * (n_candidates pairs {tile_w, tile_h} in `candidates`; powers of two,
+ * 8..256), `reps` timed frames each after one warm-up frame, on `stream`,
+ * and sets the context's DL_DIRECTL tile to the one with the lowest median
+ * device time.  best[2] receives it; ms (optional, n_candidates entries) the
+ * medians. */
+dl_status dl_autotune_tile(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
+                           const double L0_c2w[16], const int32_t* candidates, int32_t n_candidates,
+                           int32_t reps, void* stream, int32_t* best, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

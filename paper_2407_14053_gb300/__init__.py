@@ -13,12 +13,11 @@ from ._binding import (DL_BF16, DL_DIRECTL, DL_ERR_CAPACITY, DL_ERR_CUDA, DL_ERR
                        dl_gaussians_desc, dl_get_ray_table, dl_get_subpixel_map, dl_get_view_map,
                        dl_last_error_detail, dl_last_frame_stats, dl_load_gaussians,
                        dl_query_footprint, dl_ray_table_static, dl_render_frame, dl_set_display, dl_set_option, dl_set_tile,
-                       dl_stage_totals,
-                       dl_status_string, lib)
+                       dl_stage_totals, dl_status_string, lib)
 
 
 def __getattr__(name):
-    if name == "Renderer":
-        from .renderer import Renderer
-        return Renderer
+    if name in ("Renderer", "Batch"):
+        from . import renderer
+        return getattr(renderer, name)
     raise AttributeError(name)

@@ -54,6 +54,11 @@ class dl_frame_stats(ctypes.Structure):
                                       "ms_ranges", "ms_composite", "ms_interweave", "ms_total")]
 
 
+class dl_slot_plan(ctypes.Structure):
+    _fields_ = [("scene_id", c_int32), ("display_id", c_int32), ("tile_w", c_int32),
+                ("tile_h", c_int32), ("L0_c2w", c_double * 16)]
+
+
 P = ctypes.POINTER
 SIGNATURES = {
     "dl_create": (c_int32, [P(c_void_p), c_int32]),
@@ -78,6 +83,18 @@ SIGNATURES = {
     "dl_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
     "dl_ray_table_static": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                       P(c_int64), c_void_p]),
+    "dl_batch_create": (c_int32, [c_void_p, c_int32, P(dl_slot_plan), c_double, c_void_p,
+                                  P(c_void_p)]),
+    "dl_batch_destroy": (c_int32, [c_void_p]),
+    "dl_batch_assign": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p]),
+    "dl_batch_clear": (c_int32, [c_void_p, c_int32]),
+    "dl_batch_set_pose": (c_int32, [c_void_p, c_int32, P(c_double)]),
+    "dl_batch_launch": (c_int32, [c_void_p, c_void_p]),
+    "dl_batch_capture": (c_int32, [c_void_p, c_void_p]),
+    "dl_batch_wait": (c_int32, [c_void_p, P(ctypes.c_uint32)]),
+    "dl_batch_info": (c_int32, [c_void_p, P(ctypes.c_size_t), P(c_int32)]),
+    "dl_autotune_tile": (c_int32, [c_void_p, c_int32, c_int32, P(c_double), P(c_int32), c_int32,
+                                   c_int32, c_void_p, P(c_int32), P(ctypes.c_float)]),
 }
 
 _lock = threading.Lock()
@@ -240,3 +257,74 @@ def dl_ray_table_static(width: int, height: int, V_ptr: int, src_ptr: int, ray_o
                                      c_void_p(ray_of_ptr), c_void_p(rays_ptr), ctypes.byref(n),
                                      c_void_p(stream)))
     return n.value
+
+
+# ---- frame batches (ctx only supplies the error detail) -----------------
+def dl_batch_create(ctx, plans, margin: float = 1.25, stream: int = 0):
+    """plans: sequence of (scene_id, display_id, tile_w, tile_h, L0_c2w[16])."""
+    arr = (dl_slot_plan * len(plans))()
+    for i, (sid, did, tw, th, L0) in enumerate(plans):
+        arr[i].scene_id, arr[i].display_id, arr[i].tile_w, arr[i].tile_h = sid, did, tw, th
+        arr[i].L0_c2w = (c_double * 16)(*[float(x) for x in L0])
+    h = c_void_p()
+    _check("dl_batch_create", ctx, lib().dl_batch_create(ctx, len(plans), arr, float(margin),
+                                                         c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def dl_batch_destroy(batch, ctx=None) -> None:
+    _check("dl_batch_destroy", ctx, lib().dl_batch_destroy(batch))
+
+
+def dl_batch_assign(batch, slot: int, scene_id: int, display_id: int, tile_w: int, tile_h: int,
+                    out_ptr: int, ctx=None) -> None:
+    _check("dl_batch_assign", ctx, lib().dl_batch_assign(batch, int(slot), int(scene_id),
+                                                         int(display_id), int(tile_w), int(tile_h),
+                                                         c_void_p(out_ptr)))
+
+
+def dl_batch_clear(batch, slot: int, ctx=None) -> None:
+    _check("dl_batch_clear", ctx, lib().dl_batch_clear(batch, int(slot)))
+
+
+def dl_batch_set_pose(batch, slot: int, L0_c2w, ctx=None) -> None:
+    L0 = (c_double * 16)(*[float(x) for x in L0_c2w])
+    _check("dl_batch_set_pose", ctx, lib().dl_batch_set_pose(batch, int(slot), L0))
+
+
+def dl_batch_launch(batch, stream: int = 0, ctx=None) -> None:
+    _check("dl_batch_launch", ctx, lib().dl_batch_launch(batch, c_void_p(stream)))
+
+
+def dl_batch_capture(batch, stream: int, ctx=None) -> None:
+    _check("dl_batch_capture", ctx, lib().dl_batch_capture(batch, c_void_p(stream)))
+
+
+def dl_batch_wait(batch, n_slots: int, ctx=None, raise_on_capacity: bool = True):
+    """Returns the per-slot status words."""
+    st = (ctypes.c_uint32 * n_slots)()
+    r = lib().dl_batch_wait(batch, st)
+    if r != DL_OK and (raise_on_capacity or r != DL_ERR_CAPACITY):
+        _check("dl_batch_wait", ctx, r)
+    return list(st)
+
+
+def dl_batch_info(batch, ctx=None):
+    b = ctypes.c_size_t()
+    c = c_int32()
+    _check("dl_batch_info", ctx, lib().dl_batch_info(batch, ctypes.byref(b), ctypes.byref(c)))
+    return b.value, c.value
+
+
+def dl_autotune_tile(ctx, scene_id: int, display_id: int, L0_c2w, candidates, reps: int = 3,
+                     stream: int = 0):
+    """Returns ((tile_w, tile_h), [median ms per candidate])."""
+    L0 = (c_double * 16)(*[float(x) for x in L0_c2w])
+    flat = [int(v) for c in candidates for v in c]
+    cand = (c_int32 * len(flat))(*flat)
+    best = (c_int32 * 2)()
+    ms = (ctypes.c_float * len(candidates))()
+    _check("dl_autotune_tile", ctx,
+           lib().dl_autotune_tile(ctx, int(scene_id), int(display_id), L0, cand, len(candidates),
+                                  int(reps), c_void_p(stream), best, ms))
+    return (best[0], best[1]), list(ms)

@@ -10,128 +10,11 @@
 #include <string>
 #include <vector>
 
-#include "../../include/directl.h"
-#include "dl_internal.cuh"
-
-namespace dl {
-
-// Grow-only device buffer.
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    cudaError_t reserve(size_t n) {
-        if (n <= bytes) return cudaSuccess;
-        release();
-        const size_t want = n + n / 8 + 256;
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return e;
-        }
-        bytes = want;
-        return cudaSuccess;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <class T>
-    T* as() const {
-        return static_cast<T*>(p);
-    }
-    ~DevBuf() { release(); }
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-};
-
-struct Scene {
-    int64_t n = 0;
-    int32_t sh_degree = 0, dtype = DL_F32;
-    DevBuf mean, log_scale, rot, opacity, sh;
-};
-
-struct TileGroups {
-    int32_t tw = 0, th = 0, ntx = 0, nty = 0, ntiles = 0;
-    int64_t n_work = 0;   // <= 128-ray chunks (global radix path)
-    int64_t n_gwork = 0;  // groups holding rays (binned path)
-    DevBuf grouped, work, gwork;
-};
-
-struct RaySet {
-    bool built = false;
-    int64_t n_rays = 0;
-    DevBuf src, ray_of, ray_view, ray_pix;
-    std::map<int64_t, std::unique_ptr<TileGroups>> groups;
-};
-
-struct Display {
-    dl_display_params prm{};
-    DisplayQ q{};
-    DevBuf V;
-    RaySet rep;    // Alg. 2 assignment (or identity when repurpose == 0)
-    RaySet ident;  // identity assignment, built on first DL_REQUIRED_ONLY frame
-};
-
-// Events around the stages of one frame (see dl_render_frame).
-constexpr int kStageEvents = 9;
-struct StageEvents {
-    cudaEvent_t e[kStageEvents] = {};
-};
-struct PendingFrame {
-    StageEvents* ev;
-    int64_t n_keys, n_rays;
-    int32_t launches;
-    int64_t lists_small, lists_large, max_list;
-};
-
-struct Workspace {
-    DevBuf cams, rec, count, offset, scan_tmp, keys[2], vals[2], ranges, radix_tmp, Mm, out, small,
-        pairs, gcount, gstart, gfill, lists, gscan_tmp, raycol;
-    unsigned long long* h_total = nullptr;  // pinned, 256 bytes (copy of `small`)
-    size_t last_bytes = 0;
-    std::vector<StageEvents*> ev_free;
-    std::vector<PendingFrame> pending;
-    ~Workspace() {
-        if (h_total) cudaFreeHost(h_total);
-        for (auto& f : pending) ev_free.push_back(f.ev);
-        for (StageEvents* s : ev_free) {
-            for (auto& e : s->e)
-                if (e) cudaEventDestroy(e);
-            delete s;
-        }
-    }
-    size_t footprint() const {
-        size_t b = cams.bytes + rec.bytes + count.bytes + offset.bytes + scan_tmp.bytes + ranges.bytes +
-                   radix_tmp.bytes + Mm.bytes + out.bytes + small.bytes + gcount.bytes + gstart.bytes +
-                   gfill.bytes + lists.bytes + gscan_tmp.bytes + raycol.bytes;
-        for (int i = 0; i < 2; ++i) b += keys[i].bytes + vals[i].bytes;
-        return b;
-    }
-};
-
-}  // namespace dl
-
-struct dl_ctx {
-    int32_t device = 0;
-    std::string err;
-    int32_t next_id = 1;
-    std::map<int32_t, std::unique_ptr<dl::Scene>> scenes;
-    std::map<int32_t, std::unique_ptr<dl::Display>> displays;
-    dl::Workspace ws;
-    int32_t tile[3][2] = {{32, 32}, {16, 16}, {32, 32}};
-    int32_t sort_mode = DL_SORT_AUTO;
-    int32_t eval_transposed[3] = {1, 0, 1};  // per mode
-    int32_t warp_cap = 512;
-    bool timing = false;
-    dl_frame_stats stats{};
-};
+#include "host.h"
 
 using namespace dl;
 
-namespace {
+namespace dl {
 
 dl_status fail(dl_ctx* c, dl_status s, const char* fmt, ...) {
     if (c) {
@@ -149,12 +32,6 @@ dl_status cuda_fail(dl_ctx* c, cudaError_t e, const char* what) {
     const dl_status s = (e == cudaErrorMemoryAllocation) ? DL_ERR_OOM : DL_ERR_CUDA;
     return fail(c, s, "%s: %s", what, cudaGetErrorString(e));
 }
-
-#define DL_CK(expr, what)                                   \
-    do {                                                    \
-        cudaError_t e_ = (expr);                            \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
-    } while (0)
 
 int bits_for(int64_t n) {  // bits to hold values 0..n-1
     int b = 0;
@@ -375,6 +252,29 @@ dl_status upload_cams(dl_ctx* ctx, const std::vector<Cam>& cams, cudaStream_t s)
     return DL_OK;
 }
 
+// Pinhole camera of Sec. 6: f = (w/2) / tan(fov_x/2), principal point (w/2,
+// h/2); the Jacobian's clamp at 1.3 tan(fov/2) (3DGS practice).
+ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, int32_t th) {
+    const int32_t w = D.q.w, h = D.q.h;
+    const double pi = 3.14159265358979323846;
+    const double focal = 0.5 * w / std::tan(0.5 * D.prm.fov_x_deg * pi / 180.0);
+    ProjectParams pp{};
+    pp.n = S.n;
+    pp.sh_degree = S.sh_degree;
+    pp.width = w;
+    pp.height = h;
+    pp.focal = float(focal);
+    pp.half_w = 0.5f * float(w);
+    pp.half_h = 0.5f * float(h);
+    pp.lim_x = float(1.3 * (0.5 * w / focal));
+    pp.lim_y = float(1.3 * (0.5 * h / focal));
+    pp.tile_w = tw;
+    pp.tile_h = th;
+    pp.ntx = (w + tw - 1) / tw;
+    pp.nty = (h + th - 1) / th;
+    return pp;
+}
+
 dl_status check_ctx(dl_ctx* ctx) {
     if (!ctx) return DL_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -393,7 +293,7 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
-}  // namespace
+}  // namespace dl
 
 extern "C" {
 
@@ -437,6 +337,8 @@ dl_status dl_create(dl_ctx** out, int32_t device) {
 
 dl_status dl_destroy(dl_ctx* ctx) {
     if (!ctx) return DL_ERR_INVALID_ARG;
+    if (ctx->n_batches > 0)
+        return fail(ctx, DL_ERR_INVALID_ARG, "%d batch(es) still exist", ctx->n_batches);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     delete ctx;
@@ -509,6 +411,9 @@ dl_status dl_free_scene(dl_ctx* ctx, int32_t scene_id) {
     if (st) return st;
     auto it = ctx->scenes.find(scene_id);
     if (it == ctx->scenes.end()) return fail(ctx, DL_ERR_NOT_FOUND, "scene %d", scene_id);
+    if (it->second->in_use)
+        return fail(ctx, DL_ERR_INVALID_ARG, "scene %d is assigned to %d batch slot(s)", scene_id,
+                    it->second->in_use);
     cudaDeviceSynchronize();
     ctx->scenes.erase(it);
     return DL_OK;
@@ -543,6 +448,9 @@ dl_status dl_free_display(dl_ctx* ctx, int32_t display_id) {
     if (st) return st;
     auto it = ctx->displays.find(display_id);
     if (it == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    if (it->second->in_use)
+        return fail(ctx, DL_ERR_INVALID_ARG, "display %d is assigned to %d batch slot(s)",
+                    display_id, it->second->in_use);
     cudaDeviceSynchronize();
     ctx->displays.erase(it);
     return DL_OK;
@@ -803,22 +711,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     make_cams(D.prm, L0_c2w, cams);
     st = upload_cams(ctx, cams, s);
     if (st) return st;
-    const double pi = 3.14159265358979323846;
-    const double focal = 0.5 * w / std::tan(0.5 * D.prm.fov_x_deg * pi / 180.0);
-    ProjectParams pp{};
-    pp.n = S.n;
-    pp.sh_degree = S.sh_degree;
-    pp.width = w;
-    pp.height = h;
-    pp.focal = float(focal);
-    pp.half_w = 0.5f * float(w);
-    pp.half_h = 0.5f * float(h);
-    pp.lim_x = float(1.3 * (0.5 * w / focal));
-    pp.lim_y = float(1.3 * (0.5 * h / focal));
-    pp.tile_w = tw;
-    pp.tile_h = th;
-    pp.ntx = (w + tw - 1) / tw;
-    pp.nty = (h + th - 1) / th;
+    const ProjectParams pp = make_project_params(S, D, tw, th);
     const int64_t ntiles = int64_t(pp.ntx) * pp.nty;
     const int64_t ne = int64_t(nv) * S.n;
     if (ne >= (int64_t(1) << 31)) return fail(ctx, DL_ERR_CAPACITY, "views x Gaussians >= 2^31");
@@ -856,7 +749,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     const bool warp_path = mode != DL_STANDARD && ctx->warp_cap > 0;
     if (warp_path) {
         DL_CK(launch_partition_warp(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(ctx->warp_cap),
-                                    ctx->warp_cap < 1024 ? 1024u : 0u, items, large_list, d_meta, s),
+                                    ctx->warp_cap < 1024 ? 1024u : 0u, items, large_list, d_meta,
+                                    nullptr, 0u, nullptr, s),
               "partition");
     } else {
         DL_CK(launch_partition(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(kSmallCap), small_list,
@@ -920,7 +814,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         DL_CK(mark(3), "event");
         DL_CK(launch_emit_binned(pp, nv, W.rec.as<float4>(), W.count.as<uint32_t>(),
                                  W.gstart.as<uint32_t>(), W.gfill.as<uint32_t>(),
-                                 W.keys[0].as<unsigned long long>(), s),
+                                 W.keys[0].as<unsigned long long>(), nullptr, 0u, nullptr, s),
               "emit binned");
         DL_CK(mark(4), "event");
         DL_CK(mark(5), "event");
@@ -935,23 +829,43 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                                                W.gstart.as<uint32_t>(), keys, W.rec.as<float4>(), Mm,
                                                pairs, ctx->eval_transposed[mode], s),
                   "composite full (large lists)");
+        } else if (warp_path) {
+            // one frame through the frame-batched persistent kernels
+            FrameDesc fd{};
+            fd.cp = cp;
+            fd.grouped = G->grouped.as<int2>();
+            fd.keys = keys;
+            fd.rec = W.rec.as<float4>();
+            fd.raycol = raycol;
+            fd.items = items;
+            fd.gwork = G->gwork.as<int4>();
+            fd.block_list = large_list;
+            fd.gstart = W.gstart.as<uint32_t>();
+            fd.meta = d_meta;
+            fd.status = d_meta + 7;
+            fd.n_work = n_work;
+            DL_CK(W.fdesc.reserve(sizeof(FrameDesc)), "alloc frame table");
+            // pageable source: staged by the call, so fd may go out of scope
+            DL_CK(cudaMemcpyAsync(W.fdesc.p, &fd, sizeof(FrameDesc), cudaMemcpyHostToDevice, s),
+                  "copy frame table");
+            const FrameDesc* dF = W.fdesc.as<FrameDesc>();
+            int64_t* prefix = reinterpret_cast<int64_t*>(W.small.as<char>() + 192);
+            DL_CK(launch_batch_prefix(dF, 1, prefix, s), "prefix");
+            DL_CK(launch_composite_rays_warp(ctx->warp_cap, 0, dF, prefix, 1, n_small, d_meta + 3,
+                                             pairs, s),
+                  "composite rays (warp per group)");
+            DL_CK(launch_composite_rays_warp(1024, 1, dF, prefix, 1, n_mid, d_meta + 5, pairs, s),
+                  "composite rays (warp per group, 1024 keys)");
+            DL_CK(launch_composite_rays_block(cap_large, dF, prefix, 1, n_large, d_meta + 6, pairs,
+                                              ctx->eval_transposed[mode], s),
+                  "composite rays (block per group)");
+            launches += 1;
         } else {
-            if (warp_path) {
-                DL_CK(launch_composite_rays_warp(cp, ctx->warp_cap, items, n_small, d_meta + 3,
-                                                 G->grouped.as<int2>(), keys, W.rec.as<float4>(),
-                                                 raycol, pairs, s),
-                      "composite rays (warp per group)");
-                DL_CK(launch_composite_rays_warp(cp, 1024, items + (n_work - n_mid), n_mid,
-                                                 d_meta + 5, G->grouped.as<int2>(), keys,
-                                                 W.rec.as<float4>(), raycol, pairs, s),
-                      "composite rays (warp per group, 1024 keys)");
-            } else {
-                DL_CK(launch_composite_rays_binned(cp, G->gwork.as<int4>(), small_list, n_small,
-                                                   kSmallCap, G->grouped.as<int2>(),
-                                                   W.gstart.as<uint32_t>(), keys, W.rec.as<float4>(),
-                                                   raycol, pairs, ctx->eval_transposed[mode], s),
-                      "composite rays (small lists)");
-            }
+            DL_CK(launch_composite_rays_binned(cp, G->gwork.as<int4>(), small_list, n_small, kSmallCap,
+                                               G->grouped.as<int2>(), W.gstart.as<uint32_t>(), keys,
+                                               W.rec.as<float4>(), raycol, pairs,
+                                               ctx->eval_transposed[mode], s),
+                  "composite rays (small lists)");
             DL_CK(launch_composite_rays_binned(cp, G->gwork.as<int4>(), large_list, n_large, cap_large,
                                                G->grouped.as<int2>(), W.gstart.as<uint32_t>(), keys,
                                                W.rec.as<float4>(), raycol, pairs,
@@ -1005,7 +919,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     if (mode == DL_STANDARD) {
         DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), Mm, dst, s), "interweave");
     } else {
-        DL_CK(launch_reorder(R->ray_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst, s), "reorder");
+        DL_CK(launch_reorder(R->ray_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst, nullptr, s),
+              "reorder");
     }
     launches += 1;
     DL_CK(mark(8), "event");

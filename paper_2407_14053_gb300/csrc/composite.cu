@@ -875,48 +875,77 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Persistent: one resident warp per slot takes items until none is left; an
-// item is {group, first key, first ray, rays << 16 | keys}.  While one group
-// is composited, the next item is loaded and its keys and rays are
-// prefetched into L2.  *cursor must be 0 at launch.
+// Index of the frame whose class range holds item i: the last f with
+// prefix[f] <= i (prefix ascending, prefix[0] = 0).
+__device__ __forceinline__ int frame_of(const int64_t* __restrict__ prefix, int n_frames, int64_t i) {
+    int lo = 0, hi = n_frames - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Item i of class cls (0: front of items, 1: back of items) across frames.
+__device__ __forceinline__ int4 batch_item(const FrameDesc* __restrict__ F,
+                                           const int64_t* __restrict__ prefix, int n_frames, int cls,
+                                           int64_t i, int& f) {
+    f = frame_of(prefix, n_frames, i);
+    const int64_t j = i - __ldg(prefix + f);
+    const int4* items = F[f].items;
+    return cls == 0 ? items[j] : items[F[f].n_work - 1 - j];
+}
+
+// Persistent: resident warps take items until none is left (the first
+// n_warps by warp id, the rest claimed from *cursor: groups differ widely in
+// cost); an item is {group, first key, first ray, rays << 16 | keys} of
+// frame f.  While one group is composited, the next item is loaded and its
+// keys and rays are prefetched into L2.
 template <int CAP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ items, int64_t n_items,
-                           uint32_t* __restrict__ cursor, const int2* __restrict__ grouped,
-                           const unsigned long long* __restrict__ keys,
-                           const float4* __restrict__ rec, float* __restrict__ raycol,
+composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __restrict__ prefix,
+                           int n_frames, int cls, uint32_t* __restrict__ cursor,
                            unsigned long long* __restrict__ pairs) {
     extern __shared__ __align__(16) unsigned char wsm_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP>& W = reinterpret_cast<WarpSmem<CAP>*>(wsm_raw)[warp];
+    const int64_t n_items = __ldg(prefix + n_frames);
     const int64_t n_warps = int64_t(gridDim.x) * kWarpsPerBlock;
     int64_t item = int64_t(blockIdx.x) * kWarpsPerBlock + warp;
     uint32_t evals = 0, blended = 0;
-    int4 cur = item < n_items ? items[item] : make_int4(0, 0, 0, 0);
+    int fcur = 0;
+    int4 cur = item < n_items ? batch_item(F, prefix, n_frames, cls, item, fcur) : make_int4(0, 0, 0, 0);
     while (item < n_items) {
-        // next item: the first n_warps items are taken by warp id, the rest
-        // claimed from the cursor (groups differ widely in cost)
         uint32_t c = 0;
         if (lane == 0) c = atomicAdd(cursor, 1u);
         const int64_t nxt = n_warps + int64_t(__shfl_sync(0xffffffffu, c, 0));
-        const int4 next = nxt < n_items ? items[nxt] : make_int4(0, 0, 0, 0);
+        int fnxt = 0;
+        const int4 next = nxt < n_items ? batch_item(F, prefix, n_frames, cls, nxt, fnxt)
+                                        : make_int4(0, 0, 0, 0);
+        const FrameDesc& d = F[fcur];
+        const int2* __restrict__ grouped = d.grouped;
+        const float4* __restrict__ rec = d.rec;
+        float* __restrict__ raycol = d.raycol;
         const int group = cur.x;
         const uint32_t start = uint32_t(cur.y);
         const int rbeg = cur.z, nrays = int(uint32_t(cur.w) >> 16), len = cur.w & 0xFFFF;
-        const int v = group / p.ntiles;
-        warp_sort<CAP>(keys, start, len, W);
+        const int v = group / d.cp.ntiles;
+        const float half_w = d.cp.half_w, half_h = d.cp.half_h;
+        warp_sort<CAP>(d.keys, start, len, W);
         if (nxt < n_items) {  // warm L2 for the next group
+            const FrameDesc& dn = F[fnxt];
             const int nlen = next.w & 0xFFFF, nr = int(uint32_t(next.w) >> 16);
-            for (int i = lane * 16; i < nlen; i += 32 * 16) prefetch_l2(keys + uint32_t(next.y) + i);
-            for (int i = lane * 16; i < nr; i += 32 * 16) prefetch_l2(grouped + next.z + i);
+            for (int i = lane * 16; i < nlen; i += 32 * 16) prefetch_l2(dn.keys + uint32_t(next.y) + i);
+            for (int i = lane * 16; i < nr; i += 32 * 16) prefetch_l2(dn.grouped + next.z + i);
         }
-        const int64_t vbase = int64_t(v) * p.n;
+        const int64_t vbase = int64_t(v) * d.cp.n;
         for (int r0 = 0; r0 < nrays; r0 += 32) {
             const int rid = r0 + lane;
             const bool active = rid < nrays;
             const int2 ray = active ? grouped[rbeg + rid] : make_int2(0, -1);
             const int col = int(uint32_t(ray.x) & 0xFFFFu), row = int(uint32_t(ray.x) >> 16);
-            const float px = float(col) - p.half_w, py = float(row) - p.half_h;
+            const float px = float(col) - half_w, py = float(row) - half_h;
             int bx0, bx1, by0, by1;
             warp_box(active, col, row, bx0, bx1, by0, by1);
             Acc a{1.f, 0.f, 0.f, 0.f, 0u};
@@ -932,8 +961,83 @@ composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ items, in
         }
         item = nxt;
         cur = next;
+        fcur = fnxt;
     }
     if (pairs) count_pairs(pairs, evals, blended);
+}
+
+// Block class across frames: one block per group list longer than 1024 keys
+// (sorted in shared memory up to `cap` keys), persistent like the warp
+// classes.
+template <bool TRANSPOSED>
+__global__ void __launch_bounds__(kBinnedThreads)
+composite_rays_block_kernel(const FrameDesc* __restrict__ F, const int64_t* __restrict__ prefix,
+                            int n_frames, int cap, uint32_t* __restrict__ cursor,
+                            unsigned long long* __restrict__ pairs) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    __shared__ int64_t s_item;
+    const int nthr = blockDim.x;
+    const BinnedSmem S = carve_binned(smb, cap, nthr);
+    const int64_t n_items = __ldg(prefix + n_frames);
+    uint32_t evals = 0, blended = 0;
+    int64_t item = blockIdx.x;
+    while (item < n_items) {
+        const int f = frame_of(prefix, n_frames, item);
+        const FrameDesc& d = F[f];
+        const int4 wi = d.gwork[d.block_list[item - __ldg(prefix + f)]];
+        const uint32_t start = d.gstart[wi.x];
+        const int len = int(d.gstart[wi.x + 1] - start);
+        if (len > cap) {
+            if (threadIdx.x == 0) atomicOr(d.status, 2u);
+        } else {
+            const int v = wi.x / d.cp.ntiles;
+            block_sort<0>(d.keys, start, len, cap, S.sk, S.cnt);
+            const int64_t vbase = int64_t(v) * d.cp.n;
+            for (int r0 = wi.y; r0 < wi.z; r0 += nthr) {
+                const int rid = r0 + int(threadIdx.x);
+                const bool active = rid < wi.z;
+                const int2 ray = active ? d.grouped[rid] : make_int2(0, -1);
+                const int col = int(uint32_t(ray.x) & 0xFFFFu), row = int(uint32_t(ray.x) >> 16);
+                const float px = float(col) - d.cp.half_w, py = float(row) - d.cp.half_h;
+                int bx0, bx1, by0, by1;
+                warp_box(active, col, row, bx0, bx1, by0, by1);
+                Acc a{1.f, 0.f, 0.f, 0.f, 0u};
+                bool done = !active;
+                stream_list<TRANSPOSED>(S.sk, len, vbase, d.rec, S.buf, S.wbuf, a, done, evals, px,
+                                        py, bx0, bx1, by0, by1);
+                if (active) {
+                    float* o = d.raycol + 3 * int64_t(ray.y);
+                    o[0] = a.c0;
+                    o[1] = a.c1;
+                    o[2] = a.c2;
+                }
+                blended += a.blended;
+            }
+        }
+        __syncthreads();  // shared memory reused by the next item
+        if (threadIdx.x == 0) s_item = int64_t(gridDim.x) + int64_t(atomicAdd(cursor, 1u));
+        __syncthreads();
+        item = s_item;
+    }
+    if (pairs) count_pairs(pairs, evals, blended);
+}
+
+__global__ void batch_prefix_kernel(const FrameDesc* __restrict__ F, int n_frames,
+                                    int64_t* __restrict__ prefix) {
+    if (threadIdx.x != 0) return;
+    int64_t a = 0, b = 0, c = 0;
+    const int stride = n_frames + 1;
+    for (int f = 0; f < n_frames; ++f) {
+        prefix[f] = a;
+        prefix[stride + f] = b;
+        prefix[2 * stride + f] = c;
+        a += F[f].meta[0];
+        b += F[f].meta[4];
+        c += F[f].meta[1];
+    }
+    prefix[n_frames] = a;
+    prefix[stride + n_frames] = b;
+    prefix[2 * stride + n_frames] = c;
 }
 
 // Items of the warp classes: DirectL groups with fewer than 65536 rays and
@@ -944,7 +1048,13 @@ composite_rays_warp_kernel(CompositeParams p, const int4* __restrict__ items, in
 __global__ void partition_warp_kernel(const int4* __restrict__ gwork, int64_t n_work,
                                       const uint32_t* __restrict__ gstart, uint32_t cap1,
                                       uint32_t cap2, int4* __restrict__ items,
-                                      int32_t* __restrict__ block_list, uint32_t* __restrict__ meta) {
+                                      int32_t* __restrict__ block_list, uint32_t* __restrict__ meta,
+                                      const uint32_t* __restrict__ total_keys, uint32_t key_cap,
+                                      uint32_t* __restrict__ status) {
+    if (total_keys && *total_keys > key_cap) {  // keys were not emitted
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 1u);
+        return;
+    }
     for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < n_work;
          w += int64_t(gridDim.x) * blockDim.x) {
         const int4 wi = gwork[w];
@@ -977,7 +1087,8 @@ __global__ void partition_kernel(const int4* __restrict__ gwork, int64_t n_work,
 }
 
 __global__ void reorder_kernel(const uint32_t* __restrict__ ray_of, const float* __restrict__ raycol,
-                               int64_t n, float* __restrict__ out) {
+                               int64_t n, float* __restrict__ out, const uint32_t* __restrict__ skip) {
+    if (skip && *skip) return;  // the frame was not composited
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x)
         out[i] = raycol[3 * int64_t(ray_of[i]) + (i % 3)];
@@ -1068,40 +1179,69 @@ cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t
     return regs ? go(composite_full_binned_kernel<false, 4>) : go(composite_full_binned_kernel<false, 0>);
 }
 
-cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* items,
-                                       int64_t n_items, uint32_t* cursor, const int2* grouped,
-                                       const unsigned long long* keys, const float4* rec,
-                                       float* raycol, unsigned long long* pairs, cudaStream_t s) {
-    if (n_items <= 0) return cudaSuccess;
+namespace {
+template <class K>
+cudaError_t launch_persistent(K kernel, int threads, size_t smem, int64_t max_blocks,
+                              const FrameDesc* frames, const int64_t* prefix, int32_t n_frames,
+                              int extra, uint32_t* cursor, unsigned long long* pairs, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = int64_t(num_sms()) * (per_sm > 0 ? per_sm : 1);
+    if (blocks > max_blocks) blocks = max_blocks;
+    kernel<<<unsigned(blocks), threads, smem, s>>>(frames, prefix, n_frames, extra, cursor, pairs);
+    return cudaGetLastError();
+}
+}  // namespace
 
-    auto go = [&](auto kernel, size_t smem) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerBlock * 32, smem);
-        if (e != cudaSuccess) return e;
-        int64_t blocks = int64_t(num_sms()) * (per_sm > 0 ? per_sm : 1);
-        const int64_t need = (n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        if (blocks > need) blocks = need;
-        kernel<<<unsigned(blocks), kWarpsPerBlock * 32, smem, s>>>(p, items, n_items, cursor, grouped,
-                                                                   keys, rec, raycol, pairs);
-        return cudaGetLastError();
-    };
+cudaError_t launch_batch_prefix(const FrameDesc* frames, int32_t n_frames, int64_t* prefix,
+                                cudaStream_t s) {
+    batch_prefix_kernel<<<1, 32, 0, s>>>(frames, n_frames, prefix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_rays_warp(int cap, int cls, const FrameDesc* frames,
+                                       const int64_t* prefix, int32_t n_frames, int64_t max_items,
+                                       uint32_t* cursor, unsigned long long* pairs, cudaStream_t s) {
+    if (max_items <= 0 || n_frames <= 0) return cudaSuccess;
+    const int64_t need = (max_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t* pc = prefix + int64_t(cls) * (n_frames + 1);
     if (cap == 1024)
-        return go(composite_rays_warp_kernel<1024>, kWarpsPerBlock * sizeof(WarpSmem<1024>));
-    return go(composite_rays_warp_kernel<512>, kWarpsPerBlock * sizeof(WarpSmem<512>));
+        return launch_persistent(composite_rays_warp_kernel<1024>, kWarpsPerBlock * 32,
+                                 kWarpsPerBlock * sizeof(WarpSmem<1024>), need, frames, pc, n_frames,
+                                 cls, cursor, pairs, s);
+    return launch_persistent(composite_rays_warp_kernel<512>, kWarpsPerBlock * 32,
+                             kWarpsPerBlock * sizeof(WarpSmem<512>), need, frames, pc, n_frames, cls,
+                             cursor, pairs, s);
+}
+
+cudaError_t launch_composite_rays_block(int block_cap, const FrameDesc* frames,
+                                        const int64_t* prefix, int32_t n_frames, int64_t max_items,
+                                        uint32_t* cursor, unsigned long long* pairs, int transposed,
+                                        cudaStream_t s) {
+    if (max_items <= 0 || n_frames <= 0) return cudaSuccess;
+    const size_t smem = binned_smem_bytes(block_cap, kBinnedThreads);
+    const int64_t* p2 = prefix + 2 * (n_frames + 1);
+    if (transposed)
+        return launch_persistent(composite_rays_block_kernel<true>, kBinnedThreads, smem, max_items,
+                                 frames, p2, n_frames, block_cap, cursor, pairs, s);
+    return launch_persistent(composite_rays_block_kernel<false>, kBinnedThreads, smem, max_items,
+                             frames, p2, n_frames, block_cap, cursor, pairs, s);
 }
 
 cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
                                   uint32_t cap1, uint32_t cap2, int4* items, int32_t* block_list,
-                                  uint32_t* meta, cudaStream_t s) {
+                                  uint32_t* meta, const uint32_t* total_keys, uint32_t key_cap,
+                                  uint32_t* status, cudaStream_t s) {
     if (n_work <= 0) return cudaSuccess;
     int64_t grid = (n_work + 255) / 256;
     const int64_t lim = int64_t(num_sms()) * 16;
     if (grid > lim) grid = lim;
     partition_warp_kernel<<<unsigned(grid), 256, 0, s>>>(gwork, n_work, gstart, cap1, cap2, items,
-                                                         block_list, meta);
+                                                         block_list, meta, total_keys, key_cap,
+                                                         status);
     return cudaGetLastError();
 }
 
@@ -1118,12 +1258,12 @@ cudaError_t launch_partition(const int4* gwork, int64_t n_work, const uint32_t* 
 }
 
 cudaError_t launch_reorder(const uint32_t* ray_of, const float* raycol, int64_t n, float* out,
-                           cudaStream_t s) {
+                           const uint32_t* skip, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t grid = (n + 255) / 256;
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
-    reorder_kernel<<<unsigned(grid), 256, 0, s>>>(ray_of, raycol, n, out);
+    reorder_kernel<<<unsigned(grid), 256, 0, s>>>(ray_of, raycol, n, out, skip);
     return cudaGetLastError();
 }
 

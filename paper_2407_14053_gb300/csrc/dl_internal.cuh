@@ -113,9 +113,12 @@ cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectPar
                            const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s);
 // Keys depth << 32 | Gaussian into their group's slice [gstart[g], gstart[g+1])
 // (gfill zeroed by the caller).
+// total_keys (optional) = gstart + n_groups: when it exceeds key_cap no key is
+// written and *status |= 1.
 cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const float4* rec,
                                const uint32_t* count, const uint32_t* gstart, uint32_t* gfill,
-                               unsigned long long* keys, cudaStream_t s);
+                               unsigned long long* keys, const uint32_t* total_keys,
+                               uint32_t key_cap, uint32_t* status, cudaStream_t s);
 cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* rec,
                              const uint32_t* count, const uint32_t* offset,
                              unsigned long long* keys, uint32_t* vals, cudaStream_t s);
@@ -153,8 +156,9 @@ cudaError_t launch_composite_rays(const CompositeParams& p, const int4* work, in
                                   cudaStream_t s);
 // Encoded image from ray colours (Sec. 4 step (3), Sec. 6: the channel
 // reorder by precomputed indices): out[i] = raycol[3 ray_of[i] + i mod 3].
+// Nothing is written when skip (optional, device) holds a nonzero word.
 cudaError_t launch_reorder(const uint32_t* ray_of, const float* raycol, int64_t n_subpixels,
-                           float* out, cudaStream_t s);
+                           float* out, const uint32_t* skip, cudaStream_t s);
 // Standard paradigm: every pixel of every view into Mm (nv x h x w x 3).
 cudaError_t launch_composite_full(const CompositeParams& p, int32_t nv, const uint2* ranges,
                                   const uint32_t* vals, const float4* rec, float* Mm,
@@ -183,15 +187,46 @@ cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t
 // rays << 16 | keys} made by launch_partition_warp: groups of at most cap1
 // keys at the front of `items`, cap1 < keys <= cap2 at the back (from
 // items[n_work - 1] down), the other groups' gwork indices in block_list;
-// meta = {n_items1, n_block, max keys, cursor1, n_items2, cursor2}.  The
-// compositing kernel claims items through *cursor, which must be 0.
+// meta = {n_items1, n_block, max keys, -, n_items2}.  When *total_keys
+// (gstart[n_groups]) exceeds key_cap nothing is written and status |= 1.
 cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
                                   uint32_t cap1, uint32_t cap2, int4* items, int32_t* block_list,
-                                  uint32_t* meta, cudaStream_t s);
-cudaError_t launch_composite_rays_warp(const CompositeParams& p, int cap, const int4* items,
-                                       int64_t n_items, uint32_t* cursor, const int2* grouped,
-                                       const unsigned long long* keys, const float4* rec,
-                                       float* raycol, unsigned long long* pairs, cudaStream_t s);
+                                  uint32_t* meta, const uint32_t* total_keys, uint32_t key_cap,
+                                  uint32_t* status, cudaStream_t s);
+
+// One DirectL frame's compositing inputs, as read by the frame-batched
+// persistent kernels (device memory, one entry per frame).
+struct FrameDesc {
+    CompositeParams cp;
+    const int2* grouped;              // {pixel, ray id} per grouped ray
+    const unsigned long long* keys;   // binned keys (slices by gstart)
+    const float4* rec;                // records, view-major
+    float* raycol;                    // 3 floats per ray id
+    const int4* items;                // launch_partition_warp output
+    const int4* gwork;                // {group, ray begin, ray end, -}
+    const int32_t* block_list;
+    const uint32_t* gstart;
+    const uint32_t* meta;             // {n_items1, n_block, max, -, n_items2}
+    uint32_t* status;                 // bit 0 keys overflow, bit 1 list longer than the block cap
+    int64_t n_work;
+};
+// prefix[c * (n_frames + 1) + f] = items of class c (0: <= 512 keys,
+// 1: <= 1024 keys, 2: block list) in frames before f; one block.
+cudaError_t launch_batch_prefix(const FrameDesc* frames, int32_t n_frames, int64_t* prefix,
+                                cudaStream_t s);
+// Warp class cls (0: items at the front, 1: at the back) over every frame's
+// items with a warp sort capacity of cap (512 or 1024) keys; persistent,
+// claiming items through *cursor (0 at launch).  Grid: resident warps, at
+// most max_items / 4 blocks (max_items: an upper bound on the class's items).
+cudaError_t launch_composite_rays_warp(int cap, int cls, const FrameDesc* frames,
+                                       const int64_t* prefix, int32_t n_frames, int64_t max_items,
+                                       uint32_t* cursor, unsigned long long* pairs, cudaStream_t s);
+// Block class (lists longer than 1024 keys, up to block_cap, a power of two
+// <= 16384; longer lists set status bit 1 and are skipped), persistent.
+cudaError_t launch_composite_rays_block(int block_cap, const FrameDesc* frames,
+                                        const int64_t* prefix, int32_t n_frames, int64_t max_items,
+                                        uint32_t* cursor, unsigned long long* pairs, int transposed,
+                                        cudaStream_t s);
 // Splits work entries by their group's key count: <= small_cap -> small
 // list, else large list; meta = {n_small, n_large, max count}.  gwork NULL:
 // the entries are the groups 0..n_work-1 themselves.

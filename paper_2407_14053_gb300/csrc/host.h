@@ -1,0 +1,153 @@
+// Host-side state of the C ABI (contexts, scenes, displays, workspaces) and
+// the helpers that api.cu and batch.cu share.  Host code only.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/directl.h"
+#include "dl_internal.cuh"
+
+namespace dl {
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        release();
+        const size_t want = n + n / 8 + 256;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return e;
+        }
+        bytes = want;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+struct Scene {
+    int64_t n = 0;
+    int32_t sh_degree = 0, dtype = DL_F32;
+    int32_t in_use = 0;  // batch slots holding this scene
+    DevBuf mean, log_scale, rot, opacity, sh;
+};
+
+struct TileGroups {
+    int32_t tw = 0, th = 0, ntx = 0, nty = 0, ntiles = 0;
+    int64_t n_work = 0;   // <= 128-ray chunks (global radix path)
+    int64_t n_gwork = 0;  // groups holding rays (binned path)
+    DevBuf grouped, work, gwork;
+};
+
+struct RaySet {
+    bool built = false;
+    int64_t n_rays = 0;
+    DevBuf src, ray_of, ray_view, ray_pix;
+    std::map<int64_t, std::unique_ptr<TileGroups>> groups;
+};
+
+struct Display {
+    int32_t in_use = 0;  // batch slots holding this display
+    dl_display_params prm{};
+    DisplayQ q{};
+    DevBuf V;
+    RaySet rep;    // Alg. 2 assignment (or identity when repurpose == 0)
+    RaySet ident;  // identity assignment, built on first DL_REQUIRED_ONLY frame
+};
+
+// Events around the stages of one frame (see dl_render_frame).
+constexpr int kStageEvents = 9;
+struct StageEvents {
+    cudaEvent_t e[kStageEvents] = {};
+};
+struct PendingFrame {
+    StageEvents* ev;
+    int64_t n_keys, n_rays;
+    int32_t launches;
+    int64_t lists_small, lists_large, max_list;
+};
+
+struct Workspace {
+    DevBuf cams, rec, count, offset, scan_tmp, keys[2], vals[2], ranges, radix_tmp, Mm, out, small,
+        pairs, gcount, gstart, gfill, lists, gscan_tmp, raycol, fdesc;
+    unsigned long long* h_total = nullptr;  // pinned, 256 bytes (copy of `small`)
+    size_t last_bytes = 0;
+    std::vector<StageEvents*> ev_free;
+    std::vector<PendingFrame> pending;
+    ~Workspace() {
+        if (h_total) cudaFreeHost(h_total);
+        for (auto& f : pending) ev_free.push_back(f.ev);
+        for (StageEvents* s : ev_free) {
+            for (auto& e : s->e)
+                if (e) cudaEventDestroy(e);
+            delete s;
+        }
+    }
+    size_t footprint() const {
+        size_t b = cams.bytes + rec.bytes + count.bytes + offset.bytes + scan_tmp.bytes + ranges.bytes +
+                   radix_tmp.bytes + Mm.bytes + out.bytes + small.bytes + gcount.bytes + gstart.bytes +
+                   gfill.bytes + lists.bytes + gscan_tmp.bytes + raycol.bytes;
+        for (int i = 0; i < 2; ++i) b += keys[i].bytes + vals[i].bytes;
+        return b;
+    }
+};
+
+}  // namespace dl
+
+struct dl_ctx {
+    int32_t device = 0;
+    std::string err;
+    int32_t next_id = 1;
+    std::map<int32_t, std::unique_ptr<dl::Scene>> scenes;
+    std::map<int32_t, std::unique_ptr<dl::Display>> displays;
+    dl::Workspace ws;
+    int32_t tile[3][2] = {{32, 32}, {16, 16}, {32, 32}};
+    int32_t sort_mode = DL_SORT_AUTO;
+    int32_t eval_transposed[3] = {1, 0, 1};  // per mode
+    int32_t warp_cap = 512;
+    bool timing = false;
+    dl_frame_stats stats{};
+    int32_t n_batches = 0;  // live dl_batch objects on this context
+};
+
+namespace dl {
+
+dl_status fail(dl_ctx* c, dl_status s, const char* fmt, ...);
+dl_status cuda_fail(dl_ctx* c, cudaError_t e, const char* what);
+dl_status check_ctx(dl_ctx* ctx);
+int bits_for(int64_t n);
+size_t max_smem_optin(int device);
+// Rays of a ray set grouped by (view, tile) for one tile shape (cached per shape).
+dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th, cudaStream_t s,
+                     TileGroups** out);
+// View cameras of Eq. (17) for a light-field centre pose.
+void make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>& cams);
+// Projection parameters of a frame (tile shape tw x th).
+ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, int32_t th);
+
+}  // namespace dl
+
+#define DL_CK(expr, what)                                       \
+    do {                                                        \
+        cudaError_t e_ = (expr);                                \
+        if (e_ != cudaSuccess) return dl::cuda_fail(ctx, e_, what); \
+    } while (0)

@@ -253,7 +253,13 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
 __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
                                    const uint32_t* __restrict__ count,
                                    const uint32_t* __restrict__ gstart, uint32_t* __restrict__ gfill,
-                                   unsigned long long* __restrict__ keys) {
+                                   unsigned long long* __restrict__ keys,
+                                   const uint32_t* __restrict__ total_keys, uint32_t key_cap,
+                                   uint32_t* __restrict__ status) {
+    if (total_keys && *total_keys > key_cap) {  // the key slice does not fit
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 1u);
+        return;
+    }
     const int64_t total = int64_t(nv) * p.n;
     const int ntiles = p.ntx * p.nty;
     const uint32_t zbits0 = __float_as_uint(0.2f);
@@ -329,13 +335,14 @@ cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectPar
 
 cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const float4* rec,
                                const uint32_t* count, const uint32_t* gstart, uint32_t* gfill,
-                               unsigned long long* keys, cudaStream_t s) {
+                               unsigned long long* keys, const uint32_t* total_keys,
+                               uint32_t key_cap, uint32_t* status, cudaStream_t s) {
     const int64_t total = int64_t(nv) * p.n;
     int64_t grid = (total + 255) / 256;
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
     emit_binned_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, rec, count, gstart, gfill,
-                                                                     keys);
+                                                                     keys, total_keys, key_cap, status);
     return cudaGetLastError();
 }
 

@@ -33,9 +33,12 @@ class Renderer:
         self.device = int(device)
         self.ctx = B.dl_create(self.device)
         self._displays = {}
+        self._batches = []
 
     def close(self) -> None:
         if self.ctx is not None:
+            for b in list(self._batches):
+                b.close()
             B.dl_destroy(self.ctx)
             self.ctx = None
 
@@ -150,3 +153,73 @@ class Renderer:
 
     def footprint(self, sid: int, did: int, mode: str = "directl") -> int:
         return B.dl_query_footprint(self.ctx, sid, did, MODES[mode])
+
+    def display_size(self, did: int):
+        """(width, height, views) of a display."""
+        return self._displays[did]
+
+    # -- batches and the tile autotuner -----------------------------------
+    def batch(self, plans, margin: float = 1.25) -> "Batch":
+        """A frame batch; plans: [(scene_id, display_id, (tile_w, tile_h) or
+        None, L0)] sizing each slot (see dl_batch_create)."""
+        return Batch(self, plans, margin)
+
+    def autotune_tile(self, sid: int, did: int, L0, candidates=((16, 16), (32, 16), (32, 32),
+                                                                 (64, 32)), reps: int = 3):
+        """Sets the DirectL tile to the fastest candidate; returns (best, ms)."""
+        return B.dl_autotune_tile(self.ctx, sid, did, np.asarray(L0, np.float64).ravel(),
+                                  candidates, reps, _stream())
+
+
+class Batch:
+    """A ``dl_batch``: one DirectL frame per assigned slot and launch, with
+    no host synchronisation, optionally replayed from a CUDA graph."""
+
+    def __init__(self, renderer: Renderer, plans, margin: float = 1.25):
+        self.r = renderer
+        self.n_slots = len(plans)
+        flat = []
+        for sid, did, tile, L0 in plans:
+            tw, th = tile if tile else (0, 0)
+            flat.append((sid, did, tw, th, np.asarray(L0, np.float64).ravel()))
+        self.h = B.dl_batch_create(renderer.ctx, flat, margin, _stream())
+        self.outs = [None] * self.n_slots
+        renderer._batches.append(self)
+
+    def assign(self, slot: int, sid: int, did: int, out: torch.Tensor, tile=None) -> None:
+        w, h, _ = self.r._displays[did]
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == 3 * w * h
+        tw, th = tile if tile else (0, 0)
+        B.dl_batch_assign(self.h, slot, sid, did, tw, th, out.data_ptr(), self.r.ctx)
+        self.outs[slot] = out
+
+    def clear(self, slot: int) -> None:
+        B.dl_batch_clear(self.h, slot, self.r.ctx)
+        self.outs[slot] = None
+
+    def set_pose(self, slot: int, L0) -> None:
+        B.dl_batch_set_pose(self.h, slot, np.asarray(L0, np.float64).ravel(), self.r.ctx)
+
+    def launch(self) -> None:
+        """Enqueue on the current stream."""
+        B.dl_batch_launch(self.h, _stream(), self.r.ctx)
+
+    def capture(self) -> None:
+        """Capture the current assignment into a CUDA graph (current stream,
+        which must not be the default stream)."""
+        B.dl_batch_capture(self.h, _stream(), self.r.ctx)
+
+    def wait(self, raise_on_capacity: bool = True):
+        """Per-slot status words of the last launch (0 = ok)."""
+        return B.dl_batch_wait(self.h, self.n_slots, self.r.ctx, raise_on_capacity)
+
+    def info(self):
+        """(device bytes, long-list capacity)."""
+        return B.dl_batch_info(self.h, self.r.ctx)
+
+    def close(self) -> None:
+        if self.h is not None:
+            B.dl_batch_destroy(self.h, self.r.ctx)
+            self.h = None
+            self.r._batches.remove(self)

@@ -1,0 +1,195 @@
+"""Frame batches (dl_batch_*) and the tile autotuner through the C ABI.
+
+A batch runs the same kernels as dl_render_frame, so every batched frame
+must equal the frame dl_render_frame gives for the same scene, display, tile
+shape and pose, bit for bit (and that frame is pinned to the oracle by
+test_gpu_render).  Also: graph replay with new poses, key-capacity overflow
+reported on the device with the output left as it was, host-side capacity
+and lifetime checks, and the autotuner's choice."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2407_14053_gb300 import Renderer
+    r = Renderer(0)
+    tiny = W.WORKLOADS["tiny"]
+    s_uniform = r.load_gaussians(W.make_scene(tiny.scene), "f32")
+    s_clustered = r.load_gaussians(W.make_scene(W.SceneSpec(3000, 3, "clustered", "bf16", seed=4)),
+                                   "bf16")
+    d_tiny = r.set_display(tiny.display)
+    d_small = r.set_display(W.Display(96, 64, 5, 5.3, 1 / 6, view_span_deg=8.0))
+    d_wide = r.set_display(W.Display(160, 90, 60, 5.3344, 0.12, p_w=4))
+    yield r, (s_uniform, s_clustered), (d_tiny, d_small, d_wide)
+    r.close()
+
+
+def _single(r, sid, did, L0, tile):
+    r.set_tile("directl", *tile)
+    try:
+        out = r.render(sid, did, L0, "directl")
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        r.set_tile("directl", 32, 32)
+
+
+def _out(r, did, fill=0.0):
+    w, h, _ = r.display_size(did)
+    return torch.full((h, w, 3), fill, dtype=torch.float32, device="cuda")
+
+
+FRAMES = [  # (scene index, display index, tile, yaw)
+    (0, 0, (32, 32), 3.0),
+    (1, 1, (16, 16), -2.0),
+    (1, 0, (32, 16), 1.0),
+    (0, 2, (64, 32), 0.0),
+]
+
+
+def test_mixed_batch_equals_single_frames(env):
+    r, S, D = env
+    plans = [(S[s], D[d], t, W.light_field_centre(4.0, y)) for s, d, t, y in FRAMES]
+    b = r.batch(plans, margin=1.5)
+    try:
+        outs = []
+        for i, (s, d, t, y) in enumerate(FRAMES):
+            outs.append(_out(r, D[d], np.nan))
+            b.assign(i, S[s], D[d], outs[-1], tile=t)
+            b.set_pose(i, W.light_field_centre(4.0, y + 0.5))
+        b.launch()
+        assert b.wait() == [0] * len(FRAMES)
+        for i, (s, d, t, y) in enumerate(FRAMES):
+            ref = _single(r, S[s], D[d], W.light_field_centre(4.0, y + 0.5), t)
+            assert np.array_equal(outs[i].cpu().numpy(), ref), f"slot {i}"
+        # a cleared slot is left out, the others still render
+        b.clear(2)
+        outs[2].fill_(-5.0)
+        b.set_pose(0, W.light_field_centre(4.0, 2.0))
+        b.launch()
+        b.wait()
+        assert torch.all(outs[2] == -5.0)
+        ref = _single(r, S[0], D[0], W.light_field_centre(4.0, 2.0), (32, 32))
+        assert np.array_equal(outs[0].cpu().numpy(), ref)
+    finally:
+        b.close()
+
+
+def test_batch_matches_oracle_on_a_sample(env):
+    r, S, D = env
+    tiny = W.WORKLOADS["tiny"]
+    L0 = W.light_field_centre(4.0, -1.0)
+    b = r.batch([(S[0], D[0], None, L0)])
+    try:
+        out = _out(r, D[0])
+        b.assign(0, S[0], D[0], out)
+        b.set_pose(0, L0)
+        b.launch()
+        b.wait()
+        img = out.cpu().numpy().reshape(-1)
+    finally:
+        b.close()
+    d = tiny.display
+    V = oracle.view_map(d)
+    src = oracle.repurpose(d, V)
+    sub = W.sample_subpixels(d, 400, windows=1, window_px=16, seed=3)
+    ref = oracle.render_subpixels(oracle.Scene(W.make_scene(tiny.scene)), d, L0, sub, V, src)
+    ok = (img[sub] >= ref["lo"] - 2e-3) & (img[sub] <= ref["hi"] + 2e-3)
+    assert ok.all(), f"{int((~ok).sum())} subpixels outside 2e-3"
+
+
+def test_graph_replay_follows_new_poses(env):
+    r, S, D = env
+    plans = [(S[0], D[0], None, W.light_field_centre(4.0, 0.0)),
+             (S[1], D[1], (16, 16), W.light_field_centre(4.0, 0.0))]
+    b = r.batch(plans, margin=2.0)
+    st = torch.cuda.Stream()
+    try:
+        outs = [_out(r, D[0]), _out(r, D[1])]
+        b.assign(0, S[0], D[0], outs[0])
+        b.assign(1, S[1], D[1], outs[1], tile=(16, 16))
+        with torch.cuda.stream(st):
+            b.capture()
+            for yaw in (-3.0, 4.0):
+                b.set_pose(0, W.light_field_centre(4.0, yaw))
+                b.set_pose(1, W.light_field_centre(4.0, -yaw))
+                b.launch()
+                assert b.wait() == [0, 0]
+                st.synchronize()
+                r0 = _single(r, S[0], D[0], W.light_field_centre(4.0, yaw), (32, 32))
+                r1 = _single(r, S[1], D[1], W.light_field_centre(4.0, -yaw), (16, 16))
+                assert np.array_equal(outs[0].cpu().numpy(), r0)
+                assert np.array_equal(outs[1].cpu().numpy(), r1)
+    finally:
+        b.close()
+
+
+def test_key_overflow_is_reported_and_output_kept(env):
+    from paper_2407_14053_gb300 import DL_ERR_CAPACITY, DirectLError
+    r, S, D = env
+    far = W.light_field_centre(14.0, 0.0)
+    near = W.light_field_centre(2.2, 0.0)
+    b = r.batch([(S[0], D[0], None, far), (S[0], D[0], None, far)], margin=1.0)
+    try:
+        outs = [_out(r, D[0], -7.0), _out(r, D[0], -7.0)]
+        for i in range(2):
+            b.assign(i, S[0], D[0], outs[i])
+        b.set_pose(0, near)
+        b.set_pose(1, far)
+        b.launch()
+        with pytest.raises(DirectLError) as e:
+            b.wait()
+        assert e.value.status == DL_ERR_CAPACITY
+        status = b.wait(raise_on_capacity=False)
+        assert status[0] & 1 and status[1] == 0
+        assert torch.all(outs[0] == -7.0)
+        assert np.array_equal(outs[1].cpu().numpy(), _single(r, S[0], D[0], far, (32, 32)))
+    finally:
+        b.close()
+
+
+def test_host_side_limits_and_lifetime(env):
+    from paper_2407_14053_gb300 import DL_ERR_CAPACITY, DL_ERR_INVALID_ARG, DirectLError
+    r, S, D = env
+    b = r.batch([(S[0], D[1], None, W.light_field_centre(4.0, 0.0))])
+    try:
+        with pytest.raises(DirectLError) as e:  # 45 views do not fit a 5-view slot
+            b.assign(0, S[0], D[0], _out(r, D[0]))
+        assert e.value.status == DL_ERR_CAPACITY
+        with pytest.raises(DirectLError) as e:  # 3000 Gaussians do not fit a 2000-Gaussian slot
+            b.assign(0, S[1], D[1], _out(r, D[1]))
+        assert e.value.status == DL_ERR_CAPACITY
+        b.assign(0, S[0], D[1], _out(r, D[1]))
+        with pytest.raises(DirectLError) as e:
+            r.free_scene(S[0])
+        assert e.value.status == DL_ERR_INVALID_ARG
+        with pytest.raises(DirectLError):
+            r.free_display(D[1])
+        with pytest.raises(DirectLError):  # poses need an assigned slot
+            b.set_pose(5, W.light_field_centre(4.0, 0.0))
+        bytes_, cap = b.info()
+        assert bytes_ > 0 and cap >= 2048
+    finally:
+        b.close()
+
+
+def test_autotuner_picks_the_fastest_candidate(env):
+    r, S, D = env
+    cands = [(16, 16), (32, 32), (64, 32)]
+    best, ms = r.autotune_tile(S[1], D[0], W.light_field_centre(4.0, 0.0), cands, reps=3)
+    try:
+        assert best in cands and len(ms) == 3 and all(m > 0 for m in ms)
+        assert ms[cands.index(best)] == min(ms)
+        r.render(S[1], D[0], W.light_field_centre(4.0, 0.0), "directl")
+        torch.cuda.synchronize()
+        st = r.stats()
+        assert (st["tile_w"], st["tile_h"]) == best
+    finally:
+        r.set_tile("directl", 32, 32)
