@@ -119,6 +119,30 @@ def test_4k_bf16_sampled(renderer, mode):
     renderer.free_scene(sid)
 
 
+def test_1080p_f16_storage_sampled(renderer):
+    # FP16 storage of scale, rotation, opacity and SH (the serving mix's
+    # format): 2e-3 against the oracle on the FP16-rounded attributes, 8e-3
+    # against the FP32 originals
+    wl = W.WORKLOADS["1080p"]
+    scene = W.make_scene(W.SceneSpec(wl.scene.n, 3, "clustered", "f16", seed=8))
+    sid = renderer.load_gaussians(scene, "f16")
+    did = renderer.set_display(wl.display)
+    L0 = W.light_field_centre(wl.camera_distance, 2.5)
+    img = _frame(renderer, sid, did, L0, "directl").reshape(-1)
+    sub = W.sample_subpixels(wl.display, 1024, windows=1, window_px=16, seed=13)
+    V, src = _sources(renderer, did, wl.display, "directl")
+    deq = oracle.render_subpixels(oracle.Scene(W.quantise_storage(scene, "f16")), wl.display, L0,
+                                  sub, V, src)
+    ok, maxerr, nbad = _accept(img[sub], deq, TOL)
+    assert nbad == 0, f"vs dequantised oracle: {nbad} outside 2e-3; max |err| {maxerr:.3g}"
+    full = oracle.render_subpixels(oracle.Scene(scene), wl.display, L0, sub, V, src)
+    ok, maxerr32, nbad = _accept(img[sub], full, TOL_BF16_VS_FP32)
+    print(f"1080p f16: max |err| vs dequantised {maxerr:.2e}, vs FP32 attributes {maxerr32:.2e}")
+    assert nbad == 0, f"vs FP32 oracle: {nbad} outside 8e-3; max |err| {maxerr32:.3g}"
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
 def _tiny_case(n=400, seed=21, **disp):
     d = W.Display(**{**dict(width=96, height=54, num_views=9, pitch_lx=5.3, tan_slant=1 / 6,
                             view_span_deg=30.0), **disp})
