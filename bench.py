@@ -16,6 +16,13 @@ the tile rasteriser, then interweaved) is timed the same way on the same GPU
 and reported under "standard".  Every step works on more than L2's worth of
 data (2.2 GB of per-view splat records alone), so no L2 flush is added.
 
+Two more sections follow on fresh contexts (skipped under torchrun):
+"graph_batched" renders the 8K panel (100 views, 3M Gaussians, BF16) from a
+captured CUDA graph of the frame batch after the autotuner has picked the
+tile shape, and "serving" runs the continuous-batching server on a mix of
+256 Poisson-arriving requests (scenes of 100k-3M Gaussians in FP16, 1080p/45,
+4K/45 and 4K/60 displays, 150 GB HBM budget) and reports p50/p99 latency.
+
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead
 (a bounded sample of rays per step, extrapolated to frames/s).
 """
@@ -58,6 +65,10 @@ def parse():
     ap.add_argument("--no-standard", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the continuous-batching serving mix")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="skip the 8K/100-view captured-graph batch section")
     return ap.parse_args()
 
 
@@ -311,6 +322,119 @@ def load_traffic(kernel: str, workload: str, source_file: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def run_graph_batched(device: int, steps: int) -> dict:
+    """8K panel, 100 views, 3M Gaussians (BF16): tile shape picked by the
+    autotuner, then one frame per step from a captured CUDA graph of the
+    frame batch (no host synchronisation inside a frame)."""
+    import torch
+
+    from paper_2407_14053_gb300 import Renderer
+    wl = W.WORKLOADS["8k"]
+    r = Renderer(device)
+    try:
+        t0 = time.perf_counter()
+        scene = W.make_scene(wl.scene)
+        sid = r.load_gaussians(scene, wl.scene.dtype)
+        del scene
+        did = r.set_display(wl.display)
+        setup_s = time.perf_counter() - t0
+        poses = W.camera_path(200, wl.camera_distance, 10.0)
+        cands = [(16, 16), (32, 16), (32, 32), (64, 32)]
+        best, ms = r.autotune_tile(sid, did, poses[0], cands, reps=3)
+        b = r.batch([(sid, did, best, poses[0])], margin=1.25)
+        out = torch.empty((wl.display.height, wl.display.width, 3), dtype=torch.float32,
+                          device=f"cuda:{device}")
+        st = torch.cuda.Stream()
+        b.assign(0, sid, did, out, tile=best)
+        with torch.cuda.stream(st):
+            b.capture()
+            for i in range(3):
+                b.set_pose(0, poses[i])
+                b.launch()
+            b.wait()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for i in range(steps):
+                b.set_pose(0, poses[(7 * i) % 200])
+                b.launch()
+            e1.record()
+            status = b.wait(raise_on_capacity=False)
+        st.synchronize()
+        graph_ms = e0.elapsed_time(e1) / steps
+        # the same frames through dl_render_frame (host sync per frame)
+        r.set_tile("directl", *best)
+        torch.cuda.synchronize()
+        e0.record()
+        for i in range(steps):
+            r.render(sid, did, poses[(7 * i) % 200], "directl", out)
+        e1.record()
+        torch.cuda.synchronize()
+        direct_ms = e0.elapsed_time(e1) / steps
+        n_rays, beta = r.display_info(did)
+        bytes_, long_cap = b.info()
+        b.close()
+        return {"workload": workload_desc(wl), "tile_autotuned": list(best),
+                "autotune_ms": {f"{c[0]}x{c[1]}": m for c, m in zip(cands, ms)},
+                "frames_per_s": 1e3 / graph_ms, "ms_per_frame": graph_ms, "steps": steps,
+                "subpixels_per_s": 1e3 / graph_ms * 3 * wl.display.width * wl.display.height,
+                "render_frame_ms": direct_ms, "status": status, "batch_bytes": bytes_,
+                "beta": beta, "n_rays": int(n_rays), "setup_s": setup_s,
+                "note": "one slot, captured graph replayed with a new pose per step"}
+    finally:
+        r.close()
+        torch.cuda.empty_cache()
+
+
+def run_serving(device: int, n_requests: int = 256, n_scenes: int = 8, util: float = 0.7,
+                seed: int = 0) -> dict:
+    """Serving mix: Poisson arrivals, scenes of 100k-3M Gaussians
+    (log-uniform, SH 3, FP16 storage), displays 1080p/45, 4K/45, 4K/60, head
+    yaw U[-5, 5] degrees, 150 GB HBM budget.  The arrival rate is `util`
+    times the service rate measured on a burst of the same mix."""
+    import torch
+
+    from paper_2407_14053_gb300 import Renderer
+    from paper_2407_14053_gb300.serving import Request, Server, poisson_arrivals
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    sizes = np.exp(rng.uniform(np.log(1e5), np.log(3e6), size=n_scenes)).astype(int)
+    sizes[0] = 3_000_000  # the slot-sizing scene: the largest of the mix
+    scenes = {f"s{i}": (W.make_scene(W.SceneSpec(int(n), 3, "clustered", "f16", seed=50 + i)), "f16")
+              for i, n in enumerate(sizes)}
+    p1080, p4k = W.WORKLOADS["1080p"].display, W.WORKLOADS["4k"].display
+    displays = {"1080p45": p1080, "4k45": p4k, "4k60": p4k.replace(num_views=60)}
+    gen_s = time.perf_counter() - t0
+    r = Renderer(device)
+    try:
+        L0 = W.light_field_centre(4.0, 0.0)
+        plans = [("s0", "4k60"), ("s0", "4k60"), ("s0", "1080p45"), ("s0", "1080p45")]
+        srv = Server(r, scenes, displays, plans, L0, lanes=2, hbm_budget=150e9, margin=1.3)
+
+        def mix(n, arrivals, base):
+            keys, dkeys = sorted(scenes), sorted(displays)
+            return [Request(base + i, keys[rng.integers(len(keys))], dkeys[rng.integers(3)],
+                            W.light_field_centre(4.0, float(rng.uniform(-5, 5))), float(a))
+                    for i, a in enumerate(arrivals)]
+
+        burst = srv.run(mix(32, np.zeros(32), 0))            # warm-up + service rate
+        rate = util * burst["frames_per_s"]
+        reqs = mix(n_requests, poisson_arrivals(n_requests, rate, seed + 1), 1000)
+        summary = srv.run(reqs)
+        summary.update({"arrival_rate_per_s": rate, "burst_frames_per_s": burst["frames_per_s"],
+                        "target_utilisation": util, "hbm_budget_gb": 150.0,
+                        "hbm_reserved_gb": srv.cache.reserved / 1e9,
+                        "hbm_used_gb": srv.cache.used / 1e9, "scene_loads": srv.cache.loads,
+                        "evictions": srv.cache.evictions, "scene_sizes": [int(x) for x in sizes],
+                        "lanes": 2, "slots_per_lane": len(plans), "scene_gen_s": gen_s,
+                        "mix": "scenes log-uniform 100k-3M (SH3, FP16), displays 1080p/45, "
+                               "4K/45, 4K/60 uniform, yaw U[-5,5] deg, Poisson arrivals"})
+        srv.close()
+        return summary
+    finally:
+        r.close()
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -389,18 +513,25 @@ def main():
         e2e = {"value": reduce_sum(args.steps, world, dev) / wall, "unit": "frames/s",
                "h2d_bytes_per_step": cam_bytes, "d2h_bytes_per_step": 12 * d.width * d.height}
 
-    # ---- roofline of the compositing kernel (ALU bound) ----
+    # ---- roofline of the compositing stage (ALU bound) ----
+    # The stage is the persistent warp-per-tile kernel's two classes (lists
+    # of <= 512 and <= 1024 keys; longer lists would add the block class),
+    # timed with CUDA events on the launching stream around the launches.
     comp_ms = dl_stages["composite"]
     flops = FLOP_PER_EVAL * dl_stages["pairs_evaluated"] + FLOP_PER_BLEND * dl_stages["pairs_blended"]
     clk = 2070.0
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
     achieved = flops / (comp_ms / 1e3) / 1e12 if comp_ms > 0 else 0.0
     src_file = os.path.join(ROOT, "paper_2407_14053_gb300", "csrc", "composite.cu")
-    roofline = {"kernel": "composite_rays_kernel", "bound": "alu", "achieved": achieved,
+    kname = "composite_rays_warp_kernel"
+    roofline = {"kernel": kname + " (512- and 1024-key classes: the compositing stage)",
+                "bound": "alu", "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
-                "traffic": load_traffic("composite_rays_kernel", args.workload, src_file),
-                "flop_per_launch": flops, "ms_per_launch": comp_ms}
+                "traffic": load_traffic(kname, args.workload, src_file),
+                "flop_per_launch": flops, "ms_per_launch": comp_ms,
+                "flop_model": f"{FLOP_PER_EVAL} per evaluated (ray, Gaussian) pair + "
+                              f"{FLOP_PER_BLEND} per composited pair"}
 
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
@@ -412,6 +543,19 @@ def main():
                           f"every view's {wl.scene.n} Gaussians projected in FP64), frame time "
                           f"extrapolated as N_v*T_project + N_rays*T_ray, N_rays={n_rays}; "
                           f"{est['sample_s']:.1f} s of CPU time")}
+
+    r.free_scene(sid)
+    r.free_display(did)
+    r.close()
+    del out
+    torch.cuda.empty_cache()
+
+    graph = None
+    if not args.no_graph and world == 1:
+        graph = run_graph_batched(local, max(3, args.steps // 4))
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = run_serving(local)
 
     if rank == 0:
         line = {
@@ -432,9 +576,10 @@ def main():
             "e2e": e2e,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "graph_batched": graph,
+            "serving": serving,
         }
         print(json.dumps(line))
-    r.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
