@@ -771,9 +771,11 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     int cap_large = warp_path ? 2048 : 1;
     while (cap_large < max_len) cap_large <<= 1;
     const int binned_threads = mode == DL_STANDARD ? tw * th : kBinnedThreads;
+    const size_t class_smem = warp_path ? block_smem_bytes(cap_large)
+                                        : binned_smem_bytes(std::max(cap_large, kSmallCap),
+                                                            binned_threads);
     bool binned = ctx->sort_mode != DL_SORT_RADIX && max_len <= kLargeCap &&
-                  binned_smem_bytes(std::max(cap_large, kSmallCap), binned_threads) <=
-                      max_smem_optin(ctx->device);
+                  class_smem <= max_smem_optin(ctx->device);
     if (ctx->sort_mode == DL_SORT_BINNED && !binned)
         return fail(ctx, DL_ERR_CAPACITY, "a tile list holds %lld keys (binned limit %d)",
                     (long long)max_len, kLargeCap);
@@ -856,8 +858,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                   "composite rays (warp per group)");
             DL_CK(launch_composite_rays_warp(1024, 1, dF, prefix, 1, n_mid, d_meta + 5, pairs, s),
                   "composite rays (warp per group, 1024 keys)");
-            DL_CK(launch_composite_rays_block(cap_large, dF, prefix, 1, n_large, d_meta + 6, pairs,
-                                              ctx->eval_transposed[mode], s),
+            DL_CK(launch_composite_rays_block(cap_large, dF, prefix, 1, n_large, d_meta + 6, pairs, s),
                   "composite rays (block per group)");
             launches += 1;
         } else {

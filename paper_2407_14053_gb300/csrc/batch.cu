@@ -16,6 +16,8 @@
 namespace dl {
 namespace {
 
+// lists of <= 512 and <= 1024 keys: one warp each (two shared-memory sizes);
+// longer lists: the four-warp quadrant blocks
 constexpr int kWarpCap1 = 512, kWarpCap2 = 1024;
 constexpr int kMetaWords = 16;  // per slot: partition counters, key total (u64 at word 8)
 
@@ -180,11 +182,12 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
         DL_CK(launch_composite_rays_warp(kWarpCap1, 0, b->frames_d(), prefix, n_act, max_items, cur,
                                          nullptr, s),
               "composite rays (warp class 512)");
-        DL_CK(launch_composite_rays_warp(kWarpCap2, 1, b->frames_d(), prefix, n_act, max_items,
-                                         cur + 1, nullptr, s),
-              "composite rays (warp class 1024)");
+        if (kWarpCap2 > 0)
+            DL_CK(launch_composite_rays_warp(kWarpCap2, 1, b->frames_d(), prefix, n_act, max_items,
+                                             cur + 1, nullptr, s),
+                  "composite rays (warp class 1024)");
         DL_CK(launch_composite_rays_block(b->block_cap, b->frames_d(), prefix, n_act, max_items,
-                                          cur + 2, nullptr, ctx->eval_transposed[DL_DIRECTL], s),
+                                          cur + 2, nullptr, s),
               "composite rays (block class)");
     }
     for (int32_t i = 0; i < n_slots; ++i) {
@@ -280,7 +283,7 @@ dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plan
     if (st) return st;
     b->block_cap = 2048;
     while (b->block_cap < longest && b->block_cap < 16384) b->block_cap <<= 1;
-    if (binned_smem_bytes(b->block_cap, kBinnedThreads) > max_smem_optin(ctx->device))
+    if (block_smem_bytes(b->block_cap) > max_smem_optin(ctx->device))
         return fail(ctx, DL_ERR_CAPACITY, "long-list capacity %d exceeds shared memory", b->block_cap);
     // ---- arena layout ----
     size_t off = 0;

@@ -500,7 +500,7 @@ __device__ __forceinline__ void stream_list(const unsigned long long* sk, int le
     for (int b = 0; b < len; b += nthr) {
         const int i = b + t;
         if (i < len) {
-            const int64_t e = vbase + uint32_t(sk[i]);
+            const int64_t e = vbase + (uint32_t(sk[i]) >> 4);
             buf[t] = rec[3 * e];
             buf[nthr + t] = rec[3 * e + 1];
             buf[2 * nthr + t] = rec[3 * e + 2];
@@ -528,7 +528,7 @@ __device__ __forceinline__ void stream_list_db(const unsigned long long* sk, int
         float4* dst = buf + (b & 1) * 3 * nthr;
         const int i = b * nthr + t;
         if (i < len) {
-            const int64_t e = vbase + uint32_t(sk[i]);
+            const int64_t e = vbase + (uint32_t(sk[i]) >> 4);
             cp_async16(dst + t, rec + 3 * e);
             cp_async16(dst + nthr + t, rec + 3 * e + 1);
             cp_async16(dst + 2 * nthr + t, rec + 3 * e + 2);
@@ -559,6 +559,12 @@ struct BinnedSmem {
     float4* buf;
     int* wbuf;
 };
+
+// Bytes of the key array (cap keys) and the bucket counters (cap + 2) of
+// block_sort, rounded up to 16.
+__host__ __device__ __forceinline__ size_t block_sort_bytes(int cap) {
+    return (8 * size_t(cap) + 4 * size_t(cap + 2) + 15) & ~size_t(15);
+}
 
 __device__ __forceinline__ BinnedSmem carve_binned(unsigned char* base, int cap, int nthr) {
     BinnedSmem m;
@@ -657,6 +663,13 @@ composite_full_binned_kernel(CompositeParams p, const int32_t* __restrict__ list
 // its rays.  Only __syncwarp is used, so warps never wait on each other.
 constexpr int kWarpsPerBlock = 4;
 
+// Positions of the warp's rays about their box centre (x, y), written per
+// ray chunk, and the per-ray candidate masks of one batch.
+struct RayTable {
+    float2 xy[32];
+    unsigned mask[32];
+};
+
 template <int CAP>
 struct WarpSmem {
     static constexpr int kBuckets = CAP / 2;
@@ -664,6 +677,7 @@ struct WarpSmem {
     uint32_t bstart[kBuckets + 1];
     uint32_t bfill[kBuckets];
     float4 buf[2][3][32];
+    RayTable rays;
 };
 
 // Warp-level version of block_sort (len <= CAP).  Lists of up to 512 keys
@@ -790,20 +804,100 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
     }
 }
 
+// Margin of the batch test below: the expanded quadratic is rounded
+// differently from log2_alpha, by less than 0.05 for tiles up to 256 x 256
+// pixels (its terms are bounded by lambda_max(conic) <= 1/0.3 times the
+// squared distance from the box centre), so a pair passes the test whenever
+// log2_alpha reaches the threshold; blend() then decides exactly.
+constexpr float kTestMargin = 0.05f;
+
+// Transposed evaluation of a batch of n <= 32 records held in shared memory
+// (c0, c1, c2) for the warp's rays: lane j holds record j's conic (u, v, A,
+// B, C, L) when `hit` (its pixel box meets the rays' box).  The lane expands
+// the quadratic about the box centre (ox, oy) into
+// l2(x, y) = x (A x + B y + D) + y (C y + E) + F and tests it against every
+// ray (5 FMAs per pair, ray positions from the table), four rays per step;
+// ray r's mask of candidate records goes to T.mask[r].  Then every lane
+// blends its candidates in list order.
+__device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const float4* c2, int n,
+                                       bool hit, float u, float v, float A, float B, float C,
+                                       float L, Acc& a, bool& done, uint32_t& evals, float px,
+                                       float py, RayTable& T, float ox, float oy) {
+    const int lane = threadIdx.x & 31;
+    if (!__any_sync(0xffffffffu, hit)) return;
+    const unsigned act = __ballot_sync(0xffffffffu, !done);
+    const float du = u - ox, dv = v - oy;
+    const float D = -fmaf(2.f * A, du, B * dv);
+    const float E = -fmaf(2.f * C, dv, B * du);
+    const float F = hit ? fmaf(du, fmaf(A, du, B * dv), fmaf(C * dv, dv, L)) + kTestMargin : -1e30f;
+#pragma unroll
+    for (int g = 0; g < 32; g += 4) {
+        if (!((act >> g) & 0xFu)) continue;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 q = T.xy[g + k];
+            const float t1 = fmaf(A, q.x, fmaf(B, q.y, D));
+            const float l2 = fmaf(q.x, t1, fmaf(q.y, fmaf(C, q.y, E), F));
+            const unsigned m = __ballot_sync(0xffffffffu, l2 >= kLog2MinAlpha);
+            if (lane == 0) T.mask[g + k] = m;
+        }
+    }
+    __syncwarp();
+    unsigned mine = (act >> lane) & 1u ? T.mask[lane] : 0u;
+    if (!done) evals += uint32_t(n);
+    while (mine && !done) {
+        const int sidx = __ffs(mine) - 1;
+        mine &= mine - 1;
+        if (!blend(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
+    }
+    __syncwarp();
+}
+
+// Fills the ray table for the warp's current rays (box centre (ox, oy)).
+__device__ __forceinline__ void ray_table(RayTable& T, bool active, float px, float py, float& ox,
+                                          float& oy, int bx0, int bx1, int by0, int by1,
+                                          float half_w, float half_h) {
+    const int lane = threadIdx.x & 31;
+    ox = 0.5f * float(bx0 + bx1) - half_w;
+    oy = 0.5f * float(by0 + by1) - half_h;
+    T.xy[lane] = active ? make_float2(px - ox, py - oy) : make_float2(1e18f, 1e18f);
+    __syncwarp();
+}
+
+// Lane's record of a shared-memory batch against the warp's ray box:
+// returns `hit` and loads the conic into registers when it does.
+__device__ __forceinline__ bool batch_conic(const float4* c0, const float4* c1, const float4* c2,
+                                            int n, int bx0, int bx1, int by0, int by1, float& u,
+                                            float& v, float& A, float& B, float& C, float& L) {
+    const int lane = threadIdx.x & 31;
+    u = 0.f; v = 0.f; A = 0.f; B = 0.f; C = 0.f; L = -1e30f;
+    if (lane >= n) return false;
+    const float4 q2 = c2[lane];
+    const uint32_t rc = __float_as_uint(q2.z), rr = __float_as_uint(q2.w);
+    const bool hit = int(rc & 0xFFFFu) <= bx1 && int(rc >> 16) >= bx0 && int(rr & 0xFFFFu) <= by1 &&
+                     int(rr >> 16) >= by0;
+    if (hit) {
+        const float4 q0 = c0[lane];
+        const float2 q1 = *reinterpret_cast<const float2*>(c1 + lane);
+        u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y;
+    }
+    return hit;
+}
+
 // Streams the warp's sorted list in batches of 32 records (cp.async double
 // buffering) and composites them, transposed, for the warp's rays.
 template <int CAP>
 __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t vbase,
                                             const float4* __restrict__ rec, Acc& a, bool& done,
                                             uint32_t& evals, float px, float py, int bx0, int bx1,
-                                            int by0, int by1) {
+                                            int by0, int by1, float ox, float oy) {
     const int lane = threadIdx.x & 31;
     const int nbatch = (len + 31) / 32;
     if (nbatch == 0) return;
     auto issue = [&](int b) {
         const int i = b * 32 + lane;
         if (i < len) {
-            const int64_t e = vbase + uint32_t(W.sk[i]);
+            const int64_t e = vbase + (uint32_t(W.sk[i]) >> 4);
             cp_async16(&W.buf[b & 1][0][lane], rec + 3 * e);
             cp_async16(&W.buf[b & 1][1][lane], rec + 3 * e + 1);
             cp_async16(&W.buf[b & 1][2][lane], rec + 3 * e + 2);
@@ -820,52 +914,81 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
         const float4* c1 = W.buf[b & 1][1];
         const float4* c2 = W.buf[b & 1][2];
         const int n = len - b * 32 < 32 ? len - b * 32 : 32;
-        bool hit = false;
-        float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f, L = -1e30f;
-        if (lane < n) {
-            const float4 q2 = c2[lane];
-            const uint32_t rc = __float_as_uint(q2.z), rr = __float_as_uint(q2.w);
-            hit = int(rc & 0xFFFFu) <= bx1 && int(rc >> 16) >= bx0 && int(rr & 0xFFFFu) <= by1 &&
-                  int(rr >> 16) >= by0;
-            if (hit) {
-                const float4 q0 = c0[lane];
-                const float2 q1 = *reinterpret_cast<const float2*>(c1 + lane);
-                u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y;
-            }
-        }
-        if (__any_sync(0xffffffffu, hit)) {
-            unsigned act = __ballot_sync(0xffffffffu, !done);
-            unsigned mine = 0;
-            while (act) {  // four rays per pass: independent chains
-                int r[4];
-                r[0] = __ffs(act) - 1;
-                act &= act - 1;
-#pragma unroll
-                for (int k = 1; k < 4; ++k) {  // repeats r[0] once act runs out
-                    r[k] = act ? __ffs(act) - 1 : r[0];
-                    act &= act - 1;
-                }
-                unsigned m[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float rx = __shfl_sync(0xffffffffu, px, r[k]);
-                    const float ry = __shfl_sync(0xffffffffu, py, r[k]);
-                    m[k] = __ballot_sync(0xffffffffu,
-                                         log2_alpha(rx, ry, u, v, A, B, C, L) >= kLog2MinAlpha);
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (lane == r[k]) mine = m[k];
-            }
-            if (!done) evals += uint32_t(n);
-            while (mine && !done) {
-                const int sidx = __ffs(mine) - 1;
-                mine &= mine - 1;
-                if (!blend(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
-            }
-        }
-        __syncwarp();
+        float u, v, A, B, C, L;
+        const bool hit = batch_conic(c0, c1, c2, n, bx0, bx1, by0, by1, u, v, A, B, C, L);
+        eval32(c0, c1, c2, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.rays, ox, oy);
         if (__all_sync(0xffffffffu, done)) break;
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// Per-warp shared memory of the quadrant block kernel: list positions
+// selected for the warp's quadrant and not yet batched, and two batches of 32
+// records in flight (cp.async double buffering).
+struct QuadPipe {
+    int stage[64];
+    int idx[2][32];
+    float4 buf[2][3][32];
+    RayTable rays;
+};
+
+// Streams the records of a block-sorted list whose key marks quadrant `q`
+// (bit q of the key's low nibble) for the warp's rays, in list order: the
+// selected positions are compacted 32 at a time and their records fetched
+// with cp.async one batch ahead of the batch being evaluated (as in
+// warp_stream).
+__device__ void quadrant_stream(const unsigned long long* sk, int len, int q, int64_t vbase,
+                                const float4* __restrict__ rec, QuadPipe& Q, Acc& a, bool& done,
+                                uint32_t& evals, float px, float py, int bx0, int bx1, int by0,
+                                int by1, float ox, float oy) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int pos = 0, cnt = 0;  // scan position, staged positions (uniform)
+    // next batch of up to 32 selected positions into Q.idx[slot], its records
+    // requested; returns its size
+    auto produce = [&](int slot) -> int {
+        while (cnt < 32 && pos < len) {
+            const int i = pos + lane;
+            const bool sel = i < len && ((uint32_t(sk[i]) >> q) & 1u);
+            const unsigned m = __ballot_sync(0xffffffffu, sel);
+            if (sel) Q.stage[cnt + __popc(m & lt)] = i;
+            cnt += __popc(m);
+            pos += 32;
+            __syncwarp();
+        }
+        const int n = cnt < 32 ? cnt : 32;
+        const int mine = lane < n ? Q.stage[lane] : 0;
+        const int rest = lane + 32 < cnt ? Q.stage[lane + 32] : 0;
+        __syncwarp();
+        if (lane + 32 < cnt) Q.stage[lane] = rest;
+        Q.idx[slot][lane] = mine;
+        cnt -= n;
+        if (lane < n) {
+            const int64_t e = vbase + (uint32_t(sk[mine]) >> 4);
+            cp_async16(&Q.buf[slot][0][lane], rec + 3 * e);
+            cp_async16(&Q.buf[slot][1][lane], rec + 3 * e + 1);
+            cp_async16(&Q.buf[slot][2][lane], rec + 3 * e + 2);
+        }
+        cp_async_commit();
+        __syncwarp();
+        return n;
+    };
+    int slot = 0;
+    int n_cur = produce(0);
+    while (n_cur > 0) {
+        const int n_next = __all_sync(0xffffffffu, done) ? 0 : produce(slot ^ 1);
+        if (n_next > 0) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncwarp();
+        const float4* c0 = Q.buf[slot][0];
+        const float4* c1 = Q.buf[slot][1];
+        const float4* c2 = Q.buf[slot][2];
+        float u, v, A, B, C, L;
+        const bool hit = batch_conic(c0, c1, c2, n_cur, bx0, bx1, by0, by1, u, v, A, B, C, L);
+        eval32(c0, c1, c2, n_cur, hit, u, v, A, B, C, L, a, done, evals, px, py, Q.rays, ox, oy);
+        slot ^= 1;
+        n_cur = __all_sync(0xffffffffu, done) ? 0 : n_next;
     }
     cp_async_wait<0>();
     __syncwarp();
@@ -948,9 +1071,11 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
             const float px = float(col) - half_w, py = float(row) - half_h;
             int bx0, bx1, by0, by1;
             warp_box(active, col, row, bx0, bx1, by0, by1);
+            float ox, oy;
+            ray_table(W.rays, active, px, py, ox, oy, bx0, bx1, by0, by1, half_w, half_h);
             Acc a{1.f, 0.f, 0.f, 0.f, 0u};
             bool done = !active;
-            warp_stream(W, len, vbase, rec, a, done, evals, px, py, bx0, bx1, by0, by1);
+            warp_stream(W, len, vbase, rec, a, done, evals, px, py, bx0, bx1, by0, by1, ox, oy);
             if (active) {
                 float* o = raycol + 3 * int64_t(ray.y);
                 o[0] = a.c0;
@@ -966,18 +1091,22 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
     if (pairs) count_pairs(pairs, evals, blended);
 }
 
-// Block class across frames: one block per group list longer than 1024 keys
-// (sorted in shared memory up to `cap` keys), persistent like the warp
+// Block class across frames: one block of four warps per group list too long
+// for a warp (sorted together in shared memory up to `cap` keys); warp q then
+// composites the group's rays in quadrant q of the tile (x half + 2 * y half)
+// over the records whose key marks that quadrant, so every warp has work and
+// each streams only about half of the list.  Persistent like the warp
 // classes.
-template <bool TRANSPOSED>
 __global__ void __launch_bounds__(kBinnedThreads)
 composite_rays_block_kernel(const FrameDesc* __restrict__ F, const int64_t* __restrict__ prefix,
                             int n_frames, int cap, uint32_t* __restrict__ cursor,
                             unsigned long long* __restrict__ pairs) {
     extern __shared__ __align__(16) unsigned char smb[];
     __shared__ int64_t s_item;
-    const int nthr = blockDim.x;
-    const BinnedSmem S = carve_binned(smb, cap, nthr);
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(smb);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smb + 8 * size_t(cap));
+    QuadPipe* pipes = reinterpret_cast<QuadPipe*>(smb + block_sort_bytes(cap));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_items = __ldg(prefix + n_frames);
     uint32_t evals = 0, blended = 0;
     int64_t item = blockIdx.x;
@@ -991,21 +1120,42 @@ composite_rays_block_kernel(const FrameDesc* __restrict__ F, const int64_t* __re
             if (threadIdx.x == 0) atomicOr(d.status, 2u);
         } else {
             const int v = wi.x / d.cp.ntiles;
-            block_sort<0>(d.keys, start, len, cap, S.sk, S.cnt);
+            const int tile = wi.x - v * d.cp.ntiles;
+            const int xm = (tile % d.cp.ntx) * d.cp.tile_w + (d.cp.tile_w >> 1);
+            const int ym = (tile / d.cp.ntx) * d.cp.tile_h + (d.cp.tile_h >> 1);
+            const int qx = warp & 1, qy = warp >> 1;
+            block_sort<0>(d.keys, start, len, cap, sk, cnt);
             const int64_t vbase = int64_t(v) * d.cp.n;
-            for (int r0 = wi.y; r0 < wi.z; r0 += nthr) {
-                const int rid = r0 + int(threadIdx.x);
-                const bool active = rid < wi.z;
-                const int2 ray = active ? d.grouped[rid] : make_int2(0, -1);
+            // quadrant bits: bit q set when the record's pixel box overlaps
+            // quadrant q (x half + 2 * y half) of the tile
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const unsigned long long k = sk[i];
+                const uint2 box = *reinterpret_cast<const uint2*>(
+                    reinterpret_cast<const float*>(d.rec + 3 * (vbase + (uint32_t(k) >> 4)) + 2) + 2);
+                const int c0 = int(box.x & 0xFFFFu), c1 = int(box.x >> 16);
+                const int rr0 = int(box.y & 0xFFFFu), rr1 = int(box.y >> 16);
+                const uint32_t lo_x = c0 < xm, hi_x = c1 >= xm, lo_y = rr0 < ym, hi_y = rr1 >= ym;
+                sk[i] = k | ((lo_x & lo_y) | ((hi_x & lo_y) << 1) | ((lo_x & hi_y) << 2) |
+                             ((hi_x & hi_y) << 3));
+            }
+            __syncthreads();
+            for (int r0 = wi.y; r0 < wi.z; r0 += 32) {
+                const int rid = r0 + lane;
+                const int2 ray = rid < wi.z ? d.grouped[rid] : make_int2(0, -1);
                 const int col = int(uint32_t(ray.x) & 0xFFFFu), row = int(uint32_t(ray.x) >> 16);
+                const bool mine = rid < wi.z && int(col >= xm) == qx && int(row >= ym) == qy;
+                if (!__any_sync(0xffffffffu, mine)) continue;
                 const float px = float(col) - d.cp.half_w, py = float(row) - d.cp.half_h;
                 int bx0, bx1, by0, by1;
-                warp_box(active, col, row, bx0, bx1, by0, by1);
+                warp_box(mine, col, row, bx0, bx1, by0, by1);
+                float ox, oy;
+                ray_table(pipes[warp].rays, mine, px, py, ox, oy, bx0, bx1, by0, by1, d.cp.half_w,
+                          d.cp.half_h);
                 Acc a{1.f, 0.f, 0.f, 0.f, 0u};
-                bool done = !active;
-                stream_list<TRANSPOSED>(S.sk, len, vbase, d.rec, S.buf, S.wbuf, a, done, evals, px,
-                                        py, bx0, bx1, by0, by1);
-                if (active) {
+                bool done = !mine;
+                quadrant_stream(sk, len, warp, vbase, d.rec, pipes[warp], a, done, evals, px, py,
+                                bx0, bx1, by0, by1, ox, oy);
+                if (mine) {
                     float* o = d.raycol + 3 * int64_t(ray.y);
                     o[0] = a.c0;
                     o[1] = a.c1;
@@ -1130,6 +1280,10 @@ cudaError_t launch_composite_full(const CompositeParams& p, int32_t nv, const ui
     return cudaGetLastError();
 }
 
+size_t block_smem_bytes(int cap) {
+    return block_sort_bytes(cap) + (kBinnedThreads / 32) * sizeof(QuadPipe);
+}
+
 size_t binned_smem_bytes(int cap, int nthr) {
     const size_t off = (8 * size_t(cap) + 4 * size_t(cap + 2) + 15) & ~size_t(15);
     return off + size_t(nthr) * 3 * sizeof(float4) + size_t(nthr / 32) * 64 * sizeof(int);
@@ -1219,16 +1373,11 @@ cudaError_t launch_composite_rays_warp(int cap, int cls, const FrameDesc* frames
 
 cudaError_t launch_composite_rays_block(int block_cap, const FrameDesc* frames,
                                         const int64_t* prefix, int32_t n_frames, int64_t max_items,
-                                        uint32_t* cursor, unsigned long long* pairs, int transposed,
-                                        cudaStream_t s) {
+                                        uint32_t* cursor, unsigned long long* pairs, cudaStream_t s) {
     if (max_items <= 0 || n_frames <= 0) return cudaSuccess;
-    const size_t smem = binned_smem_bytes(block_cap, kBinnedThreads);
-    const int64_t* p2 = prefix + 2 * (n_frames + 1);
-    if (transposed)
-        return launch_persistent(composite_rays_block_kernel<true>, kBinnedThreads, smem, max_items,
-                                 frames, p2, n_frames, block_cap, cursor, pairs, s);
-    return launch_persistent(composite_rays_block_kernel<false>, kBinnedThreads, smem, max_items,
-                             frames, p2, n_frames, block_cap, cursor, pairs, s);
+    const size_t smem = block_smem_bytes(block_cap);
+    return launch_persistent(composite_rays_block_kernel, kBinnedThreads, smem, max_items, frames,
+                             prefix + 2 * (n_frames + 1), n_frames, block_cap, cursor, pairs, s);
 }
 
 cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,

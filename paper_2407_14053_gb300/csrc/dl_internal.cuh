@@ -111,7 +111,9 @@ cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_p
 cudaError_t launch_store_cams(const CamBatch& b, int32_t n, Cam* dst, cudaStream_t s);
 cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectParams& p,
                            const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s);
-// Keys depth << 32 | Gaussian into their group's slice [gstart[g], gstart[g+1])
+// Keys depth << 32 | Gaussian << 4 (Gaussians < 2^28; the low nibble is left
+// for the block class's quadrant bits) into their group's slice
+// [gstart[g], gstart[g+1])
 // (gfill zeroed by the caller).
 // total_keys (optional) = gstart + n_groups: when it exceeds key_cap no key is
 // written and *status |= 1.
@@ -170,6 +172,8 @@ cudaError_t launch_composite_full(const CompositeParams& p, int32_t nv, const ui
 // {group, ray begin, ray end, -} per DirectL group with rays.
 constexpr int kBinnedThreads = 128;
 size_t binned_smem_bytes(int cap_p, int nthr);
+// Dynamic shared memory of launch_composite_rays_block for a list capacity.
+size_t block_smem_bytes(int cap);
 cudaError_t launch_composite_rays_binned(const CompositeParams& p, const int4* gwork,
                                          const int32_t* list, int64_t n_list, int cap_p,
                                          const int2* grouped, const uint32_t* gstart,
@@ -221,12 +225,14 @@ cudaError_t launch_batch_prefix(const FrameDesc* frames, int32_t n_frames, int64
 cudaError_t launch_composite_rays_warp(int cap, int cls, const FrameDesc* frames,
                                        const int64_t* prefix, int32_t n_frames, int64_t max_items,
                                        uint32_t* cursor, unsigned long long* pairs, cudaStream_t s);
-// Block class (lists longer than 1024 keys, up to block_cap, a power of two
-// <= 16384; longer lists set status bit 1 and are skipped), persistent.
+// Block class (the block lists: lists too long for the warp classes, up to
+// block_cap keys, a power of two <= 16384; longer lists set status bit 1 and
+// are skipped), persistent: four warps sort a list together, then warp q
+// composites the rays in quadrant q of the tile over the records whose key
+// marks quadrant q.
 cudaError_t launch_composite_rays_block(int block_cap, const FrameDesc* frames,
                                         const int64_t* prefix, int32_t n_frames, int64_t max_items,
-                                        uint32_t* cursor, unsigned long long* pairs, int transposed,
-                                        cudaStream_t s);
+                                        uint32_t* cursor, unsigned long long* pairs, cudaStream_t s);
 // Splits work entries by their group's key count: <= small_cap -> small
 // list, else large list; meta = {n_small, n_large, max count}.  gwork NULL:
 // the entries are the groups 0..n_work-1 themselves.

@@ -70,7 +70,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 template <typename T, int DEG>
-__global__ void __launch_bounds__(256) project_kernel(GaussiansView<T> G, ProjectParams p,
+__global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, ProjectParams p,
                                                       const Cam* __restrict__ cams, int32_t nv,
                                                       ProjectOut out) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
@@ -249,7 +249,10 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
 
 // Binned emission: every (view, tile, Gaussian) key goes straight into its
 // group's slice of the key array (slot from an atomic cursor); the order
-// inside a group is fixed later by sorting the unique keys depth << 32 | index.
+// inside a group is fixed later by sorting the unique keys
+// depth << 32 | index << 4.  The low nibble stays free for the quadrant bits
+// that the block class sets after sorting; the index is unique in a group, so
+// they never decide the order.
 __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
                                    const uint32_t* __restrict__ count,
                                    const uint32_t* __restrict__ gstart, uint32_t* __restrict__ gfill,
@@ -274,7 +277,7 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
         if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
         const int64_t v = e / p.n;
         const uint32_t gidx = uint32_t(e - v * p.n);
-        const unsigned long long key = ((unsigned long long)dk << 32) | gidx;
+        const unsigned long long key = ((unsigned long long)dk << 32) | (gidx << 4);
         const uint32_t vb = uint32_t(v) * uint32_t(ntiles);
         const int lane = threadIdx.x & 31;
         const unsigned lt = (1u << lane) - 1u;
