@@ -171,6 +171,16 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                           const double L0_c2w[16], int32_t mode, float* out,
                           int32_t out_on_device, void* stream);
 
+/* Encoded image from per-ray colours (Sec. 4 step (3) and Sec. 6: the rays
+ * of U_rays are rendered by any renderer, then the subpixels take their
+ * channel by the precomputed ray indices): out[i] = ray_rgb[3 ray_of[i] +
+ * (i mod 3)] for the 3wh subpixels i = (x*w + y)*3 + k.  ray_rgb: device,
+ * N_rays x 3 FP32 (RGB of ray r, rays numbered as dl_get_ray_table reports
+ * them); out: device, h x w x 3 FP32 (caller-owned).  Enqueued on `stream`;
+ * NULL pointers are DL_ERR_INVALID_ARG. */
+dl_status dl_encode_rays(dl_ctx* ctx, int32_t display_id, const float* ray_rgb, float* out,
+                         void* stream);
+
 /* Device bytes the last frame of (scene, display, mode) used for scratch,
  * or an estimate before any frame was rendered. */
 dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, int32_t mode,

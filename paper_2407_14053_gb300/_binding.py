@@ -77,6 +77,7 @@ SIGNATURES = {
                                   c_int32, c_void_p]),
     "dl_query_footprint": (c_int32, [c_void_p, c_int32, c_int32, c_int32, P(ctypes.c_size_t)]),
     "dl_set_tile": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
+    "dl_encode_rays": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "dl_enable_stage_timing": (c_int32, [c_void_p, c_int32]),
     "dl_last_frame_stats": (c_int32, [c_void_p, P(dl_frame_stats)]),
     "dl_stage_totals": (c_int32, [c_void_p, P(dl_frame_stats), P(c_int32)]),
@@ -220,6 +221,11 @@ def dl_query_footprint(ctx, scene_id: int, display_id: int, mode: int) -> int:
     _check("dl_query_footprint", ctx,
            lib().dl_query_footprint(ctx, int(scene_id), int(display_id), int(mode), ctypes.byref(b)))
     return b.value
+
+
+def dl_encode_rays(ctx, display_id: int, ray_rgb_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _check("dl_encode_rays", ctx, lib().dl_encode_rays(ctx, int(display_id), c_void_p(ray_rgb_ptr),
+                                                       c_void_p(out_ptr), c_void_p(stream)))
 
 
 def dl_set_tile(ctx, mode: int, tile_w: int, tile_h: int) -> None:

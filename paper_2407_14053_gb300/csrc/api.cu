@@ -531,6 +531,20 @@ dl_status dl_get_ray_table(dl_ctx* ctx, int32_t display_id, uint32_t* ray_of, in
     return DL_OK;
 }
 
+dl_status dl_encode_rays(dl_ctx* ctx, int32_t display_id, const float* ray_rgb, float* out,
+                         void* stream) {
+    dl_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!ray_rgb || !out) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
+    auto it = ctx->displays.find(display_id);
+    if (it == ctx->displays.end()) return fail(ctx, DL_ERR_NOT_FOUND, "display %d", display_id);
+    const Display& D = *it->second;
+    DL_CK(launch_reorder(D.rep.ray_of.as<uint32_t>(), ray_rgb, 3 * int64_t(D.q.w) * D.q.h, out,
+                         nullptr, static_cast<cudaStream_t>(stream)),
+          "encode rays");
+    return DL_OK;
+}
+
 dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h) {
     dl_status st = check_ctx(ctx);
     if (st) return st;

@@ -672,7 +672,7 @@ struct RayTable {
 
 template <int CAP>
 struct WarpSmem {
-    static constexpr int kBuckets = CAP / 2;
+    static constexpr int kBuckets = CAP / 4;  // ~4 keys a bucket: insertion-sorted
     unsigned long long sk[CAP];
     uint32_t bstart[kBuckets + 1];
     uint32_t bfill[kBuckets];
@@ -1026,7 +1026,7 @@ __device__ __forceinline__ int4 batch_item(const FrameDesc* __restrict__ F,
 // frame f.  While one group is composited, the next item is loaded and its
 // keys and rays are prefetched into L2.
 template <int CAP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 6)  // 6 blocks (24 warps) a SM
 composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __restrict__ prefix,
                            int n_frames, int cls, uint32_t* __restrict__ cursor,
                            unsigned long long* __restrict__ pairs) {

@@ -102,6 +102,18 @@ class Renderer:
         B.dl_get_ray_table(self.ctx, did, ray_of.ctypes.data, rays.ctypes.data, 0, _stream())
         return ray_of, rays
 
+    def encode_rays(self, did: int, ray_rgb: torch.Tensor, out: torch.Tensor | None = None):
+        """Encoded frame (h, w, 3) from per-ray RGB (N_rays, 3) on the device,
+        rays numbered as ``ray_table`` reports them."""
+        w, h, _ = self._displays[did]
+        n_rays, _ = self.display_info(did)
+        assert ray_rgb.is_cuda and ray_rgb.dtype == torch.float32 and ray_rgb.is_contiguous()
+        assert ray_rgb.numel() == 3 * n_rays
+        if out is None:
+            out = torch.empty((h, w, 3), dtype=torch.float32, device=ray_rgb.device)
+        B.dl_encode_rays(self.ctx, did, ray_rgb.data_ptr(), out.data_ptr(), _stream())
+        return out
+
     # -- frames -----------------------------------------------------------
     def set_tile(self, mode: str, tile_w: int, tile_h: int) -> None:
         B.dl_set_tile(self.ctx, MODES[mode], tile_w, tile_h)

@@ -58,3 +58,32 @@ def test_paper_panel_tables(renderer, name):
 ])
 def test_edge_displays(renderer, kw):
     _check_tables(renderer, W.Display(**kw))
+
+
+def test_encode_rays_is_the_ray_table_gather(renderer):
+    # any per-ray renderer plugs in: per-ray colours -> encoded image by the
+    # repurposing table (Sec. 4 step (3)), bit for bit
+    import torch
+    d = W.Display(160, 90, 45, 5.3, 1 / 6)
+    did = renderer.set_display(d)
+    ray_of, rays = renderer.ray_table(did)
+    rng = np.random.default_rng(4)
+    rgb = rng.uniform(-1, 2, size=(rays.shape[0], 3)).astype(np.float32)
+    out = renderer.encode_rays(did, torch.as_tensor(rgb).cuda())
+    torch.cuda.synchronize()
+    k = np.arange(3)[None, None, :]
+    assert np.array_equal(out.cpu().numpy(), rgb[ray_of, np.broadcast_to(k, ray_of.shape)])
+    # a DirectL frame's subpixels regathered into ray colours re-encode to
+    # the same frame
+    scene = W.make_scene(W.SceneSpec(800, 1, "uniform", "f32", seed=3))
+    sid = renderer.load_gaussians(scene, "f32")
+    frame = renderer.render(sid, did, W.light_field_centre(4.0, 0.0), "directl")
+    torch.cuda.synchronize()
+    f = frame.cpu().numpy().reshape(-1)
+    ray_rgb = np.zeros((rays.shape[0], 3), np.float32)
+    ray_rgb[ray_of.reshape(-1), np.tile(np.arange(3), ray_of.size // 3)] = f
+    again = renderer.encode_rays(did, torch.as_tensor(ray_rgb).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(again.cpu().numpy().reshape(-1), f)
+    renderer.free_scene(sid)
+    renderer.free_display(did)
