@@ -266,34 +266,71 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
     const int64_t total = int64_t(nv) * p.n;
     const int ntiles = p.ntx * p.nty;
     const uint32_t zbits0 = __float_as_uint(0.2f);
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        if (!count[e]) continue;
-        const float4 q2 = rec[3 * e + 2];
-        const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
-        const int tx0 = int(rx & 0xFFFF) / p.tile_w, tx1 = int(rx >> 16) / p.tile_w;
-        const int ty0 = int(ry & 0xFFFF) / p.tile_h, ty1 = int(ry >> 16) / p.tile_h;
-        uint32_t dk = __float_as_uint(q2.y) - zbits0;
-        if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
-        const int64_t v = e / p.n;
-        const uint32_t gidx = uint32_t(e - v * p.n);
-        const unsigned long long key = ((unsigned long long)dk << 32) | (gidx << 4);
-        const uint32_t vb = uint32_t(v) * uint32_t(ntiles);
-        const int lane = threadIdx.x & 31;
-        const unsigned lt = (1u << lane) - 1u;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                // lanes of the warp on the same group take consecutive slots
-                // with one atomic
-                const uint32_t grp = vb + uint32_t(ty * p.ntx + tx);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    // each warp takes 32 consecutive records and expands their (record,
+    // tile) pairs into dense rounds of 32, so every lane emits a key per
+    // round and each round costs one cursor atomic per group it touches
+    for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < total;
+         w += warps) {
+        const int64_t e = w * 32 + lane;
+        uint32_t cnt = e < total ? count[e] : 0u;
+        int tx0 = 0, ty0 = 0, span = 1;
+        uint32_t vb = 0, khi = 0, klo = 0;
+        if (cnt) {
+            const float4 q2 = rec[3 * e + 2];
+            const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
+            tx0 = int(rx & 0xFFFF) / p.tile_w;
+            span = int(rx >> 16) / p.tile_w - tx0 + 1;
+            ty0 = int(ry & 0xFFFF) / p.tile_h;
+            uint32_t dk = __float_as_uint(q2.y) - zbits0;
+            if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
+            const int64_t v = e / p.n;
+            khi = dk;
+            klo = uint32_t(e - v * p.n) << 4;
+            vb = uint32_t(v) * uint32_t(ntiles);
+        }
+        uint32_t incl = cnt;  // inclusive scan of the pair counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t off = incl - cnt, n_pairs = __shfl_sync(0xffffffffu, incl, 31);
+        const float rspan = 1.0f / float(span);
+        for (uint32_t r0 = 0; r0 < n_pairs; r0 += 32) {
+            const uint32_t pr = r0 + uint32_t(lane);
+            // owner: the last lane whose first pair is <= pr
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t o2 = __shfl_sync(0xffffffffu, off, src + step);
+                if (o2 <= pr) src += step;
+            }
+            const uint32_t k = pr - __shfl_sync(0xffffffffu, off, src);
+            const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src);
+            const int s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
+            const int s_span = __shfl_sync(0xffffffffu, span, src);
+            const float s_r = __shfl_sync(0xffffffffu, rspan, src);
+            const uint32_t s_vb = __shfl_sync(0xffffffffu, vb, src);
+            const uint32_t s_hi = __shfl_sync(0xffffffffu, khi, src);
+            const uint32_t s_lo = __shfl_sync(0xffffffffu, klo, src);
+            if (pr < n_pairs) {
+                // k = dy * span + dx; the +0.5 keeps the float quotient's floor exact
+                const int dy = int((float(k) + 0.5f) * s_r);
+                const int dx = int(k) - dy * s_span;
+                const uint32_t grp = s_vb + uint32_t((s_ty0 + dy) * p.ntx + s_tx0 + dx);
                 const unsigned am = __activemask();
                 const unsigned peers = __match_any_sync(am, grp);
                 const int leader = __ffs(peers) - 1;
                 uint32_t base = 0;
                 if (lane == leader) base = atomicAdd(gfill + grp, uint32_t(__popc(peers)));
                 base = __shfl_sync(peers, base, leader);
-                keys[gstart[grp] + base + __popc(peers & lt)] = key;
+                keys[gstart[grp] + base + __popc(peers & lt)] =
+                    ((unsigned long long)s_hi << 32) | s_lo;
             }
+        }
     }
 }
 
