@@ -56,16 +56,18 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ float log2_alpha(float px, float py, float u, float v, float A, float B,
                                             float C, float L) {
     const float dx = px - u, dy = py - v;
-    return fmaf(A * dx, dx, fmaf(B * dx, dy, fmaf(C * dy, dy, L)));
+    return fmaf(dx, fmaf(A, dx, B * dy), fmaf(C * dy, dy, L));
 }
 
 // One record against one ray.  Returns false once the ray is finished.
-// alpha = min(0.99, 2^log2_alpha); skip alpha < 1/255 (tested first on
-// log2 alpha, then on alpha itself); stop before T would drop below 1e-4.
+// alpha = min(0.99, 2^log2_alpha); skip alpha < 1/255 (CHECK_L2: tested
+// first on log2 alpha, which spares the ex2 for records that miss the ray,
+// then on alpha itself); stop before T would drop below 1e-4.
+template <bool CHECK_L2 = true>
 __device__ __forceinline__ bool blend(Acc& a, float px, float py, const float4& q0,
                                       const float4& q1, float b) {
     const float l2 = log2_alpha(px, py, q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
-    if (l2 < kLog2MinAlpha) return true;
+    if (CHECK_L2 && l2 < kLog2MinAlpha) return true;
     const float alpha = fminf(0.99f, ex2_approx(l2));
     if (alpha < (1.0f / 255.0f)) return true;
     const float Tn = a.T * (1.f - alpha);
@@ -845,10 +847,10 @@ __device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const
     __syncwarp();
     unsigned mine = (act >> lane) & 1u ? T.mask[lane] : 0u;
     if (!done) evals += uint32_t(n);
-    while (mine && !done) {
+    while (mine && !done) {  // candidates passed the (widened) test: alpha decides
         const int sidx = __ffs(mine) - 1;
         mine &= mine - 1;
-        if (!blend(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
+        if (!blend<false>(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
     }
     __syncwarp();
 }

@@ -200,16 +200,10 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
             my_total += cnt;
         }
     }
-    // block sum of the tile counts -> one 64-bit atomic per block
-    __shared__ unsigned long long s_part[8];
+    // warp sum of the tile counts -> one 64-bit atomic per warp (no block
+    // barrier: warps finish at different times)
     my_total = warp_sum(my_total);
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = my_total;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += s_part[w];
-        if (t) atomicAdd(out.total, t);
-    }
+    if ((threadIdx.x & 31) == 0 && my_total) atomicAdd(out.total, my_total);
 }
 
 // Key of a (view, tile, Gaussian) overlap: (view*ntiles + tile) << 28 | depth
