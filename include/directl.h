@@ -114,7 +114,13 @@ dl_status dl_free_scene(dl_ctx* ctx, int32_t scene_id);
  * theta_d, the angle between the outermost cameras of the arc;
  * fov_x_deg = horizontal field of view of every camera.  repurpose = 1
  * applies Alg. 2, 0 gives every subpixel its own pixel.  reverse_views = 1
- * makes view 0 the rightmost camera.  1 <= width, height <= 16384,
+ * makes view 0 the rightmost camera.  rig selects the camera arrangement of
+ * Sec. 3.2: 0 = cameras on an arc about the world origin, each looking at
+ * it (T_v = R_y(-theta_v) L0); 1 = "off-axis perspective with straight
+ * lines": L0 translated by x_v = D tan(theta_v) along its own x axis (D = the
+ * depth of the world origin in L0's camera, which must be positive), all
+ * axes parallel, each view's principal point shifted by f x_v / D columns
+ * so that the plane at depth D has no parallax.  1 <= width, height <= 16384,
  * 1 <= num_views <= 65535.
  */
 typedef struct {
@@ -122,6 +128,7 @@ typedef struct {
     double pitch_lx, tan_slant, offset_k;
     double view_span_deg, fov_x_deg;
     int32_t repurpose, reverse_views;
+    int32_t rig;
 } dl_display_params;
 
 /*

@@ -48,7 +48,7 @@ class OrDisplay(ctypes.Structure):
                 ("pitch_lx", ctypes.c_double), ("tan_slant", ctypes.c_double),
                 ("offset_k", ctypes.c_double), ("view_span_deg", ctypes.c_double),
                 ("fov_x_deg", ctypes.c_double), ("repurpose", ctypes.c_int32),
-                ("reverse_views", ctypes.c_int32)]
+                ("reverse_views", ctypes.c_int32), ("rig", ctypes.c_int32)]
 
 
 class OrScene(ctypes.Structure):
@@ -77,12 +77,16 @@ def _load():
             lib.or_area_map.argtypes = [P, P]
             lib.or_repurpose.argtypes = [P, P, P]
             lib.or_ray_table.argtypes = [P, P, P, P, P, P, P, P]
-            lib.or_cameras.argtypes = [P, P, P]
+            lib.or_cameras.argtypes = [P, P, P, P]
             lib.or_sh_basis.argtypes = [P, P]
             lib.or_sh_basis.restype = None
             lib.or_project_splat.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int32,
                                              ctypes.c_int32, P]
             lib.or_project_splat.restype = None
+            lib.or_project_splat_shift.argtypes = [P, ctypes.c_int64, P, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                                   P]
+            lib.or_project_splat_shift.restype = None
             lib.or_render_rays.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P, P, P, P,
                                            ctypes.c_int]
             lib.or_interweave.argtypes = [P, P, P, P]
@@ -101,7 +105,8 @@ def _ptr(a: np.ndarray):
 def _disp(d) -> OrDisplay:
     return OrDisplay(int(d.width), int(d.height), int(d.num_views), int(d.p_w), float(d.pitch_lx),
                      float(d.tan_slant), float(d.offset_k), float(d.view_span_deg),
-                     float(d.fov_x_deg), int(d.repurpose), int(d.reverse_views))
+                     float(d.fov_x_deg), int(d.repurpose), int(d.reverse_views),
+                     int(getattr(d, "rig", 0)))
 
 
 def _check(rc: int, what: str):
@@ -167,13 +172,16 @@ def ray_table(display, V: np.ndarray, src: np.ndarray):
     return ray_of, np.stack([rv[:k], rr[:k], rc[:k]], axis=1)
 
 
-def cameras(display, L0: np.ndarray) -> np.ndarray:
+def cameras(display, L0: np.ndarray, with_shift: bool = False):
+    """Camera-to-world poses of the views (N_v, 4, 4); with_shift also
+    returns each view's principal-point shift along the columns (pixels)."""
     lib = _load()
     L0 = np.ascontiguousarray(L0, dtype=np.float64)
     out = np.empty((display.num_views, 4, 4), dtype=np.float64)
+    shift = np.empty(display.num_views, dtype=np.float64)
     d = _disp(display)
-    _check(lib.or_cameras(ctypes.byref(d), _ptr(L0), _ptr(out)), "cameras")
-    return out
+    _check(lib.or_cameras(ctypes.byref(d), _ptr(L0), _ptr(out), _ptr(shift)), "cameras")
+    return (out, shift) if with_shift else out
 
 
 def sh_basis(direction) -> np.ndarray:
@@ -202,12 +210,14 @@ def focal(display) -> float:
     return 0.5 * display.width / np.tan(np.radians(0.5 * display.fov_x_deg))
 
 
-def project(scene: Scene, g: int, c2w: np.ndarray, display) -> dict:
+def project(scene: Scene, g: int, c2w: np.ndarray, display, shift: float = 0.0) -> dict:
+    """Gaussian g in one camera (principal point at (w/2 + shift, h/2))."""
     lib = _load()
     c2w = np.ascontiguousarray(c2w, dtype=np.float64)
     sp = OrSplat()
-    lib.or_project_splat(ctypes.byref(scene.c), int(g), _ptr(c2w), float(focal(display)),
-                         int(display.width), int(display.height), ctypes.byref(sp))
+    lib.or_project_splat_shift(ctypes.byref(scene.c), int(g), _ptr(c2w), float(focal(display)),
+                               float(shift), int(display.width), int(display.height),
+                               ctypes.byref(sp))
     return {"u": sp.u, "v": sp.v, "conic": np.array(sp.conic[:]), "cov2d": np.array(sp.cov2d[:]),
             "opacity": sp.opacity, "rgb": np.array(sp.rgb[:]), "depth": sp.depth,
             "valid": bool(sp.valid)}

@@ -283,13 +283,27 @@ int or_ray_table(const or_display* p, const uint16_t* V, const uint32_t* src,
  * R_v turns the light-field centre about the world y axis through the origin
  * so that a positive theta moves the camera towards its own +x (right):
  * T_v = R_y(-theta_v) L_0. */
-int or_cameras(const or_display* p, const double L0[16], double* c2w) {
+int or_cameras(const or_display* p, const double L0[16], double* c2w, double* shift) {
     const double pi = 3.14159265358979323846;
+    /* off-axis rig: depth of the world origin in L0's camera (camera z axis
+     * = third column of the rotation) */
+    const double D = -(L0[2] * L0[3] + L0[6] * L0[7] + L0[10] * L0[11]);
+    const double focal = 0.5 * p->width / tan(0.5 * p->fov_x_deg * pi / 180.0);
+    if (p->rig == 1 && !(D > 0.0)) return -1;
     for (int32_t v = 0; v < p->num_views; ++v) {
         int32_t vv = p->reverse_views ? p->num_views - 1 - v : v;
         double th = 0.0;
         if (p->num_views > 1)
             th = (-0.5 * p->view_span_deg + vv * p->view_span_deg / (p->num_views - 1)) * pi / 180.0;
+        if (p->rig == 1) {
+            const double xv = D * tan(th);
+            double* T = c2w + 16 * (int64_t)v;
+            for (int i = 0; i < 16; ++i) T[i] = L0[i];
+            for (int i = 0; i < 3; ++i) T[4 * i + 3] = L0[4 * i + 3] + xv * L0[4 * i + 0];
+            if (shift) shift[v] = focal * xv / D;
+            continue;
+        }
+        if (shift) shift[v] = 0.0;
         double phi = -th;
         double R[16] = {cos(phi), 0, sin(phi), 0, 0, 1, 0, 0, -sin(phi), 0, cos(phi), 0, 0, 0, 0, 1};
         double* T = c2w + 16 * (int64_t)v;
@@ -346,6 +360,11 @@ void or_sh_basis(const double d[3], double o[16]) {
  * colour = max(0, SH(dir) + 0.5) with dir = normalise(mu - camera centre). */
 void or_project_splat(const or_scene* sc, int64_t g, const double c2w[16], double focal,
                       int32_t width, int32_t height, or_splat* out) {
+    or_project_splat_shift(sc, g, c2w, focal, 0.0, width, height, out);
+}
+
+void or_project_splat_shift(const or_scene* sc, int64_t g, const double c2w[16], double focal,
+                            double shift, int32_t width, int32_t height, or_splat* out) {
     memset(out, 0, sizeof(*out));
     const double* mu = sc->mean + 3 * g;
     double Rc[3][3], cen[3];
@@ -390,9 +409,12 @@ void or_project_splat(const or_scene* sc, int64_t g, const double c2w[16], doubl
     /* Sigma' = J W Sigma W^T J^T, Eq. (9), J the Jacobian of the perspective map */
     double thx = 0.5 * width / focal, thy = 0.5 * height / focal;
     double limx = 1.3 * thx, limy = 1.3 * thy;
+    /* the clamp window follows a shifted principal point: x/z + shift/f in
+     * [-limx, limx] */
+    const double sz = shift / focal;
     double xz = t[0] / t[2], yz = t[1] / t[2];
-    if (xz < -limx) xz = -limx;
-    if (xz > limx) xz = limx;
+    if (xz < -limx - sz) xz = -limx - sz;
+    if (xz > limx - sz) xz = limx - sz;
     if (yz < -limy) yz = -limy;
     if (yz > limy) yz = limy;
     double J[2][3] = {{focal / t[2], 0.0, -focal * xz / t[2]}, {0.0, focal / t[2], -focal * yz / t[2]}};
@@ -414,7 +436,7 @@ void or_project_splat(const or_scene* sc, int64_t g, const double c2w[16], doubl
     out->conic[0] = C2[1][1] / det;
     out->conic[1] = -C2[0][1] / det;
     out->conic[2] = C2[0][0] / det;
-    out->u = focal * t[0] / t[2] + 0.5 * width;
+    out->u = focal * t[0] / t[2] + 0.5 * width + shift;
     out->v = focal * t[1] / t[2] + 0.5 * height;
     out->opacity = 1.0 / (1.0 + exp(-sc->opacity_logit[g]));
 
@@ -598,12 +620,13 @@ int or_render_rays(const or_scene* sc, const or_display* p, const double L0[16],
     const int32_t nv = p->num_views;
     for (int64_t i = 0; i < n_rays; ++i)
         if (ray_v[i] < 0 || ray_v[i] >= nv) return -1;
-    double* cams = (double*)malloc(sizeof(double) * 16 * (size_t)nv);
+    double* cams = (double*)malloc(sizeof(double) * 17 * (size_t)nv);
     or_splat* sp = (or_splat*)malloc(sizeof(or_splat) * (size_t)(sc->n > 0 ? sc->n : 1));
     int64_t* cnt = (int64_t*)calloc((size_t)nv + 1, sizeof(int64_t));
     int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_rays > 0 ? n_rays : 1));
     if (!cams || !sp || !cnt || !idx) { free(cams); free(sp); free(cnt); free(idx); return -2; }
-    or_cameras(p, L0, cams);
+    double* shift = cams + 16 * (size_t)nv;
+    if (or_cameras(p, L0, cams, shift)) { free(cams); free(sp); free(cnt); free(idx); return -1; }
     const double pi = 3.14159265358979323846;
     const double focal = 0.5 * p->width / tan(0.5 * p->fov_x_deg * pi / 180.0);
     /* group the rays by view */
@@ -619,7 +642,8 @@ int or_render_rays(const or_scene* sc, const or_display* p, const double L0[16],
         if (cnt[v + 1] == cnt[v]) continue;
         const double* T = cams + 16 * (int64_t)v;
 #pragma omp parallel for schedule(static)
-        for (int64_t g = 0; g < sc->n; ++g) or_project_splat(sc, g, T, focal, p->width, p->height, sp + g);
+        for (int64_t g = 0; g < sc->n; ++g)
+            or_project_splat_shift(sc, g, T, focal, shift[v], p->width, p->height, sp + g);
 #pragma omp parallel for schedule(dynamic, 8)
         for (int64_t j = cnt[v]; j < cnt[v + 1]; ++j) {
             int64_t i = idx[j];

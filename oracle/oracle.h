@@ -14,7 +14,9 @@
  *                          (iteration order, search order, buffer capacity):
  *                          parity unpinned for the exact tie-breaking.
  *   or_ray_table           pinned by invariants (R-first order, uniqueness).
- *   or_cameras             pinned (arc radius, angles, look-at, leftmost v=0).
+ *   or_cameras             pinned (arc radius, angles, look-at, leftmost v=0;
+ *                          off-axis rig: parallel axes, straight baseline,
+ *                          no parallax on the convergence plane).
  *   or_project_splat /     pinned (isotropic closed form, finite-difference
  *   or_render_rays         Jacobian, 1-3 Gaussian brute force, back-to-front
  *                          identity, SH addition theorem and orthonormality).
@@ -40,6 +42,7 @@ typedef struct {
     double fov_x_deg;        /* horizontal field of view of each camera    */
     int32_t repurpose;       /* 0 = identity assignment, 1 = Alg. 2        */
     int32_t reverse_views;   /* 1 = view 0 is the rightmost camera         */
+    int32_t rig;             /* 0 = arc (Sec. 3.2), 1 = off-axis straight line */
 } or_display;
 
 /* Gaussian scene, FP64 structure of arrays. */
@@ -84,8 +87,14 @@ int or_ray_table(const or_display* p, const uint16_t* V, const uint32_t* src,
                  uint32_t* ray_of, int32_t* ray_v, int32_t* ray_r, int32_t* ray_c,
                  int64_t* n_rays);
 
-/* Camera-to-world poses of every view (N_v x 16, row-major): T_v = R_v L_0. */
-int or_cameras(const or_display* p, const double L0[16], double* c2w);
+/* Camera-to-world poses of every view (N_v x 16, row-major) and the shift of
+ * each view's principal point along the image columns (N_v pixels; may be
+ * NULL).  rig 0: T_v = R_v L_0 on an arc (Sec. 3.2), no shift.  rig 1: the
+ * "off-axis perspective with straight lines" of Sec. 3.2: L_0 translated by
+ * D tan(theta_v) along its x axis, D the depth of the world origin in L_0's
+ * camera, and the principal point shifted by f x_v / D so that the plane at
+ * depth D has no parallax.  Returns -1 when D <= 0 for rig 1. */
+int or_cameras(const or_display* p, const double L0[16], double* c2w, double* shift);
 
 /* Real spherical-harmonic basis up to degree 3 at a unit direction. */
 void or_sh_basis(const double dir[3], double out[16]);
@@ -93,6 +102,9 @@ void or_sh_basis(const double dir[3], double out[16]);
 /* Project Gaussian g of the scene into a camera (c2w, 4x4 row-major). */
 void or_project_splat(const or_scene* sc, int64_t g, const double c2w[16],
                       double focal, int32_t width, int32_t height, or_splat* out);
+/* The same with the principal point at (w/2 + shift, h/2). */
+void or_project_splat_shift(const or_scene* sc, int64_t g, const double c2w[16], double focal,
+                            double shift, int32_t width, int32_t height, or_splat* out);
 
 /* Colour of rays (view, row, col) by front-to-back compositing over every
  * Gaussian.  rgb/lo/hi are n_rays*3; lo/hi bound the results of the

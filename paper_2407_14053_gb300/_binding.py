@@ -42,7 +42,7 @@ class dl_display_params(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("num_views", c_int32), ("p_w", c_int32),
                 ("pitch_lx", c_double), ("tan_slant", c_double), ("offset_k", c_double),
                 ("view_span_deg", c_double), ("fov_x_deg", c_double), ("repurpose", c_int32),
-                ("reverse_views", c_int32)]
+                ("reverse_views", c_int32), ("rig", c_int32)]
 
 
 class dl_frame_stats(ctypes.Structure):

@@ -54,6 +54,7 @@ bool pow2_in(int32_t v, int32_t lo, int32_t hi) {
 dl_status make_display_q(dl_ctx* ctx, const dl_display_params& p, DisplayQ* q) {
     if (p.width < 1 || p.height < 1 || p.width > 16384 || p.height > 16384)
         return fail(ctx, DL_ERR_INVALID_ARG, "panel size %dx%d out of range", p.width, p.height);
+    if (p.rig != 0 && p.rig != 1) return fail(ctx, DL_ERR_INVALID_ARG, "rig %d", p.rig);
     if (p.num_views < 1 || p.num_views > 65535)
         return fail(ctx, DL_ERR_INVALID_ARG, "num_views %d out of range", p.num_views);
     if (p.p_w < 1) return fail(ctx, DL_ERR_INVALID_ARG, "p_w must be >= 1");
@@ -209,23 +210,35 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
 // View cameras: T_v = R_y(-theta_v) L0 (Eq. (17)); theta_v = -theta_d/2 +
 // v theta_d/(N_v-1), view 0 the leftmost unless reverse_views.  Computed in
 // double on the host, handed to the kernels as float world->camera matrices.
-void make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>& cams) {
+bool make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>& cams) {
     cams.resize(size_t(p.num_views));
     const double pi = 3.14159265358979323846;
+    // off-axis rig: depth of the world origin in L0's camera
+    const double D = -(L0[2] * L0[3] + L0[6] * L0[7] + L0[10] * L0[11]);
+    const double focal = 0.5 * p.width / std::tan(0.5 * p.fov_x_deg * pi / 180.0);
+    if (p.rig == 1 && !(D > 0.0)) return false;
     for (int32_t v = 0; v < p.num_views; ++v) {
         const int32_t vv = p.reverse_views ? p.num_views - 1 - v : v;
         double th = 0.0;
         if (p.num_views > 1)
             th = (-0.5 * p.view_span_deg + vv * p.view_span_deg / (p.num_views - 1)) * pi / 180.0;
-        const double ph = -th, cs = std::cos(ph), sn = std::sin(ph);
-        const double Ry[3][3] = {{cs, 0, sn}, {0, 1, 0}, {-sn, 0, cs}};
         double T[3][4];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 4; ++j) {
-                double a = 0.0;
-                for (int k = 0; k < 3; ++k) a += Ry[i][k] * L0[4 * k + j];
-                T[i][j] = a;  // last row of L0 is (0,0,0,1): no contribution
-            }
+        double shift = 0.0;
+        if (p.rig == 1) {  // L0 moved by D tan(theta) along its x axis
+            const double xv = D * std::tan(th);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 4; ++j) T[i][j] = L0[4 * i + j] + (j == 3 ? xv * L0[4 * i] : 0.0);
+            shift = focal * xv / D;
+        } else {  // T_v = R_y(-theta_v) L0
+            const double ph = -th, cs = std::cos(ph), sn = std::sin(ph);
+            const double Ry[3][3] = {{cs, 0, sn}, {0, 1, 0}, {-sn, 0, cs}};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    double a = 0.0;
+                    for (int k = 0; k < 3; ++k) a += Ry[i][k] * L0[4 * k + j];
+                    T[i][j] = a;  // last row of L0 is (0,0,0,1): no contribution
+                }
+        }
         Cam& c = cams[size_t(v)];
         // world->camera: R_wc = R_cw^T, t = -R_cw^T centre
         for (int i = 0; i < 3; ++i) {
@@ -237,7 +250,10 @@ void make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>
             }
             c.t[i] = float(t);
         }
+        c.shift = float(shift);
+        c.shift_f = float(shift / focal);
     }
+    return true;
 }
 
 dl_status upload_cams(dl_ctx* ctx, const std::vector<Cam>& cams, cudaStream_t s) {
@@ -722,7 +738,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
 
     // ---- cameras (Eq. (17)) and projection (Eqs. (8)-(10)) ----
     std::vector<Cam> cams;
-    make_cams(D.prm, L0_c2w, cams);
+    if (!make_cams(D.prm, L0_c2w, cams))
+        return fail(ctx, DL_ERR_INVALID_ARG, "off-axis rig: the world origin is not in front of L0");
     st = upload_cams(ctx, cams, s);
     if (st) return st;
     const ProjectParams pp = make_project_params(S, D, tw, th);

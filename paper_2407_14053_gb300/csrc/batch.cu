@@ -377,7 +377,8 @@ dl_status dl_batch_assign(dl_batch* b, int32_t slot, int32_t scene_id, int32_t d
     z.pp = make_project_params(*S, *D, tw, th);
     z.ngroups = ng;
     // identity pose until dl_batch_set_pose
-    const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    // a pose on the -z axis at distance 4 until dl_batch_set_pose
+    const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, -4, 0, 0, 0, 1};
     std::vector<Cam> cams;
     make_cams(D->prm, I, cams);
     std::memcpy(b->cams_h() + z.cam_first, cams.data(), sizeof(Cam) * cams.size());
@@ -410,7 +411,8 @@ dl_status dl_batch_set_pose(dl_batch* b, int32_t slot, const double L0_c2w[16]) 
     st = wait_previous(b);
     if (st) return st;
     std::vector<Cam> cams;
-    make_cams(z.D->prm, L0_c2w, cams);
+    if (!make_cams(z.D->prm, L0_c2w, cams))
+        return fail(ctx, DL_ERR_INVALID_ARG, "off-axis rig: the world origin is not in front of L0");
     std::memcpy(b->cams_h() + z.cam_first, cams.data(), sizeof(Cam) * cams.size());
     return DL_OK;
 }

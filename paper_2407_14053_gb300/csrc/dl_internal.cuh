@@ -27,6 +27,8 @@ struct Cam {
     float r[9];
     float t[3];
     float c[3];
+    float shift;    // principal point (w/2 + shift, h/2): off-axis views
+    float shift_f;  // shift / focal
 };
 
 // Cameras of a frame reach the device as a kernel parameter of a one-block

@@ -139,8 +139,9 @@ size_t max_smem_optin(int device);
 // Rays of a ray set grouped by (view, tile) for one tile shape (cached per shape).
 dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th, cudaStream_t s,
                      TileGroups** out);
-// View cameras of Eq. (17) for a light-field centre pose.
-void make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>& cams);
+// View cameras of Eq. (17) (or of the off-axis rig) for a light-field centre
+// pose; false when the off-axis rig's convergence depth is not positive.
+bool make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>& cams);
 // Projection parameters of a frame (tile shape tw x th).
 ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, int32_t th);
 

@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
             if (tz > 0.2f && visible_alpha) {
                 // EWA (Eq. (9)): T = J W, Sigma' = T Sigma T^T + 0.3 I
                 const float iz = 1.f / tz;
-                const float xz = fminf(fmaxf(tx * iz, -p.lim_x), p.lim_x);
+                // the clamp window follows a shifted principal point (off-axis views)
+                const float sz = cam.shift_f;
+                const float xz = fminf(fmaxf(tx * iz, -p.lim_x - sz), p.lim_x - sz);
                 const float yz = fminf(fmaxf(ty * iz, -p.lim_y), p.lim_y);
                 const float fz = p.focal * iz;
                 const float j02 = -fz * xz, j12 = -fz * yz;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
                 const float cyy = b0 * T10 + b1 * T11 + b2 * T12 + 0.3f;
                 const float det = cxx * cyy - cxy * cxy;
                 if (det > 0.f) {
-                    const float uc = p.focal * tx * iz, vc = p.focal * ty * iz;
+                    const float uc = p.focal * tx * iz + cam.shift, vc = p.focal * ty * iz;
                     // pixels where alpha >= 1/255 lie in the ellipse
                     // d^T Sigma'^-1 d <= 2 ln(255 o); its bounding box:
                     const float rx = sqrtf(K * cxx) * 1.0001f + 1e-3f;

@@ -23,7 +23,7 @@ def display_params(d) -> B.dl_display_params:
     return B.dl_display_params(int(d.width), int(d.height), int(d.num_views), int(d.p_w),
                                float(d.pitch_lx), float(d.tan_slant), float(d.offset_k),
                                float(d.view_span_deg), float(d.fov_x_deg), int(d.repurpose),
-                               int(d.reverse_views))
+                               int(d.reverse_views), int(getattr(d, "rig", 0)))
 
 
 class Renderer:

@@ -55,7 +55,8 @@ int main(void) {
   printf("dl_display_params %zu\n", sizeof(dl_display_params));
   printf("dl_frame_stats %zu\n", sizeof(dl_frame_stats));
   P(dl_gaussians_desc, sh) P(dl_gaussians_desc, on_device) P(dl_display_params, pitch_lx)
-  P(dl_display_params, repurpose) P(dl_display_params, reverse_views) P(dl_frame_stats, ms_total)
+  P(dl_display_params, repurpose) P(dl_display_params, reverse_views) P(dl_display_params, rig)
+  P(dl_frame_stats, ms_total)
   P(dl_frame_stats, max_list) P(dl_frame_stats, lists_small)
   return 0;
 }

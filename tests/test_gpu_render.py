@@ -315,3 +315,28 @@ def test_long_tile_lists(renderer, n, expect_binned):
     assert nbad == 0, f"{nbad} outside tolerance; max |err| {maxerr:.3g}"
     renderer.free_display(did)
     renderer.free_scene(sid)
+
+
+@pytest.mark.parametrize("mode", ["directl", "standard"])
+def test_off_axis_rig_full_frame(renderer, mode):
+    # "off-axis perspective with straight lines" (Sec. 3.2): parallel cameras
+    # on a line, principal points shifted so the origin's plane has no parallax
+    from paper_2407_14053_gb300 import DirectLError
+    wl = W.WORKLOADS["tiny"]
+    d = wl.display.replace(rig=1)
+    scene = W.make_scene(wl.scene)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(wl.camera_distance, 2.0)
+    img = _frame(renderer, sid, did, L0, mode).reshape(-1)
+    V, src = _sources(renderer, did, d, mode)
+    ref = oracle.render_subpixels(oracle.Scene(scene), d, L0, np.arange(img.size), V, src)
+    ok, maxerr, nbad = _accept(img, ref, TOL)
+    assert nbad == 0, f"{nbad} of {img.size} outside tolerance; max |err| {maxerr:.3g}"
+    behind = L0.copy()
+    behind[:3, 0] *= -1.0
+    behind[:3, 2] *= -1.0  # looks away from the origin: no convergence depth
+    with pytest.raises(DirectLError):
+        renderer.render(sid, did, behind, mode)
+    renderer.free_display(did)
+    renderer.free_scene(sid)

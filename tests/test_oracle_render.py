@@ -256,3 +256,45 @@ def test_alg1_interweave_equals_per_subpixel_standard():
     Ed = oracle.render_frame(sc, d.replace(repurpose=0), L0, mode="directl")["value"]
     assert np.array_equal(Ed, E)
     assert np.abs(E).max() > 0.05
+
+
+# ---- the off-axis (straight-line) rig of Sec. 3.2 -------------------------
+def _theta(d, v):
+    return math.radians(-0.5 * d.view_span_deg + v * d.view_span_deg / (d.num_views - 1))
+
+
+def test_off_axis_rig_cameras():
+    d = W.Display(240, 135, 9, 5.3, 1 / 6, view_span_deg=24.0, rig=1)
+    L0 = W.light_field_centre(4.0, 7.0)
+    c2w, shift = oracle.cameras(d, L0, with_shift=True)
+    f = oracle.focal(d)
+    for v in range(d.num_views):
+        xv = 4.0 * math.tan(_theta(d, v))
+        assert np.array_equal(c2w[v, :3, :3], L0[:3, :3])            # parallel axes
+        assert np.allclose(c2w[v, :3, 3], L0[:3, 3] + xv * L0[:3, 0], atol=1e-12)
+        assert shift[v] == pytest.approx(f * xv / 4.0, rel=1e-12)
+    assert c2w[0, :3, 3] @ L0[:3, 0] < c2w[-1, :3, 3] @ L0[:3, 0]     # view 0 leftmost
+    arc = oracle.cameras(d.replace(rig=0), L0)
+    assert np.allclose(arc[4], c2w[4], atol=1e-12)                     # same centre view
+    with pytest.raises(RuntimeError):                                  # origin behind L0
+        flipped = L0.copy()
+        flipped[:3, 2] *= -1.0
+        flipped[:3, 0] *= -1.0
+        oracle.cameras(d, flipped)
+
+
+def test_off_axis_rig_has_no_parallax_on_the_convergence_plane():
+    d = W.Display(240, 135, 7, 5.3, 1 / 6, view_span_deg=30.0, rig=1)
+    L0 = W.light_field_centre(4.0, 0.0)            # optical axis = world +z, origin at depth 4
+    c2w, shift = oracle.cameras(d, L0, with_shift=True)
+    sc = W.make_scene(W.SceneSpec(3, 0, "uniform", "f32", seed=1))
+    sc["mean"][:] = np.array([[0.3, -0.2, 0.0], [0.1, 0.15, -1.0], [-0.2, 0.1, 1.5]], np.float32)
+    scene = oracle.Scene(sc)
+    us = np.array([[oracle.project(scene, g, c2w[v], d, shift[v])["u"] for v in range(7)]
+                   for g in range(3)])
+    vs = np.array([[oracle.project(scene, g, c2w[v], d, shift[v])["v"] for v in range(7)]
+                   for g in range(3)])
+    assert np.ptp(us[0]) < 1e-9 and np.ptp(vs[0]) < 1e-9   # on the plane: one pixel in all views
+    assert np.all(np.diff(us[1]) < 0)                        # nearer: moves left as x_v grows
+    assert np.all(np.diff(us[2]) > 0)                        # farther: moves right
+    assert np.ptp(vs[1]) < 1e-9                              # a horizontal rig: rows do not move

@@ -58,6 +58,7 @@ class Display:
     p_w: int = 2
     repurpose: int = 1
     reverse_views: int = 0
+    rig: int = 0  # 0: cameras on an arc; 1: off-axis cameras on a straight line
 
     def replace(self, **kw) -> "Display":
         return dataclasses.replace(self, **kw)
