@@ -492,6 +492,23 @@ def main():
         std = {"frames_per_s": fps_s, "subpixels_per_s": fps_s * subpix, "ms_per_frame": ms_s / k_std,
                "steps": k_std, "stages_ms": per_frame(tot_s, nf_s),
                "speedup_directl_over_standard": fps / fps_s}
+        # the paper's LR / MR configurations of the standard paradigm (views
+        # rendered smaller, upsampled while interweaving); 4K panel sizes
+        # from its display table, other panels scaled by the same factors
+        lowres = {}
+        for name, frac in (("lr", 800 / 3840), ("mr", 1920 / 3840)):
+            vw, vh = max(1, round(d.width * frac)), max(1, round(d.height * frac))
+            r.set_standard_view_size(vw, vh)
+            for i in range(2):
+                r.render(sid, did, poses[i % 200], "standard", out)
+            ms_l = timed_loop(lambda i: r.render(sid, did, poses[(7 * i) % 200], "standard", out),
+                              k_std, world, dev)
+            ms_l = reduce_max(ms_l, world, dev)
+            fps_l = reduce_sum(k_std, world, dev) / (ms_l / 1e3)
+            lowres[name] = {"view": [vw, vh], "frames_per_s": fps_l, "ms_per_frame": ms_l / k_std,
+                            "speedup_directl_over": fps / fps_l}
+        r.set_standard_view_size(0, 0)
+        std["lowres"] = lowres
     r.enable_stage_timing(False)
 
     # ---- end to end through the C ABI with a host (pinned) frame ----

@@ -232,7 +232,15 @@ dl_status dl_ray_table_static(int32_t width, int32_t height, const uint16_t* V,
  *   the global radix sort.  DL_SORT_BINNED: always binned; a frame with a
  *   longer list fails with DL_ERR_CAPACITY.  Both give the same image. */
 enum { DL_OPT_SORT_MODE = 1, DL_OPT_EVAL_DIRECTL = 2, DL_OPT_EVAL_STANDARD = 3,
-       DL_OPT_WARP_LIST_CAP = 4 };
+       DL_OPT_WARP_LIST_CAP = 4, DL_OPT_STANDARD_VIEW_SIZE = 5 };
+/* DL_OPT_STANDARD_VIEW_SIZE: resolution at which DL_STANDARD renders each
+ * view, value = (view_w << 16) | view_h, 0 = the panel's (HR).  Below panel
+ * resolution (the LR / MR configurations of the paper's experiments) every
+ * view is rendered at view_w x view_h with the same field of view, then
+ * upsampled while interweaving (Alg. 1, "Resize ... Upsample"): subpixel
+ * (x, y, k) takes channel k of its view V(x, 3y + k) bilinearly at
+ * (y view_w / w, x view_h / h) of that view, clamped at the border.
+ * 1 <= view_w, view_h <= 16384. */
 enum { DL_SORT_AUTO = 0, DL_SORT_RADIX = 1, DL_SORT_BINNED = 2 };
 /* DL_OPT_EVAL_DIRECTL / DL_OPT_EVAL_STANDARD: how a warp evaluates a tile's
  * Gaussians on the binned path.  DL_EVAL_DIRECT: every lane walks the

@@ -287,6 +287,47 @@ def render_subpixels(scene: Scene, display, L0: np.ndarray, subpixels: np.ndarra
             "n_contrib": res["n_contrib"][inv]}
 
 
+def bilinear_taps(n_out: int, n_in: int, pos: np.ndarray):
+    """Taps of the standard paradigm's upsampling (Alg. 1, "Resize"): output
+    index i of n_out samples the input of n_in at i * n_in / n_out (the pixel
+    grids share the corner: pixel (r, c) samples image point (c, r) about the
+    principal point in both).  Returns (i0, i1, frac): the two input indices,
+    clamped at the border, and the weight of i1."""
+    pos = np.asarray(pos, dtype=np.int64)
+    num = pos * n_in
+    i0 = num // n_out
+    frac = (num - i0 * n_out).astype(np.float64) / n_out
+    return np.minimum(i0, n_in - 1), np.minimum(i0 + 1, n_in - 1), frac
+
+
+def render_subpixels_lowres(scene: Scene, display, L0: np.ndarray, subpixels: np.ndarray,
+                            V: np.ndarray, view_w: int, view_h: int, n_threads: int = 0) -> dict:
+    """Standard paradigm with every view rendered at view_w x view_h (same
+    field of view, so f scales with the width) and upsampled bilinearly while
+    interweaving: subpixel (x, y, k) takes channel k of view V(x, 3y + k) at
+    column y view_w / w, row x view_h / h of that view."""
+    subpixels = np.asarray(subpixels, dtype=np.int64)
+    w = display.width
+    row = subpixels // (3 * w)
+    col = (subpixels % (3 * w)) // 3
+    k = subpixels % 3
+    v = V.reshape(-1)[subpixels].astype(np.int64)
+    x0, x1, fx = bilinear_taps(w, view_w, col)
+    y0, y1, fy = bilinear_taps(display.height, view_h, row)
+    taps = [(y0, x0, (1 - fy) * (1 - fx)), (y0, x1, (1 - fy) * fx),
+            (y1, x0, fy * (1 - fx)), (y1, x1, fy * fx)]
+    rays = np.concatenate([np.stack([v, yy, xx], axis=1) for yy, xx, _ in taps])
+    uniq, inv = np.unique(rays, axis=0, return_inverse=True)
+    inv = inv.reshape(4, -1)
+    small = display.replace(width=int(view_w), height=int(view_h))
+    res = render_rays(scene, small, L0, uniq, n_threads=n_threads)
+    out = {}
+    for key, name in (("value", "rgb"), ("lo", "lo"), ("hi", "hi")):
+        out[key] = sum(wt * res[name][inv[t], k] for t, (_, _, wt) in enumerate(taps))
+    out["n_rays"] = int(uniq.shape[0])
+    return out
+
+
 def render_frame(scene: Scene, display, L0: np.ndarray, mode: str = "directl",
                  n_threads: int = 0) -> dict:
     """Whole encoded image (h, w, 3) for ``mode`` in {"directl", "standard"}."""

@@ -270,8 +270,9 @@ dl_status upload_cams(dl_ctx* ctx, const std::vector<Cam>& cams, cudaStream_t s)
 
 // Pinhole camera of Sec. 6: f = (w/2) / tan(fov_x/2), principal point (w/2,
 // h/2); the Jacobian's clamp at 1.3 tan(fov/2) (3DGS practice).
-ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, int32_t th) {
-    const int32_t w = D.q.w, h = D.q.h;
+ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, int32_t th,
+                                  int32_t rw, int32_t rh) {
+    const int32_t w = rw > 0 ? rw : D.q.w, h = rh > 0 ? rh : D.q.h;
     const double pi = 3.14159265358979323846;
     const double focal = 0.5 * w / std::tan(0.5 * D.prm.fov_x_deg * pi / 180.0);
     ProjectParams pp{};
@@ -588,6 +589,15 @@ dl_status dl_set_option(dl_ctx* ctx, int32_t option, int64_t value) {
         ctx->warp_cap = int32_t(value);
         return DL_OK;
     }
+    if (option == DL_OPT_STANDARD_VIEW_SIZE) {
+        const int64_t vw = value >> 16, vh = value & 0xFFFF;
+        if (value != 0 && (vw < 1 || vw > 16384 || vh < 1 || vh > 16384))
+            return fail(ctx, DL_ERR_INVALID_ARG, "standard view size %lldx%lld", (long long)vw,
+                        (long long)vh);
+        ctx->std_view_w = int32_t(vw);
+        ctx->std_view_h = int32_t(vh);
+        return DL_OK;
+    }
     if (option == DL_OPT_EVAL_DIRECTL || option == DL_OPT_EVAL_STANDARD) {
         if (value != DL_EVAL_DIRECT && value != DL_EVAL_TRANSPOSED)
             return fail(ctx, DL_ERR_INVALID_ARG, "evaluation strategy %lld", (long long)value);
@@ -717,6 +727,11 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
 
     const int32_t nv = D.q.nv, w = D.q.w, h = D.q.h;
     const int32_t tw = ctx->tile[mode][0], th = ctx->tile[mode][1];
+    // the standard paradigm's views: panel resolution, or LR / MR upsampled
+    // while interweaving
+    const bool lowres = mode == DL_STANDARD && ctx->std_view_w > 0 &&
+                        (ctx->std_view_w != w || ctx->std_view_h != h);
+    const int32_t rw = lowres ? ctx->std_view_w : w, rh = lowres ? ctx->std_view_h : h;
     RaySet* R = nullptr;
     TileGroups* G = nullptr;
     if (mode != DL_STANDARD) {
@@ -738,11 +753,14 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
 
     // ---- cameras (Eq. (17)) and projection (Eqs. (8)-(10)) ----
     std::vector<Cam> cams;
-    if (!make_cams(D.prm, L0_c2w, cams))
+    dl_display_params view_prm = D.prm;  // the views' own resolution (focal, shifts)
+    view_prm.width = rw;
+    view_prm.height = rh;
+    if (!make_cams(view_prm, L0_c2w, cams))
         return fail(ctx, DL_ERR_INVALID_ARG, "off-axis rig: the world origin is not in front of L0");
     st = upload_cams(ctx, cams, s);
     if (st) return st;
-    const ProjectParams pp = make_project_params(S, D, tw, th);
+    const ProjectParams pp = make_project_params(S, D, tw, th, rw, rh);
     const int64_t ntiles = int64_t(pp.ntx) * pp.nty;
     const int64_t ne = int64_t(nv) * S.n;
     if (ne >= (int64_t(1) << 31)) return fail(ctx, DL_ERR_CAPACITY, "views x Gaussians >= 2^31");
@@ -814,8 +832,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
 
     CompositeParams cp{};
     cp.n = S.n;
-    cp.width = w;
-    cp.height = h;
+    cp.width = rw;
+    cp.height = rh;
     cp.half_w = pp.half_w;
     cp.half_h = pp.half_h;
     cp.tile_w = tw;
@@ -831,7 +849,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     float* Mm = nullptr;
     float* raycol = nullptr;
     if (mode == DL_STANDARD) {
-        DL_CK(W.Mm.reserve(12 * size_t(nv) * size_t(w) * size_t(h)), "alloc M_m");
+        DL_CK(W.Mm.reserve(12 * size_t(nv) * size_t(rw) * size_t(rh)), "alloc M_m");
         Mm = W.Mm.as<float>();
     } else {
         DL_CK(W.raycol.reserve(12 * size_t(R->n_rays > 0 ? R->n_rays : 1)), "alloc ray colours");
@@ -948,7 +966,10 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                     (mode == DL_STANDARD ? 1 : (G->n_work > 0 ? 1 : 0));
     }
     DL_CK(mark(7), "event");
-    if (mode == DL_STANDARD) {
+    if (lowres) {
+        DL_CK(launch_resize_interweave(w, h, rw, rh, D.V.as<uint16_t>(), Mm, dst, s),
+              "upsample and interweave");
+    } else if (mode == DL_STANDARD) {
         DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), Mm, dst, s), "interweave");
     } else {
         DL_CK(launch_reorder(R->ray_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst, nullptr, s),
@@ -962,7 +983,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     dl_frame_stats& fs = ctx->stats;
     fs = dl_frame_stats{};
     fs.n_keys = nk;
-    fs.n_rays = mode == DL_STANDARD ? int64_t(nv) * w * h : R->n_rays;
+    fs.n_rays = mode == DL_STANDARD ? int64_t(nv) * rw * rh : R->n_rays;
     fs.tile_w = tw;
     fs.tile_h = th;
     fs.sort_bits = sort_bits;

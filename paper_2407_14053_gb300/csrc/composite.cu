@@ -1260,6 +1260,35 @@ __global__ void interweave_kernel(int32_t w, int32_t h, const uint16_t* __restri
     }
 }
 
+// Alg. 1 with views rendered at rw x rh and upsampled while interweaving:
+// subpixel (x, y, k) takes channel k of view V(x, 3y + k) bilinearly at
+// column y rw / w, row x rh / h of that view (pixel (r, c) of a view samples
+// its image point (c, r) about the principal point, so the panel's and the
+// view's pixel grids share the corner), clamped at the border.  Positions
+// are split into integer and fractional parts exactly.
+__global__ void resize_interweave_kernel(int32_t w, int32_t h, int32_t rw, int32_t rh,
+                                         const uint16_t* __restrict__ V,
+                                         const float* __restrict__ Mm, float* __restrict__ out) {
+    const int64_t n = 3 * int64_t(w) * h;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t row = i / (3 * int64_t(w));
+        const int64_t s = i - row * 3 * int64_t(w);
+        const int64_t col = s / 3;
+        const int k = int(s - col * 3);
+        const int v = V[i];
+        const int64_t nx = col * rw, ny = row * rh;
+        const int x0 = int(nx / w), y0 = int(ny / h);
+        const float fx = float(nx - int64_t(x0) * w) / float(w);
+        const float fy = float(ny - int64_t(y0) * h) / float(h);
+        const int x1 = min(x0 + 1, rw - 1), y1 = min(y0 + 1, rh - 1);
+        const float* img = Mm + int64_t(v) * rh * rw * 3 + k;
+        const float a = img[(int64_t(y0) * rw + x0) * 3], b = img[(int64_t(y0) * rw + x1) * 3];
+        const float c = img[(int64_t(y1) * rw + x0) * 3], d = img[(int64_t(y1) * rw + x1) * 3];
+        out[i] = (1.f - fy) * ((1.f - fx) * a + fx * b) + fy * ((1.f - fx) * c + fx * d);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_composite_rays(const CompositeParams& p, const int4* work, int64_t n_work,
@@ -1415,6 +1444,17 @@ cudaError_t launch_reorder(const uint32_t* ray_of, const float* raycol, int64_t 
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
     reorder_kernel<<<unsigned(grid), 256, 0, s>>>(ray_of, raycol, n, out, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resize_interweave(int32_t w, int32_t h, int32_t rw, int32_t rh,
+                                     const uint16_t* V, const float* Mm, float* out,
+                                     cudaStream_t s) {
+    const int64_t n = 3 * int64_t(w) * h;
+    int64_t grid = (n + 255) / 256;
+    const int64_t cap = int64_t(num_sms()) * 32;
+    if (grid > cap) grid = cap;
+    resize_interweave_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(w, h, rw, rh, V, Mm, out);
     return cudaGetLastError();
 }
 

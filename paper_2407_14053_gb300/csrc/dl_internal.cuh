@@ -243,6 +243,11 @@ cudaError_t launch_partition(const int4* gwork, int64_t n_work, const uint32_t* 
                              uint32_t* meta, cudaStream_t s);
 
 // Alg. 1 sampling step at native resolution.
+// Alg. 1 with upsampling: views rendered at rw x rh (Mm: nv x rh x rw x 3),
+// each subpixel sampling its view bilinearly (see resize_interweave_kernel).
+cudaError_t launch_resize_interweave(int32_t w, int32_t h, int32_t rw, int32_t rh,
+                                     const uint16_t* V, const float* Mm, float* out,
+                                     cudaStream_t s);
 cudaError_t launch_interweave(int32_t w, int32_t h, int32_t nv, const uint16_t* V, const float* Mm,
                               float* out, cudaStream_t s);
 

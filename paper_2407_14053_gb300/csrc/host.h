@@ -124,6 +124,7 @@ struct dl_ctx {
     int32_t sort_mode = DL_SORT_AUTO;
     int32_t eval_transposed[3] = {1, 0, 1};  // per mode
     int32_t warp_cap = 512;
+    int32_t std_view_w = 0, std_view_h = 0;  // DL_OPT_STANDARD_VIEW_SIZE (0: panel)
     bool timing = false;
     dl_frame_stats stats{};
     int32_t n_batches = 0;  // live dl_batch objects on this context
@@ -142,8 +143,10 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
 // View cameras of Eq. (17) (or of the off-axis rig) for a light-field centre
 // pose; false when the off-axis rig's convergence depth is not positive.
 bool make_cams(const dl_display_params& p, const double L0[16], std::vector<Cam>& cams);
-// Projection parameters of a frame (tile shape tw x th).
-ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, int32_t th);
+// Projection parameters of a frame (tile shape tw x th), views rendered at
+// rw x rh (0: the panel's resolution).
+ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, int32_t th,
+                                  int32_t rw = 0, int32_t rh = 0);
 
 }  // namespace dl
 

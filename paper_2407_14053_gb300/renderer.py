@@ -149,6 +149,11 @@ class Renderer:
         B.dl_set_option(self.ctx, opt, {"direct": B.DL_EVAL_DIRECT,
                                         "transposed": B.DL_EVAL_TRANSPOSED}[strategy])
 
+    def set_standard_view_size(self, view_w: int = 0, view_h: int = 0) -> None:
+        """Resolution of the standard paradigm's views (0, 0: the panel's);
+        below panel resolution they are upsampled while interweaving."""
+        B.dl_set_option(self.ctx, B.DL_OPT_STANDARD_VIEW_SIZE, (int(view_w) << 16) | int(view_h))
+
     def set_warp_cap(self, cap: int) -> None:
         """Longest tile list (512 or 1024 keys; 0 = none) one warp composites."""
         B.dl_set_option(self.ctx, B.DL_OPT_WARP_LIST_CAP, int(cap))

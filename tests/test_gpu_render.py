@@ -340,3 +340,29 @@ def test_off_axis_rig_full_frame(renderer, mode):
         renderer.render(sid, did, behind, mode)
     renderer.free_display(did)
     renderer.free_scene(sid)
+
+
+@pytest.mark.parametrize("view", [(80, 45), (120, 68), (240, 135)])
+def test_standard_below_panel_resolution(renderer, view):
+    # the paper's LR / MR configurations: views rendered smaller, upsampled
+    # bilinearly while interweaving (Alg. 1); at panel size it is HR
+    wl = W.WORKLOADS["tiny"]
+    d = wl.display
+    scene = W.make_scene(wl.scene)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(wl.camera_distance, -2.0)
+    renderer.set_standard_view_size(*view)
+    try:
+        img = _frame(renderer, sid, did, L0, "standard").reshape(-1)
+    finally:
+        renderer.set_standard_view_size(0, 0)
+    V = oracle.view_map(d)
+    sub = np.arange(img.size)
+    ref = oracle.render_subpixels_lowres(oracle.Scene(scene), d, L0, sub, V, *view)
+    ok, maxerr, nbad = _accept(img, ref, TOL)
+    assert nbad == 0, f"{nbad} of {img.size} outside tolerance; max |err| {maxerr:.3g}"
+    if view == (d.width, d.height):
+        assert np.array_equal(img, _frame(renderer, sid, did, L0, "standard").reshape(-1))
+    renderer.free_display(did)
+    renderer.free_scene(sid)

@@ -298,3 +298,45 @@ def test_off_axis_rig_has_no_parallax_on_the_convergence_plane():
     assert np.all(np.diff(us[1]) < 0)                        # nearer: moves left as x_v grows
     assert np.all(np.diff(us[2]) > 0)                        # farther: moves right
     assert np.ptp(vs[1]) < 1e-9                              # a horizontal rig: rows do not move
+
+
+# ---- the standard paradigm below panel resolution (Alg. 1, Resize) --------
+def test_bilinear_taps_match_scipy_order_one_sampling():
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(5)
+    img = rng.normal(size=(9, 16))
+    w, h = 48, 27  # panel; the view is 16 x 9 (the 4K panel's LR aspect)
+    r, c = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    x0, x1, fx = oracle.bilinear_taps(w, 16, c.ravel())
+    y0, y1, fy = oracle.bilinear_taps(h, 9, r.ravel())
+    ours = ((1 - fy) * ((1 - fx) * img[y0, x0] + fx * img[y0, x1]) +
+            fy * ((1 - fx) * img[y1, x0] + fx * img[y1, x1]))
+    ref = ndimage.map_coordinates(img, [r.ravel() * 9 / h, c.ravel() * 16 / w], order=1,
+                                  mode="nearest")
+    assert np.allclose(ours, ref, atol=1e-12)
+    # the last columns and rows clamp at the border
+    assert x0.max() == 15 and x1.max() == 15 and y1.max() == 8
+
+
+def test_lowres_standard_at_panel_resolution_is_the_standard_frame():
+    d = W.Display(48, 27, 5, 5.3, 1 / 6, view_span_deg=10.0)
+    sc = oracle.Scene(W.make_scene(W.SceneSpec(150, 1, "uniform", "f32", seed=2)))
+    L0 = W.light_field_centre(4.0, 1.0)
+    V = oracle.view_map(d)
+    sub = np.arange(3 * d.width * d.height)
+    hr = oracle.render_subpixels(sc, d, L0, sub, V, None)
+    same = oracle.render_subpixels_lowres(sc, d, L0, sub, V, d.width, d.height)
+    assert np.array_equal(same["value"], hr["value"])
+    # views of a third of the panel: every subpixel is a convex mix of the
+    # four view pixels around its position, so it lies within their range
+    low = oracle.render_subpixels_lowres(sc, d, L0, sub, V, 16, 9)
+    small = d.replace(width=16, height=9)
+    vv, rr, cc = np.meshgrid(np.arange(5), np.arange(9), np.arange(16), indexing="ij")
+    views = oracle.render_rays(sc, small, L0, np.stack([vv.ravel(), rr.ravel(), cc.ravel()], 1))
+    img = views["rgb"].reshape(5, 9, 16, 3)
+    row, col, k = sub // (3 * d.width), (sub % (3 * d.width)) // 3, sub % 3
+    v = V.reshape(-1)[sub]
+    x0, x1, _ = oracle.bilinear_taps(d.width, 16, col)
+    y0, y1, _ = oracle.bilinear_taps(d.height, 9, row)
+    taps = np.stack([img[v, y0, x0, k], img[v, y0, x1, k], img[v, y1, x0, k], img[v, y1, x1, k]])
+    assert np.all(low["value"] >= taps.min(0) - 1e-12) and np.all(low["value"] <= taps.max(0) + 1e-12)
