@@ -90,9 +90,12 @@ def _load():
             lib.or_render_rays.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P, P, P, P,
                                            ctypes.c_int]
             lib.or_interweave.argtypes = [P, P, P, P]
+            lib.or_raycast_rays.argtypes = [P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int32, P,
+                                            P, P, P, ctypes.c_int]
             lib.or_max_threads.argtypes = []
             for f in ("or_quantise", "or_view_map", "or_area_map", "or_repurpose", "or_ray_table",
-                      "or_cameras", "or_render_rays", "or_interweave", "or_max_threads"):
+                      "or_cameras", "or_render_rays", "or_interweave", "or_max_threads",
+                      "or_raycast_rays"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -285,6 +288,40 @@ def render_subpixels(scene: Scene, display, L0: np.ndarray, subpixels: np.ndarra
     return {"value": res["rgb"][inv, k], "lo": res["lo"][inv, k], "hi": res["hi"][inv, k],
             "flags": res["flags"][inv], "n_rays": int(uniq.shape[0]),
             "n_contrib": res["n_contrib"][inv]}
+
+
+def raycast_rays(scene: Scene, display, L0: np.ndarray, rays: np.ndarray, heap_cap: int = 128,
+                 n_threads: int = 0) -> dict:
+    """Ray-order 3DGS (Sec. 7, Alg. 3) colours of rays (n,3) = (view, row,
+    col) with a heap of ``heap_cap`` intersections per ray; rgb, lo, hi (n,3)
+    and flags as in ``render_rays``."""
+    lib = _load()
+    rays = np.ascontiguousarray(rays, dtype=np.int32).reshape(-1, 3)
+    n = rays.shape[0]
+    rv, rr, rc = (np.ascontiguousarray(rays[:, j]) for j in range(3))
+    rgb, lo, hi = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    flags = np.zeros(n, dtype=np.int32)
+    L0 = np.ascontiguousarray(L0, dtype=np.float64)
+    d = _disp(display)
+    _check(lib.or_raycast_rays(ctypes.byref(scene.c), ctypes.byref(d), _ptr(L0), n, _ptr(rv),
+                               _ptr(rr), _ptr(rc), int(heap_cap), _ptr(rgb), _ptr(lo), _ptr(hi),
+                               _ptr(flags), int(n_threads)), "raycast_rays")
+    return {"rgb": rgb, "lo": lo, "hi": hi, "flags": flags}
+
+
+def raycast_subpixels(scene: Scene, display, L0: np.ndarray, subpixels: np.ndarray, V: np.ndarray,
+                      src: np.ndarray | None, heap_cap: int = 128) -> dict:
+    """Per-subpixel colour of the ray-order 3DGS frame (the rays of the
+    DirectL assignment when ``src`` is given, else every subpixel's own
+    pixel)."""
+    subpixels = np.asarray(subpixels, dtype=np.int64)
+    rays = subpixel_rays(display, subpixels, V, src)
+    uniq, inv = np.unique(rays, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    res = raycast_rays(scene, display, L0, uniq, heap_cap)
+    k = subpixels % 3
+    return {"value": res["rgb"][inv, k], "lo": res["lo"][inv, k], "hi": res["hi"][inv, k],
+            "flags": res["flags"][inv], "n_rays": int(uniq.shape[0])}
 
 
 def bilinear_taps(n_out: int, n_in: int, pos: np.ndarray):

@@ -666,6 +666,185 @@ int or_render_rays(const or_scene* sc, const or_display* p, const double L0[16],
 /* a9: interlacing, Alg. 1 (the sampling step, at native resolution).        */
 /* ------------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------------ */
+/* Ray-order 3DGS (Sec. 7, Alg. 3): per ray, every Gaussian it meets gives the */
+/* point of highest density along the ray, t_j = (mu - o)^T S^-1 d /        */
+/* (d^T S^-1 d) (Eq. (16)), and alpha_j = o_j G(o + t_j d) (Eq. (17)); a     */
+/* max-heap of capacity c_h keeps the c_h nearest; they are sorted by t and */
+/* alpha-blended, colour from the SH at the ray direction d.                */
+/* Readings: the ray meets a Gaussian when alpha_j >= 1/255 at t_j and t_j  */
+/* exceeds the 0.2 near plane; the heap keeps the c_h smallest (t, index);  */
+/* alpha is clamped to 0.99 and blending follows or_composite.              */
+/* ------------------------------------------------------------------------ */
+
+/* or_composite over the first `cap` included contributors. */
+static int64_t or_composite_cap(or_contrib* c, int64_t n, double t_stop, int64_t cap,
+                                double out[3]) {
+    int64_t kept = 0, cut = n;
+    for (int64_t i = 0; i < n; ++i)
+        if (c[i].include && ++kept == cap) { cut = i + 1; break; }
+    return or_composite(c, cut, t_stop, out, NULL);
+}
+
+int or_raycast_rays(const or_scene* sc, const or_display* p, const double L0[16], int64_t n_rays,
+                    const int32_t* ray_v, const int32_t* ray_r, const int32_t* ray_c,
+                    int32_t heap_cap, double* rgb, double* lo, double* hi, int32_t* flags,
+                    int n_threads) {
+    if (or_check_display(p) || heap_cap < 1) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    const int32_t nv = p->num_views;
+    for (int64_t i = 0; i < n_rays; ++i)
+        if (ray_v[i] < 0 || ray_v[i] >= nv) return -1;
+    const int64_t n = sc->n;
+    const int nc = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    double* cams = (double*)malloc(sizeof(double) * 17 * (size_t)nv);
+    double* sinv = (double*)malloc(sizeof(double) * 6 * (size_t)(n > 0 ? n : 1));
+    if (!cams || !sinv) { free(cams); free(sinv); return -2; }
+    double* shift = cams + 16 * (size_t)nv;
+    if (or_cameras(p, L0, cams, shift)) { free(cams); free(sinv); return -1; }
+    const double pi = 3.14159265358979323846;
+    const double focal = 0.5 * p->width / tan(0.5 * p->fov_x_deg * pi / 180.0);
+    /* Sigma^-1 = R diag(s^-2) R^T (Eq. (8) inverted), upper triangle */
+    for (int64_t g = 0; g < n; ++g) {
+        const double* q = sc->rot_wxyz + 4 * g;
+        double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        double qw = q[0] / qn, qx = q[1] / qn, qy = q[2] / qn, qz = q[3] / qn;
+        double R[3][3] = {
+            {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+        double is2[3];
+        for (int i = 0; i < 3; ++i) is2[i] = exp(-2.0 * sc->log_scale[3 * g + i]);
+        double* o = sinv + 6 * g;
+        const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        for (int e = 0; e < 6; ++e) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[ij[e][0]][k] * is2[k] * R[ij[e][1]][k];
+            o[e] = acc;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n_rays; ++i) {
+        const double* T = cams + 16 * (int64_t)ray_v[i];
+        const double dc[3] = {((double)ray_c[i] - 0.5 * p->width - shift[ray_v[i]]) / focal,
+                              ((double)ray_r[i] - 0.5 * p->height) / focal, 1.0};
+        double d[3], o[3], dn = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            d[a] = T[4 * a] * dc[0] + T[4 * a + 1] * dc[1] + T[4 * a + 2] * dc[2];
+            o[a] = T[4 * a + 3];
+            dn += d[a] * d[a];
+        }
+        dn = sqrt(dn);
+        for (int a = 0; a < 3; ++a) d[a] /= dn;
+        double Y[16];
+        or_sh_basis(d, Y);
+        int64_t cap = 64, m = 0;
+        or_contrib* L = (or_contrib*)malloc(sizeof(or_contrib) * (size_t)cap);
+        double* col = (double*)malloc(sizeof(double) * 3 * (size_t)cap);
+        for (int64_t g = 0; g < n; ++g) {
+            const double* S = sinv + 6 * g;
+            const double* mu = sc->mean + 3 * g;
+            const double Sd[3] = {S[0] * d[0] + S[1] * d[1] + S[2] * d[2],
+                                  S[1] * d[0] + S[3] * d[1] + S[4] * d[2],
+                                  S[2] * d[0] + S[4] * d[1] + S[5] * d[2]};
+            const double den = d[0] * Sd[0] + d[1] * Sd[1] + d[2] * Sd[2];
+            const double t = ((mu[0] - o[0]) * Sd[0] + (mu[1] - o[1]) * Sd[1] +
+                              (mu[2] - o[2]) * Sd[2]) / den;
+            if (!(t > 0.2)) continue;
+            const double x[3] = {o[0] + t * d[0] - mu[0], o[1] + t * d[1] - mu[1],
+                                 o[2] + t * d[2] - mu[2]};
+            const double qf = S[0] * x[0] * x[0] + S[3] * x[1] * x[1] + S[5] * x[2] * x[2] +
+                              2.0 * (S[1] * x[0] * x[1] + S[2] * x[0] * x[2] + S[4] * x[1] * x[2]);
+            if (qf > 120.0) continue; /* alpha < 1e-26 */
+            double a = 1.0 / (1.0 + exp(-sc->opacity_logit[g])) * exp(-0.5 * qf);
+            if (a > 0.99) a = 0.99;
+            if (a < OR_ALPHA_MIN - 1e-6) continue;
+            if (m == cap) {
+                cap *= 2;
+                L = (or_contrib*)realloc(L, sizeof(or_contrib) * (size_t)cap);
+                col = (double*)realloc(col, sizeof(double) * 3 * (size_t)cap);
+            }
+            for (int k = 0; k < 3; ++k) {
+                double acc = 0.0;
+                for (int j = 0; j < nc; ++j) acc += Y[j] * sc->sh[(g * nc + j) * 3 + k];
+                acc += 0.5;
+                col[3 * m + k] = acc > 0.0 ? acc : 0.0;
+            }
+            L[m].depth = t;
+            L[m].idx = g;
+            L[m].alpha = a;
+            L[m].include = a >= OR_ALPHA_MIN;
+            ++m;
+        }
+        for (int64_t j = 0; j < m; ++j) L[j].rgb = col + 3 * j;  /* arrays no longer move */
+        qsort(L, (size_t)m, sizeof(or_contrib), or_cmp_contrib);
+        double base[3], alt[3];
+        or_composite_cap(L, m, OR_T_STOP, heap_cap, base);
+        double* R3 = rgb + 3 * i;
+        double* lo3 = lo + 3 * i;
+        double* hi3 = hi + 3 * i;
+        for (int k = 0; k < 3; ++k) R3[k] = lo3[k] = hi3[k] = base[k];
+        int32_t f = 0;
+        /* alternatives: alpha within 1e-6 of 1/255, t near-ties (|dt| <=
+         * 2^-20 t, incl. the heap's last slot), T within 1e-8 of 1e-4 */
+        for (int64_t j = 0; j < m; ++j)
+            if (fabs(L[j].alpha - OR_ALPHA_MIN) < 1e-6) {
+                f |= 2;
+                L[j].include = !L[j].include;
+                or_composite_cap(L, m, OR_T_STOP, heap_cap, alt);
+                or_envelope(alt, lo3, hi3);
+                L[j].include = !L[j].include;
+            }
+        {
+            int64_t prev = -1;
+            for (int64_t j = 0; j < m; ++j) {
+                if (!L[j].include) continue;
+                if (prev >= 0 && fabs(L[j].depth - L[prev].depth) <= ldexp(fabs(L[prev].depth), -20)) {
+                    f |= 1;
+                    or_contrib tmp = L[j];
+                    L[j] = L[prev];
+                    L[prev] = tmp;
+                    or_composite_cap(L, m, OR_T_STOP, heap_cap, alt);
+                    or_envelope(alt, lo3, hi3);
+                    tmp = L[j];
+                    L[j] = L[prev];
+                    L[prev] = tmp;
+                }
+                prev = j;
+            }
+        }
+        {
+            double Tt = 1.0;
+            int64_t kept = 0;
+            for (int64_t j = 0; j < m && kept < heap_cap; ++j) {
+                if (!L[j].include) continue;
+                ++kept;
+                double Tn = Tt * (1.0 - L[j].alpha);
+                if (fabs(Tn - OR_T_STOP) < 1e-8) {
+                    f |= 4;
+                    or_composite_cap(L, m, OR_T_STOP + 2e-8, heap_cap, alt);
+                    or_envelope(alt, lo3, hi3);
+                    or_composite_cap(L, m, OR_T_STOP - 2e-8, heap_cap, alt);
+                    or_envelope(alt, lo3, hi3);
+                    break;
+                }
+                if (Tn < OR_T_STOP) break;
+                Tt = Tn;
+            }
+        }
+        if (flags) flags[i] = f;
+        free(L);
+        free(col);
+    }
+    free(cams);
+    free(sinv);
+    return 0;
+}
+
 int or_interweave(const or_display* p, const uint16_t* V, const double* Mm, double* Me) {
     if (or_check_display(p)) return -1;
     const int64_t w = p->width, h = p->height;

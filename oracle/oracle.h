@@ -14,6 +14,9 @@
  *                          (iteration order, search order, buffer capacity):
  *                          parity unpinned for the exact tie-breaking.
  *   or_ray_table           pinned by invariants (R-first order, uniqueness).
+ *   or_raycast_rays        pinned (closed-form t and alpha of isotropic
+ *                          Gaussians, t maximises the density along the ray,
+ *                          heap capacity, SH at the ray direction).
  *   or_cameras             pinned (arc radius, angles, look-at, leftmost v=0;
  *                          off-axis rig: parallel axes, straight baseline,
  *                          no parallax on the convergence plane).
@@ -105,6 +108,17 @@ void or_project_splat(const or_scene* sc, int64_t g, const double c2w[16],
 /* The same with the principal point at (w/2 + shift, h/2). */
 void or_project_splat_shift(const or_scene* sc, int64_t g, const double c2w[16], double focal,
                             double shift, int32_t width, int32_t height, or_splat* out);
+
+/* Ray-order 3DGS (Sec. 7, Alg. 3) colour of rays (view, row, col): per ray
+ * (origin at the view's camera, unit direction through the pixel), every
+ * Gaussian with alpha_j = o_j G(o + t_j d) >= 1/255 at its highest-density
+ * point t_j = (mu - o)^T S^-1 d / (d^T S^-1 d) > 0.2 enters a heap keeping
+ * the heap_cap nearest (t, index); those are blended in t order with the
+ * SH colour at d.  rgb/lo/hi as or_render_rays. */
+int or_raycast_rays(const or_scene* sc, const or_display* p, const double L0[16], int64_t n_rays,
+                    const int32_t* ray_v, const int32_t* ray_r, const int32_t* ray_c,
+                    int32_t heap_cap, double* rgb, double* lo, double* hi, int32_t* flags,
+                    int n_threads);
 
 /* Colour of rays (view, row, col) by front-to-back compositing over every
  * Gaussian.  rgb/lo/hi are n_rays*3; lo/hi bound the results of the
