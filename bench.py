@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the continuous-batching serving mix")
+    ap.add_argument("--no-raycast", action="store_true",
+                    help="skip the ray-order 3DGS timing")
     ap.add_argument("--no-graph", action="store_true",
                     help="skip the 8K/100-view captured-graph batch section")
     return ap.parse_args()
@@ -511,6 +513,19 @@ def main():
         std["lowres"] = lowres
     r.enable_stage_timing(False)
 
+    # ---- the paper's ray-order 3DGS (Alg. 3) on the same rays ----
+    raycast = None
+    if not args.no_raycast:
+        r.render(sid, did, poses[0], "raycast", out)  # builds the scene's tree
+        k_rc = 3
+        ms_rc = timed_loop(lambda i: r.render(sid, did, poses[(11 * i) % 200], "raycast", out), k_rc,
+                           world, dev)
+        ms_rc = reduce_max(ms_rc, world, dev)
+        fps_rc = reduce_sum(k_rc, world, dev) / (ms_rc / 1e3)
+        raycast = {"frames_per_s": fps_rc, "ms_per_frame": ms_rc / k_rc, "heap_capacity": 128,
+                   "steps": k_rc, "speedup_directl_over": fps / fps_rc,
+                   "note": "one thread per ray, implicit 8-wide tree over the Morton-ordered scene"}
+
     # ---- end to end through the C ABI with a host (pinned) frame ----
     e2e = None
     if not args.no_e2e:
@@ -588,6 +603,7 @@ def main():
             "stages_ms": dl_stages,
             "offline_tables_s": offline_s,
             "standard": std,
+            "raycast": raycast,
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": e2e,

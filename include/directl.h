@@ -57,8 +57,10 @@ enum { DL_F32 = 0, DL_BF16 = 1, DL_F16 = 2 };
 enum {
     DL_DIRECTL = 0,       /* repurposed rays only (Sec. 5 and Sec. 4)     */
     DL_STANDARD = 1,      /* all N_v views at panel resolution + Alg. 1   */
-    DL_REQUIRED_ONLY = 2  /* identity ray assignment: blend only the pixels
+    DL_REQUIRED_ONLY = 2, /* identity ray assignment: blend only the pixels
                              the panel shows (Table 3, "Required Only")   */
+    DL_RAYCAST = 3        /* the rays of DL_DIRECTL cast through the scene:
+                             ray-order 3DGS (Sec. 7, Alg. 3)              */
 };
 
 typedef struct dl_ctx dl_ctx;
@@ -232,7 +234,18 @@ dl_status dl_ray_table_static(int32_t width, int32_t height, const uint16_t* V,
  *   the global radix sort.  DL_SORT_BINNED: always binned; a frame with a
  *   longer list fails with DL_ERR_CAPACITY.  Both give the same image. */
 enum { DL_OPT_SORT_MODE = 1, DL_OPT_EVAL_DIRECTL = 2, DL_OPT_EVAL_STANDARD = 3,
-       DL_OPT_WARP_LIST_CAP = 4, DL_OPT_STANDARD_VIEW_SIZE = 5 };
+       DL_OPT_WARP_LIST_CAP = 4, DL_OPT_STANDARD_VIEW_SIZE = 5, DL_OPT_HEAP_CAPACITY = 6 };
+/* DL_OPT_HEAP_CAPACITY: c_h of DL_RAYCAST, the number of nearest
+ * intersections each ray keeps and blends (1..256, default 128).
+ *
+ * DL_RAYCAST: per ray (origin at its view's camera, unit direction d through
+ * its pixel), every Gaussian with alpha_j = o_j G(o + t_j d) >= 1/255 at its
+ * highest-density point t_j = (mu - o)^T S^-1 d / (d^T S^-1 d) > 0.2 (Eqs.
+ * (16)-(17)) enters a max-heap that keeps the c_h smallest (t, index); they
+ * are blended in t order (alpha clamped to 0.99, stop before T < 1e-4) with
+ * the SH colour at d.  An implicit 8-wide tree of the Gaussians' alpha >=
+ * 1/255 boxes over the scene's stored order is built on the first such frame
+ * of a scene and kept with it. */
 /* DL_OPT_STANDARD_VIEW_SIZE: resolution at which DL_STANDARD renders each
  * view, value = (view_w << 16) | view_h, 0 = the panel's (HR).  Below panel
  * resolution (the LR / MR configurations of the paper's experiments) every

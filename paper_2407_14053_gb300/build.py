@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdirectl.so")
-SOURCES = ["api.cu", "batch.cu", "display.cu", "project.cu", "sort.cu", "composite.cu", "scene.cu"]
+SOURCES = ["api.cu", "batch.cu", "display.cu", "project.cu", "sort.cu", "composite.cu", "scene.cu",
+           "raycast.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -310,6 +310,93 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
+// Per-Gaussian data and the implicit tree of the ray-order renderer.
+dl_status build_raycast(dl_ctx* ctx, Scene& S, cudaStream_t s) {
+    S.rc_level_n.assign(kMaxRayLevels + 8, 0);
+    int levels = 0;
+    const size_t n_nodes = raycast_bvh_nodes(S.n, S.rc_level_n.data(), &levels);
+    if (levels > kMaxRayLevels)
+        return fail(ctx, DL_ERR_CAPACITY, "ray-order tree of %d levels", levels);
+    S.rc_level_n.resize(size_t(levels));
+    S.rc_level_off.assign(size_t(levels), 0);
+    for (int lv = 1; lv < levels; ++lv)
+        S.rc_level_off[size_t(lv)] = S.rc_level_off[size_t(lv - 1)] + S.rc_level_n[size_t(lv - 1)];
+    DL_CK(S.rc_gauss.reserve(48 * size_t(S.n)), "alloc ray-order data");
+    DL_CK(S.rc_gbox.reserve(32 * size_t(S.n)), "alloc ray-order boxes");
+    DL_CK(S.rc_nodes.reserve(32 * n_nodes), "alloc ray-order tree");
+    DL_CK(S.rc_meta.reserve(16 * size_t(levels)), "alloc ray-order levels");
+    int64_t* meta = S.rc_meta.as<int64_t>();
+    DL_CK(cudaMemcpyAsync(meta, S.rc_level_off.data(), 8 * size_t(levels), cudaMemcpyHostToDevice, s),
+          "copy levels");
+    DL_CK(cudaMemcpyAsync(meta + levels, S.rc_level_n.data(), 8 * size_t(levels),
+                          cudaMemcpyHostToDevice, s),
+          "copy levels");
+    const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
+    DL_CK(launch_raycast_prepare(S.dtype, attrs, S.n, S.rc_gauss.as<float4>(), S.rc_gbox.as<float4>(),
+                                 S.rc_nodes.as<float4>(), S.rc_level_off.data(),
+                                 S.rc_level_n.data(), levels, s),
+          "ray-order preparation");
+    DL_CK(cudaStreamSynchronize(s), "sync");
+    S.rc_levels = levels;
+    S.rc_built = true;
+    return DL_OK;
+}
+
+// DL_RAYCAST frame: the DirectL rays cast through the scene (Alg. 3), then
+// the ray colours gathered into the encoded image.  E: stage events (when
+// stage timing is on), the unused stages recorded empty.
+dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[16], float* out,
+                         int32_t out_on_device, cudaStream_t s, StageEvents* E) {
+    Workspace& W = ctx->ws;
+    auto mark = [&](int i) -> cudaError_t { return E ? cudaEventRecord(E->e[i], s) : cudaSuccess; };
+    RaySet& R = D.rep;
+    const int32_t w = D.q.w, h = D.q.h;
+    std::vector<Cam> cams;
+    if (!make_cams(D.prm, L0_c2w, cams))
+        return fail(ctx, DL_ERR_INVALID_ARG, "off-axis rig: the world origin is not in front of L0");
+    dl_status st = upload_cams(ctx, cams, s);
+    if (st) return st;
+    if (!S.rc_built) {
+        st = build_raycast(ctx, S, s);
+        if (st) return st;
+    }
+    for (int i = 1; i <= 6; ++i) DL_CK(mark(i), "event");
+    DL_CK(W.raycol.reserve(12 * size_t(R.n_rays > 0 ? R.n_rays : 1)), "alloc ray colours");
+    const double pi = 3.14159265358979323846;
+    const double focal = 0.5 * w / std::tan(0.5 * D.prm.fov_x_deg * pi / 180.0);
+    const int64_t* meta = S.rc_meta.as<int64_t>();
+    DL_CK(launch_raycast(S.dtype, S.sh_degree, S.rc_gauss.as<float4>(), S.rc_nodes.as<float4>(), meta,
+                         meta + S.rc_levels, S.rc_levels, S.n, S.sh.p, R.ray_view.as<uint32_t>(),
+                         R.ray_pix.as<uint32_t>(), R.n_rays, W.cams.as<Cam>(), float(focal),
+                         0.5f * float(w), 0.5f * float(h), ctx->heap_cap, W.raycol.as<float>(), s),
+          "ray-order rendering");
+    DL_CK(mark(7), "event");
+    const size_t out_bytes = 12 * size_t(w) * size_t(h);
+    float* dst = out;
+    if (!out_on_device) {
+        DL_CK(W.out.reserve(out_bytes), "alloc out");
+        dst = W.out.as<float>();
+    }
+    DL_CK(launch_reorder(R.ray_of.as<uint32_t>(), W.raycol.as<float>(), 3 * int64_t(w) * h, dst,
+                         nullptr, s),
+          "reorder");
+    DL_CK(mark(8), "event");
+    if (!out_on_device)
+        DL_CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, s), "copy frame");
+    dl_frame_stats& fs = ctx->stats;
+    fs = dl_frame_stats{};
+    fs.n_rays = R.n_rays;
+    fs.n_launches = int32_t((D.q.nv + kCamBatch - 1) / kCamBatch) + 2;
+    if (E) {
+        PendingFrame& pf = W.pending.back();
+        pf.n_rays = fs.n_rays;
+        pf.launches = fs.n_launches;
+    }
+    W.last_bytes = W.footprint();
+    if (!out_on_device) DL_CK(cudaStreamSynchronize(s), "sync");
+    return DL_OK;
+}
+
 }  // namespace dl
 
 extern "C" {
@@ -589,6 +676,13 @@ dl_status dl_set_option(dl_ctx* ctx, int32_t option, int64_t value) {
         ctx->warp_cap = int32_t(value);
         return DL_OK;
     }
+    if (option == DL_OPT_HEAP_CAPACITY) {
+        if (value < 1 || value > kMaxHeap)
+            return fail(ctx, DL_ERR_INVALID_ARG, "heap capacity %lld out of [1, %d]",
+                        (long long)value, kMaxHeap);
+        ctx->heap_cap = int32_t(value);
+        return DL_OK;
+    }
     if (option == DL_OPT_STANDARD_VIEW_SIZE) {
         const int64_t vw = value >> 16, vh = value & 0xFFFF;
         if (value != 0 && (vw < 1 || vw > 16384 || vh < 1 || vh > 16384))
@@ -698,7 +792,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     dl_status st = check_ctx(ctx);
     if (st) return st;
     if (!L0_c2w || !out) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
-    if (mode < 0 || mode > 2) return fail(ctx, DL_ERR_INVALID_ARG, "mode %d", mode);
+    if (mode < 0 || mode > DL_RAYCAST) return fail(ctx, DL_ERR_INVALID_ARG, "mode %d", mode);
     auto si = ctx->scenes.find(scene_id);
     if (si == ctx->scenes.end()) return fail(ctx, DL_ERR_NOT_FOUND, "scene %d", scene_id);
     auto di = ctx->displays.find(display_id);
@@ -724,6 +818,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         return timing ? cudaEventRecord(E->e[i], s) : cudaSuccess;
     };
     DL_CK(mark(0), "event");
+    if (mode == DL_RAYCAST) return render_raycast(ctx, S, D, L0_c2w, out, out_on_device, s, E);
 
     const int32_t nv = D.q.nv, w = D.q.w, h = D.q.h;
     const int32_t tw = ctx->tile[mode][0], th = ctx->tile[mode][1];

@@ -127,6 +127,27 @@ cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* r
                              const uint32_t* count, const uint32_t* offset,
                              unsigned long long* keys, uint32_t* vals, cudaStream_t s);
 
+// ---- ray-order 3DGS (raycast.cu) ------------------------------------------
+constexpr int kMaxHeap = 256;       // largest heap capacity c_h
+constexpr int kMaxRayLevels = 10;   // tree levels for n <= 2^28 Gaussians
+constexpr int kRayStack = 7 * kMaxRayLevels + 8;
+// Levels of the implicit 8-wide tree over n Gaussians: level_n[k] nodes at
+// level k (k = 0 the leaves), *n_levels levels; returns the node count.
+size_t raycast_bvh_nodes(int64_t n, int64_t* level_n, int* n_levels);
+// Per-Gaussian data (gauss: 3 float4, gbox: 2 float4 per Gaussian) and the
+// tree's boxes (nodes: 2 float4 per node, level k at node level_off[k]);
+// level_off / level_n are host arrays here.
+cudaError_t launch_raycast_prepare(int dtype, const void* const* attrs, int64_t n, float4* gauss,
+                                   float4* gbox, float4* nodes, const int64_t* level_off,
+                                   const int64_t* level_n, int n_levels, cudaStream_t s);
+// One thread per ray (view ray_view, pixel ray_pix): ray colours into raycol
+// (3 floats per ray); level_off_dev / level_n_dev in device memory.
+cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const float4* nodes,
+                           const int64_t* level_off_dev, const int64_t* level_n_dev, int n_levels,
+                           int64_t n, const void* sh, const uint32_t* ray_view,
+                           const uint32_t* ray_pix, int64_t n_rays, const Cam* cams, float focal,
+                           float half_w, float half_h, int heap_cap, float* raycol, cudaStream_t s);
+
 // ---- scan / radix sort / ranges (sort.cu) ---------------------------------
 size_t scan_tmp_bytes(int64_t n);
 // out[i] = sum_{j<i} in[j]; *d_total (device) = sum of all.

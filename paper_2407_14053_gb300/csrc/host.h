@@ -49,6 +49,13 @@ struct Scene {
     int32_t sh_degree = 0, dtype = DL_F32;
     int32_t in_use = 0;  // batch slots holding this scene
     DevBuf mean, log_scale, rot, opacity, sh;
+    // ray-order renderer (built on the first DL_RAYCAST frame): per-Gaussian
+    // data, the implicit tree's boxes and its level table (device: offsets
+    // then counts, int64)
+    bool rc_built = false;
+    int32_t rc_levels = 0;
+    std::vector<int64_t> rc_level_n, rc_level_off;
+    DevBuf rc_gauss, rc_gbox, rc_nodes, rc_meta;
 };
 
 struct TileGroups {
@@ -125,6 +132,7 @@ struct dl_ctx {
     int32_t eval_transposed[3] = {1, 0, 1};  // per mode
     int32_t warp_cap = 512;
     int32_t std_view_w = 0, std_view_h = 0;  // DL_OPT_STANDARD_VIEW_SIZE (0: panel)
+    int32_t heap_cap = 128;                  // DL_OPT_HEAP_CAPACITY
     bool timing = false;
     dl_frame_stats stats{};
     int32_t n_batches = 0;  // live dl_batch objects on this context

@@ -9,7 +9,8 @@ import torch
 
 from . import _binding as B
 
-MODES = {"directl": B.DL_DIRECTL, "standard": B.DL_STANDARD, "required_only": B.DL_REQUIRED_ONLY}
+MODES = {"directl": B.DL_DIRECTL, "standard": B.DL_STANDARD, "required_only": B.DL_REQUIRED_ONLY,
+         "raycast": B.DL_RAYCAST}
 DTYPES = {"f32": (B.DL_F32, torch.float32), "bf16": (B.DL_BF16, torch.bfloat16),
           "f16": (B.DL_F16, torch.float16)}
 
@@ -153,6 +154,11 @@ class Renderer:
         """Resolution of the standard paradigm's views (0, 0: the panel's);
         below panel resolution they are upsampled while interweaving."""
         B.dl_set_option(self.ctx, B.DL_OPT_STANDARD_VIEW_SIZE, (int(view_w) << 16) | int(view_h))
+
+    def set_heap_capacity(self, cap: int) -> None:
+        """c_h of the ray-order renderer ('raycast' mode): nearest
+        intersections kept per ray (1..256)."""
+        B.dl_set_option(self.ctx, B.DL_OPT_HEAP_CAPACITY, int(cap))
 
     def set_warp_cap(self, cap: int) -> None:
         """Longest tile list (512 or 1024 keys; 0 = none) one warp composites."""

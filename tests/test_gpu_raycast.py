@@ -1,0 +1,64 @@
+"""Ray-order 3DGS (Sec. 7, Alg. 3) on the GPU against the FP64 oracle: the
+DirectL rays of a frame cast through the scene with a heap of c_h nearest
+intersections, full tiny frames, with a small heap (the heap overflows on
+most rays) and the default one; the BF16 case against the oracle on the
+stored values."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    from paper_2407_14053_gb300 import Renderer
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+CASES = [
+    ("uniform f32", W.SceneSpec(2000, 0, "uniform", "f32", seed=0), 128, 0),
+    ("uniform f32, c_h 4", W.SceneSpec(2000, 0, "uniform", "f32", seed=0), 4, 0),
+    ("clustered bf16 SH3", W.SceneSpec(3000, 3, "clustered", "bf16", seed=7), 128, 0),
+    ("clustered bf16 SH3, off-axis", W.SceneSpec(3000, 3, "clustered", "bf16", seed=7), 16, 1),
+]
+
+
+@pytest.mark.parametrize("name,spec,cap,rig", CASES, ids=[c[0] for c in CASES])
+def test_raycast_frame_matches_oracle(renderer, name, spec, cap, rig):
+    d = W.WORKLOADS["tiny"].display.replace(rig=rig)
+    scene = W.make_scene(spec)
+    sid = renderer.load_gaussians(scene, spec.dtype)
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 1.5)
+    renderer.set_heap_capacity(cap)
+    try:
+        img = renderer.render(sid, did, L0, "raycast")
+        torch.cuda.synchronize()
+        img = img.cpu().numpy().reshape(-1)
+    finally:
+        renderer.set_heap_capacity(128)
+    V = oracle.view_map(d)
+    src = oracle.repurpose(d, V)
+    stored = scene if spec.dtype == "f32" else W.quantise_storage(scene, spec.dtype)
+    ref = oracle.raycast_subpixels(oracle.Scene(stored), d, L0, np.arange(img.size), V, src, cap)
+    lo, hi = ref["lo"] - TOL, ref["hi"] + TOL
+    bad = ~((img >= lo) & (img <= hi))
+    err = np.abs(img - ref["value"])
+    assert bad.sum() == 0, f"{int(bad.sum())} of {img.size} outside {TOL}; max |err| {err.max():.3g}"
+    assert np.abs(img).max() > 0.05  # the frame is not empty
+    renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
+def test_heap_capacity_option(renderer):
+    from paper_2407_14053_gb300 import DirectLError
+    for bad in (0, 257):
+        with pytest.raises(DirectLError):
+            renderer.set_heap_capacity(bad)
