@@ -287,6 +287,8 @@ ProjectParams make_project_params(const Scene& S, const Display& D, int32_t tw, 
     pp.lim_y = float(1.3 * (0.5 * h / focal));
     pp.tile_w = tw;
     pp.tile_h = th;
+    pp.tile_sx = bits_for(tw);  // tw, th: powers of two
+    pp.tile_sy = bits_for(th);
     pp.ntx = (w + tw - 1) / tw;
     pp.nty = (h + th - 1) / th;
     return pp;

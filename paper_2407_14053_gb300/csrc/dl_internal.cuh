@@ -23,13 +23,26 @@ struct DisplayQ {
 };
 
 // One view's camera: world->camera rotation (row-major), translation, centre.
-struct Cam {
+// 16-byte aligned and padded to five float4, so a kernel reads it with five
+// vector loads.
+struct alignas(16) Cam {
     float r[9];
     float t[3];
     float c[3];
     float shift;    // principal point (w/2 + shift, h/2): off-axis views
     float shift_f;  // shift / focal
+    float pad[3];
 };
+static_assert(sizeof(Cam) == 80, "five float4");
+
+__device__ __forceinline__ Cam load_cam(const Cam* __restrict__ p) {
+    Cam c;
+    const float4* s = reinterpret_cast<const float4*>(p);
+    float4* d = reinterpret_cast<float4*>(&c);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) d[i] = __ldg(s + i);
+    return c;
+}
 
 // Cameras of a frame reach the device as a kernel parameter of a one-block
 // copy kernel (stream-ordered, nothing to keep alive on the host).
@@ -47,6 +60,7 @@ struct ProjectParams {
     float half_w, half_h;  // principal point (w/2, h/2)
     float lim_x, lim_y;    // 1.3 tan(fov/2) clamps of the EWA Jacobian
     int32_t tile_w, tile_h, ntx, nty;
+    int32_t tile_sx, tile_sy;  // log2 of tile_w, tile_h (powers of two)
 };
 
 // Per (view, Gaussian) record written by the projection, 3 x float4:

@@ -15,6 +15,14 @@
 namespace dl {
 namespace {
 
+// Reciprocal to about one ulp (the PTX approximate reciprocal); its operands
+// here are positive and well inside the normal range.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -62,7 +70,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
             for (int c = 0; c < 3; ++c) sh[i][c] = to_f(G.sh[(g * NC + i) * 3 + c]);
 
         for (int32_t v = 0; v < nv; ++v) {
-            const Cam& cam = cams[v];
+            const Cam cam = load_cam(cams + v);
             const int64_t e = int64_t(v) * p.n + g;
             const float tx = cam.r[0] * mx + cam.r[1] * my + cam.r[2] * mz + cam.t[0];
             const float ty = cam.r[3] * mx + cam.r[4] * my + cam.r[5] * mz + cam.t[1];
@@ -70,7 +78,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
             uint32_t cnt = 0;
             if (tz > 0.2f && visible_alpha) {
                 // EWA (Eq. (9)): T = J W, Sigma' = T Sigma T^T + 0.3 I
-                const float iz = 1.f / tz;
+                const float iz = rcp_approx(tz);  // tz > 0.2
                 // the clamp window follows a shifted principal point (off-axis views)
                 const float sz = cam.shift_f;
                 const float xz = fminf(fmaxf(tx * iz, -p.lim_x - sz), p.lim_x - sz);
@@ -97,16 +105,17 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
                     const float uc = p.focal * tx * iz + cam.shift, vc = p.focal * ty * iz;
                     // pixels where alpha >= 1/255 lie in the ellipse
                     // d^T Sigma'^-1 d <= 2 ln(255 o); its bounding box:
-                    const float rx = sqrtf(K * cxx) * 1.0001f + 1e-3f;
-                    const float ry = sqrtf(K * cyy) * 1.0001f + 1e-3f;
+                    const float kx = K * cxx, ky = K * cyy;  // > 0
+                    const float rx = kx * rsqrtf(kx) * 1.0001f + 1e-3f;
+                    const float ry = ky * rsqrtf(ky) * 1.0001f + 1e-3f;
                     const float c_lo = ceilf(uc + p.half_w - rx), c_hi = floorf(uc + p.half_w + rx);
                     const float r_lo = ceilf(vc + p.half_h - ry), r_hi = floorf(vc + p.half_h + ry);
                     if (c_hi >= 0.f && r_hi >= 0.f && c_lo <= float(p.width - 1) &&
                         r_lo <= float(p.height - 1) && c_lo <= c_hi && r_lo <= r_hi) {
                         const int ic0 = int(fmaxf(c_lo, 0.f)), ic1 = int(fminf(c_hi, float(p.width - 1)));
                         const int ir0 = int(fmaxf(r_lo, 0.f)), ir1 = int(fminf(r_hi, float(p.height - 1)));
-                        const int tx0 = ic0 / p.tile_w, tx1 = ic1 / p.tile_w;
-                        const int ty0 = ir0 / p.tile_h, ty1 = ir1 / p.tile_h;
+                        const int tx0 = ic0 >> p.tile_sx, tx1 = ic1 >> p.tile_sx;
+                        const int ty0 = ir0 >> p.tile_sy, ty1 = ir1 >> p.tile_sy;
                         cnt = uint32_t(tx1 - tx0 + 1) * uint32_t(ty1 - ty0 + 1);
                         const uint32_t rect_c = uint32_t(ic0) | (uint32_t(ic1) << 16);
                         const uint32_t rect_r = uint32_t(ir0) | (uint32_t(ir1) << 16);
@@ -128,7 +137,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
                                         atomicAdd(out.gcount + vb + uint32_t(ty * p.ntx + tx), 1u);
                             }
                         }
-                        const float id = 1.f / det;
+                        const float id = rcp_approx(det);  // det >= 0.09
                         // colour: SH at dir = normalise(mu - camera centre)
                         float dx = mx - cam.c[0], dy = my - cam.c[1], dz = mz - cam.c[2];
                         const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -177,8 +186,8 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
         if (!cnt) continue;
         const float4 q2 = rec[3 * e + 2];
         const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
-        const int tx0 = int(rx & 0xFFFF) / p.tile_w, tx1 = int(rx >> 16) / p.tile_w;
-        const int ty0 = int(ry & 0xFFFF) / p.tile_h, ty1 = int(ry >> 16) / p.tile_h;
+        const int tx0 = int(rx & 0xFFFF) >> p.tile_sx, tx1 = int(rx >> 16) >> p.tile_sx;
+        const int ty0 = int(ry & 0xFFFF) >> p.tile_sy, ty1 = int(ry >> 16) >> p.tile_sy;
         uint32_t dk = __float_as_uint(q2.y) - zbits0;
         if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
         const int64_t v = e / p.n;
@@ -201,6 +210,8 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
 // depth << 32 | index << 4.  The low nibble stays free for the quadrant bits
 // that the block class sets after sorting; the index is unique in a group, so
 // they never decide the order.
+constexpr int kEmitRounds = 4;
+
 __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
                                    const uint32_t* __restrict__ count,
                                    const uint32_t* __restrict__ gstart, uint32_t* __restrict__ gfill,
@@ -214,6 +225,7 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
     const int64_t total = int64_t(nv) * p.n;
     const int ntiles = p.ntx * p.nty;
     const uint32_t zbits0 = __float_as_uint(0.2f);
+    const float rn = 1.0f / float(p.n);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -229,14 +241,18 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
         if (cnt) {
             const float4 q2 = rec[3 * e + 2];
             const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
-            tx0 = int(rx & 0xFFFF) / p.tile_w;
-            span = int(rx >> 16) / p.tile_w - tx0 + 1;
-            ty0 = int(ry & 0xFFFF) / p.tile_h;
+            tx0 = int(rx & 0xFFFF) >> p.tile_sx;
+            span = (int(rx >> 16) >> p.tile_sx) - tx0 + 1;
+            ty0 = int(ry & 0xFFFF) >> p.tile_sy;
             uint32_t dk = __float_as_uint(q2.y) - zbits0;
             if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
-            const int64_t v = e / p.n;
+            // view and Gaussian of record e: a float quotient, corrected
+            int64_t v = int64_t(float(e) * rn);
+            int64_t gi = e - v * p.n;
+            while (gi < 0) { --v; gi += p.n; }
+            while (gi >= p.n) { ++v; gi -= p.n; }
             khi = dk;
-            klo = uint32_t(e - v * p.n) << 4;
+            klo = uint32_t(gi) << 4;
             vb = uint32_t(v) * uint32_t(ntiles);
         }
         uint32_t incl = cnt;  // inclusive scan of the pair counts
@@ -247,8 +263,8 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
         }
         const uint32_t off = incl - cnt, n_pairs = __shfl_sync(0xffffffffu, incl, 31);
         const float rspan = 1.0f / float(span);
-        for (uint32_t r0 = 0; r0 < n_pairs; r0 += 32) {
-            const uint32_t pr = r0 + uint32_t(lane);
+        // pair pr -> its group and key (false past the last pair)
+        auto pair_of = [&](uint32_t pr, uint32_t& grp, unsigned long long& key) {
             // owner: the last lane whose first pair is <= pr
             int src = 0;
 #pragma unroll
@@ -264,19 +280,42 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
             const uint32_t s_vb = __shfl_sync(0xffffffffu, vb, src);
             const uint32_t s_hi = __shfl_sync(0xffffffffu, khi, src);
             const uint32_t s_lo = __shfl_sync(0xffffffffu, klo, src);
-            if (pr < n_pairs) {
-                // k = dy * span + dx; the +0.5 keeps the float quotient's floor exact
-                const int dy = int((float(k) + 0.5f) * s_r);
-                const int dx = int(k) - dy * s_span;
-                const uint32_t grp = s_vb + uint32_t((s_ty0 + dy) * p.ntx + s_tx0 + dx);
-                const unsigned am = __activemask();
-                const unsigned peers = __match_any_sync(am, grp);
-                const int leader = __ffs(peers) - 1;
-                uint32_t base = 0;
-                if (lane == leader) base = atomicAdd(gfill + grp, uint32_t(__popc(peers)));
-                base = __shfl_sync(peers, base, leader);
-                keys[gstart[grp] + base + __popc(peers & lt)] =
-                    ((unsigned long long)s_hi << 32) | s_lo;
+            // k = dy * span + dx; the +0.5 keeps the float quotient's floor exact
+            const int dy = int((float(k) + 0.5f) * s_r);
+            const int dx = int(k) - dy * s_span;
+            grp = s_vb + uint32_t((s_ty0 + dy) * p.ntx + s_tx0 + dx);
+            key = ((unsigned long long)s_hi << 32) | s_lo;
+            return pr < n_pairs;
+        };
+        // kEmitRounds rounds of 32 pairs at once: their cursor atomics are in
+        // flight together (the kernel waits on the atomics' round trips)
+        for (uint32_t r0 = 0; r0 < n_pairs; r0 += 32 * kEmitRounds) {
+            uint32_t grp[kEmitRounds], start[kEmitRounds], base[kEmitRounds];
+            unsigned long long key[kEmitRounds];
+            unsigned peers[kEmitRounds];
+            bool ok[kEmitRounds];
+#pragma unroll
+            for (int u = 0; u < kEmitRounds; ++u) {
+                ok[u] = false;
+                peers[u] = 0u;
+                if (r0 + 32u * u < n_pairs) {  // warp-uniform
+                    ok[u] = pair_of(r0 + 32u * u + uint32_t(lane), grp[u], key[u]);
+                    peers[u] = __match_any_sync(0xffffffffu, ok[u] ? grp[u] : 0xFFFFFFFFu);
+                    start[u] = ok[u] ? gstart[grp[u]] : 0u;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kEmitRounds; ++u) {
+                base[u] = 0u;
+                if (ok[u] && lane == __ffs(peers[u]) - 1)
+                    base[u] = atomicAdd(gfill + grp[u], uint32_t(__popc(peers[u])));
+            }
+#pragma unroll
+            for (int u = 0; u < kEmitRounds; ++u) {
+                if (r0 + 32u * u < n_pairs) {
+                    const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
+                    if (ok[u]) keys[start[u] + b + __popc(peers[u] & lt)] = key[u];
+                }
             }
         }
     }
