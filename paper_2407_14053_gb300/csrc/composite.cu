@@ -666,10 +666,11 @@ composite_full_binned_kernel(CompositeParams p, const int32_t* __restrict__ list
 constexpr int kWarpsPerBlock = 4;
 
 // Positions of the warp's rays about their box centre (x, y), written per
-// ray chunk, and the per-ray candidate masks of one batch.
+// ray chunk, and the per-ray candidate masks of one batch.  Coordinates are
+// stored apart, so four rays' x (or y) are one 16-byte read.
 struct RayTable {
-    float2 xy[32];
-    unsigned mask[32];
+    float4 x[8], y[8];
+    uint4 mask[8];
 };
 
 template <int CAP>
@@ -818,9 +819,10 @@ constexpr float kTestMargin = 0.05f;
 // B, C, L) when `hit` (its pixel box meets the rays' box).  The lane expands
 // the quadratic about the box centre (ox, oy) into
 // l2(x, y) = x (A x + B y + D) + y (C y + E) + F and tests it against every
-// ray (5 FMAs per pair, ray positions from the table), four rays per step;
-// ray r's mask of candidate records goes to T.mask[r].  Then every lane
-// blends its candidates in list order.
+// ray (5 FMAs per pair, ray positions from the table), four rays per step
+// with the FMAs paired over two rays (packed FP32x2 FMA: per component the
+// same rounding as fmaf); ray r's mask of candidate records goes to
+// T.mask[r].  Then every lane blends its candidates in list order.
 __device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const float4* c2, int n,
                                        bool hit, float u, float v, float A, float B, float C,
                                        float L, Acc& a, bool& done, uint32_t& evals, float px,
@@ -832,20 +834,26 @@ __device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const
     const float D = -fmaf(2.f * A, du, B * dv);
     const float E = -fmaf(2.f * C, dv, B * du);
     const float F = hit ? fmaf(du, fmaf(A, du, B * dv), fmaf(C * dv, dv, L)) + kTestMargin : -1e30f;
+    const float2 A2 = make_float2(A, A), B2 = make_float2(B, B), C2 = make_float2(C, C);
+    const float2 D2 = make_float2(D, D), E2 = make_float2(E, E), F2 = make_float2(F, F);
 #pragma unroll
-    for (int g = 0; g < 32; g += 4) {
-        if (!((act >> g) & 0xFu)) continue;
+    for (int g = 0; g < 8; ++g) {
+        if (!((act >> (4 * g)) & 0xFu)) continue;
+        const float4 qx = T.x[g], qy = T.y[g];
+        unsigned m[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 q = T.xy[g + k];
-            const float t1 = fmaf(A, q.x, fmaf(B, q.y, D));
-            const float l2 = fmaf(q.x, t1, fmaf(q.y, fmaf(C, q.y, E), F));
-            const unsigned m = __ballot_sync(0xffffffffu, l2 >= kLog2MinAlpha);
-            if (lane == 0) T.mask[g + k] = m;
+        for (int h = 0; h < 2; ++h) {
+            const float2 x = h ? make_float2(qx.z, qx.w) : make_float2(qx.x, qx.y);
+            const float2 y = h ? make_float2(qy.z, qy.w) : make_float2(qy.x, qy.y);
+            const float2 t1 = __ffma2_rn(A2, x, __ffma2_rn(B2, y, D2));
+            const float2 l2 = __ffma2_rn(x, t1, __ffma2_rn(y, __ffma2_rn(C2, y, E2), F2));
+            m[2 * h] = __ballot_sync(0xffffffffu, l2.x >= kLog2MinAlpha);
+            m[2 * h + 1] = __ballot_sync(0xffffffffu, l2.y >= kLog2MinAlpha);
         }
+        if (lane == 0) T.mask[g] = make_uint4(m[0], m[1], m[2], m[3]);
     }
     __syncwarp();
-    unsigned mine = (act >> lane) & 1u ? T.mask[lane] : 0u;
+    unsigned mine = (act >> lane) & 1u ? reinterpret_cast<const unsigned*>(T.mask)[lane] : 0u;
     if (!done) evals += uint32_t(n);
     while (mine && !done) {  // candidates passed the (widened) test: alpha decides
         const int sidx = __ffs(mine) - 1;
@@ -862,7 +870,8 @@ __device__ __forceinline__ void ray_table(RayTable& T, bool active, float px, fl
     const int lane = threadIdx.x & 31;
     ox = 0.5f * float(bx0 + bx1) - half_w;
     oy = 0.5f * float(by0 + by1) - half_h;
-    T.xy[lane] = active ? make_float2(px - ox, py - oy) : make_float2(1e18f, 1e18f);
+    reinterpret_cast<float*>(T.x)[lane] = active ? px - ox : 1e18f;
+    reinterpret_cast<float*>(T.y)[lane] = active ? py - oy : 1e18f;
     __syncwarp();
 }
 

@@ -232,14 +232,29 @@ __global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __
     // each warp takes 32 consecutive records and expands their (record,
     // tile) pairs into dense rounds of 32, so every lane emits a key per
     // round and each round costs one cursor atomic per group it touches
-    for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < total;
-         w += warps) {
+    // the next iteration's count and record tail are loaded one iteration
+    // ahead (the tail unconditionally: culled records are few)
+    int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    uint32_t cnt_next = 0u;
+    float4 q2_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto fetch = [&](int64_t ww) {
+        const int64_t en = ww * 32 + lane;
+        if (en < total) {
+            cnt_next = __ldg(count + en);
+            q2_next = __ldg(rec + 3 * en + 2);
+        } else {
+            cnt_next = 0u;
+        }
+    };
+    fetch(w);
+    for (; w * 32 < total; w += warps) {
         const int64_t e = w * 32 + lane;
-        uint32_t cnt = e < total ? count[e] : 0u;
+        const uint32_t cnt = cnt_next;
+        const float4 q2 = q2_next;
+        fetch(w + warps);
         int tx0 = 0, ty0 = 0, span = 1;
         uint32_t vb = 0, khi = 0, klo = 0;
         if (cnt) {
-            const float4 q2 = rec[3 * e + 2];
             const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
             tx0 = int(rx & 0xFFFF) >> p.tile_sx;
             span = (int(rx >> 16) >> p.tile_sx) - tx0 + 1;
