@@ -464,7 +464,7 @@ def main():
     # ---- DirectL frames ----
     for i in range(args.warmup):
         r.render(sid, did, poses[i % 200], "directl", out)
-    r.enable_stage_timing(True)
+    r.enable_stage_timing(True, count_pairs=False)  # stage events only
     torch.cuda.synchronize()
     r.stage_totals()
     sampler = ClockSampler(gpu_id_for(local)).start() if rank == 0 else None
@@ -474,6 +474,14 @@ def main():
     tot, nf = r.stage_totals()
     dl_stages = per_frame(tot, nf)
     launches = int(tot["n_launches"])
+    # pair counts of the same poses (counting kernels, untimed)
+    r.enable_stage_timing(True, count_pairs=True)
+    for i in range(args.steps):
+        r.render(sid, did, poses[i % 200], "directl", out)
+    tot_c, nf_c = r.stage_totals()
+    cnt = per_frame(tot_c, nf_c)
+    dl_stages["pairs_evaluated"], dl_stages["pairs_blended"] = cnt["pairs_evaluated"], cnt["pairs_blended"]
+    r.enable_stage_timing(True, count_pairs=False)
     ms_max = reduce_max(ms, world, dev)
     frames_total = reduce_sum(args.steps, world, dev)
     fps = frames_total / (ms_max / 1e3)

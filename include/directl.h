@@ -287,8 +287,10 @@ typedef struct {
 } dl_frame_stats;
 
 /* While enabled, every dl_render_frame records CUDA events around its
- * stages on its stream and counts compositing pairs, without synchronising.
- * Disabled by default. */
+ * stages on its stream, without synchronising.  enable = 1 also counts the
+ * compositing pairs (pairs_evaluated / pairs_blended; the compositing kernels
+ * then run their counting variant), enable = 2 records the events only,
+ * enable = 0 turns both off (the default). */
 dl_status dl_enable_stage_timing(dl_ctx* ctx, int32_t enable);
 /* Counters of the last frame (stage times are 0: see dl_stage_totals). */
 dl_status dl_last_frame_stats(dl_ctx* ctx, dl_frame_stats* out);

@@ -237,8 +237,9 @@ def dl_set_option(ctx, option: int, value: int) -> None:
     _check("dl_set_option", ctx, lib().dl_set_option(ctx, int(option), int(value)))
 
 
-def dl_enable_stage_timing(ctx, enable: bool) -> None:
-    _check("dl_enable_stage_timing", ctx, lib().dl_enable_stage_timing(ctx, int(bool(enable))))
+def dl_enable_stage_timing(ctx, enable) -> None:
+    """enable: 0 / False off, 1 / True events and pair counters, 2 events only."""
+    _check("dl_enable_stage_timing", ctx, lib().dl_enable_stage_timing(ctx, int(enable)))
 
 
 def dl_stage_totals(ctx):

@@ -711,11 +711,13 @@ dl_status dl_set_option(dl_ctx* ctx, int32_t option, int64_t value) {
 dl_status dl_enable_stage_timing(dl_ctx* ctx, int32_t enable) {
     dl_status st = check_ctx(ctx);
     if (st) return st;
-    if (enable && !ctx->ws.pairs.p) {
+    if (enable < 0 || enable > 2) return fail(ctx, DL_ERR_INVALID_ARG, "stage timing mode %d", enable);
+    if (enable == 1 && !ctx->ws.pairs.p) {
         DL_CK(ctx->ws.pairs.reserve(16), "alloc counters");
         DL_CK(cudaMemset(ctx->ws.pairs.p, 0, 16), "memset");
     }
     ctx->timing = enable != 0;
+    ctx->count_pairs = enable == 1;
     return DL_OK;
 }
 
@@ -925,7 +927,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     if (ctx->sort_mode == DL_SORT_BINNED && !binned)
         return fail(ctx, DL_ERR_CAPACITY, "a tile list holds %lld keys (binned limit %d)",
                     (long long)max_len, kLargeCap);
-    unsigned long long* pairs = timing ? W.pairs.as<unsigned long long>() : nullptr;
+    unsigned long long* pairs =
+        timing && ctx->count_pairs ? W.pairs.as<unsigned long long>() : nullptr;
 
     CompositeParams cp{};
     cp.n = S.n;

@@ -62,22 +62,23 @@ __device__ __forceinline__ float log2_alpha(float px, float py, float u, float v
 // One record against one ray.  Returns false once the ray is finished.
 // alpha = min(0.99, 2^log2_alpha); skip alpha < 1/255 (CHECK_L2: tested
 // first on log2 alpha, which spares the ex2 for records that miss the ray,
-// then on alpha itself); stop before T would drop below 1e-4.
-template <bool CHECK_L2 = true>
+// then on alpha itself); stop before T (1 - alpha) = T - alpha T would drop
+// below 1e-4.  COUNT keeps the composited-pair statistic.
+template <bool CHECK_L2 = true, bool COUNT = true>
 __device__ __forceinline__ bool blend(Acc& a, float px, float py, const float4& q0,
                                       const float4& q1, float b) {
     const float l2 = log2_alpha(px, py, q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
     if (CHECK_L2 && l2 < kLog2MinAlpha) return true;
     const float alpha = fminf(0.99f, ex2_approx(l2));
     if (alpha < (1.0f / 255.0f)) return true;
-    const float Tn = a.T * (1.f - alpha);
-    if (Tn < 1e-4f) return false;
     const float w = alpha * a.T;
+    const float Tn = a.T - w;
+    if (Tn < 1e-4f) return false;
     a.c0 = fmaf(w, q1.z, a.c0);
     a.c1 = fmaf(w, q1.w, a.c1);
     a.c2 = fmaf(w, b, a.c2);
     a.T = Tn;
-    ++a.blended;
+    if (COUNT) ++a.blended;
     return true;
 }
 
@@ -823,6 +824,7 @@ constexpr float kTestMargin = 0.05f;
 // with the FMAs paired over two rays (packed FP32x2 FMA: per component the
 // same rounding as fmaf); ray r's mask of candidate records goes to
 // T.mask[r].  Then every lane blends its candidates in list order.
+template <bool COUNT>
 __device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const float4* c2, int n,
                                        bool hit, float u, float v, float A, float B, float C,
                                        float L, Acc& a, bool& done, uint32_t& evals, float px,
@@ -854,11 +856,11 @@ __device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const
     }
     __syncwarp();
     unsigned mine = (act >> lane) & 1u ? reinterpret_cast<const unsigned*>(T.mask)[lane] : 0u;
-    if (!done) evals += uint32_t(n);
+    if (COUNT && !done) evals += uint32_t(n);
     while (mine && !done) {  // candidates passed the (widened) test: alpha decides
         const int sidx = __ffs(mine) - 1;
         mine &= mine - 1;
-        if (!blend<false>(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
+        if (!blend<false, COUNT>(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
     }
     __syncwarp();
 }
@@ -897,7 +899,7 @@ __device__ __forceinline__ bool batch_conic(const float4* c0, const float4* c1, 
 
 // Streams the warp's sorted list in batches of 32 records (cp.async double
 // buffering) and composites them, transposed, for the warp's rays.
-template <int CAP>
+template <int CAP, bool COUNT>
 __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t vbase,
                                             const float4* __restrict__ rec, Acc& a, bool& done,
                                             uint32_t& evals, float px, float py, int bx0, int bx1,
@@ -927,7 +929,7 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
         const int n = len - b * 32 < 32 ? len - b * 32 : 32;
         float u, v, A, B, C, L;
         const bool hit = batch_conic(c0, c1, c2, n, bx0, bx1, by0, by1, u, v, A, B, C, L);
-        eval32(c0, c1, c2, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.rays, ox, oy);
+        eval32<COUNT>(c0, c1, c2, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.rays, ox, oy);
         if (__all_sync(0xffffffffu, done)) break;
     }
     cp_async_wait<0>();
@@ -997,7 +999,7 @@ __device__ void quadrant_stream(const unsigned long long* sk, int len, int q, in
         const float4* c2 = Q.buf[slot][2];
         float u, v, A, B, C, L;
         const bool hit = batch_conic(c0, c1, c2, n_cur, bx0, bx1, by0, by1, u, v, A, B, C, L);
-        eval32(c0, c1, c2, n_cur, hit, u, v, A, B, C, L, a, done, evals, px, py, Q.rays, ox, oy);
+        eval32<true>(c0, c1, c2, n_cur, hit, u, v, A, B, C, L, a, done, evals, px, py, Q.rays, ox, oy);
         slot ^= 1;
         n_cur = __all_sync(0xffffffffu, done) ? 0 : n_next;
     }
@@ -1036,7 +1038,7 @@ __device__ __forceinline__ int4 batch_item(const FrameDesc* __restrict__ F,
 // cost); an item is {group, first key, first ray, rays << 16 | keys} of
 // frame f.  While one group is composited, the next item is loaded and its
 // keys and rays are prefetched into L2.
-template <int CAP>
+template <int CAP, bool COUNT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 6)  // 6 blocks (24 warps) a SM
 composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __restrict__ prefix,
                            int n_frames, int cls, uint32_t* __restrict__ cursor,
@@ -1086,7 +1088,8 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
             ray_table(W.rays, active, px, py, ox, oy, bx0, bx1, by0, by1, half_w, half_h);
             Acc a{1.f, 0.f, 0.f, 0.f, 0u};
             bool done = !active;
-            warp_stream(W, len, vbase, rec, a, done, evals, px, py, bx0, bx1, by0, by1, ox, oy);
+            warp_stream<CAP, COUNT>(W, len, vbase, rec, a, done, evals, px, py, bx0, bx1, by0, by1,
+                                    ox, oy);
             if (active) {
                 float* o = raycol + 3 * int64_t(ray.y);
                 o[0] = a.c0;
@@ -1099,7 +1102,7 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
         cur = next;
         fcur = fnxt;
     }
-    if (pairs) count_pairs(pairs, evals, blended);
+    if (COUNT) count_pairs(pairs, evals, blended);
 }
 
 // Block class across frames: one block of four warps per group list too long
@@ -1402,13 +1405,17 @@ cudaError_t launch_composite_rays_warp(int cap, int cls, const FrameDesc* frames
     if (max_items <= 0 || n_frames <= 0) return cudaSuccess;
     const int64_t need = (max_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int64_t* pc = prefix + int64_t(cls) * (n_frames + 1);
+    const int t = kWarpsPerBlock * 32;
+    const size_t s1 = kWarpsPerBlock * sizeof(WarpSmem<512>), s2 = kWarpsPerBlock * sizeof(WarpSmem<1024>);
     if (cap == 1024)
-        return launch_persistent(composite_rays_warp_kernel<1024>, kWarpsPerBlock * 32,
-                                 kWarpsPerBlock * sizeof(WarpSmem<1024>), need, frames, pc, n_frames,
-                                 cls, cursor, pairs, s);
-    return launch_persistent(composite_rays_warp_kernel<512>, kWarpsPerBlock * 32,
-                             kWarpsPerBlock * sizeof(WarpSmem<512>), need, frames, pc, n_frames, cls,
-                             cursor, pairs, s);
+        return pairs ? launch_persistent(composite_rays_warp_kernel<1024, true>, t, s2, need, frames,
+                                         pc, n_frames, cls, cursor, pairs, s)
+                     : launch_persistent(composite_rays_warp_kernel<1024, false>, t, s2, need, frames,
+                                         pc, n_frames, cls, cursor, pairs, s);
+    return pairs ? launch_persistent(composite_rays_warp_kernel<512, true>, t, s1, need, frames, pc,
+                                     n_frames, cls, cursor, pairs, s)
+                 : launch_persistent(composite_rays_warp_kernel<512, false>, t, s1, need, frames, pc,
+                                     n_frames, cls, cursor, pairs, s);
 }
 
 cudaError_t launch_composite_rays_block(int block_cap, const FrameDesc* frames,

@@ -134,6 +134,7 @@ struct dl_ctx {
     int32_t std_view_w = 0, std_view_h = 0;  // DL_OPT_STANDARD_VIEW_SIZE (0: panel)
     int32_t heap_cap = 128;                  // DL_OPT_HEAP_CAPACITY
     bool timing = false;
+    bool count_pairs = false;  // with timing: the compositing pair counters
     dl_frame_stats stats{};
     int32_t n_batches = 0;  // live dl_batch objects on this context
 };

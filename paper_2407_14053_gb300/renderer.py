@@ -164,8 +164,10 @@ class Renderer:
         """Longest tile list (512 or 1024 keys; 0 = none) one warp composites."""
         B.dl_set_option(self.ctx, B.DL_OPT_WARP_LIST_CAP, int(cap))
 
-    def enable_stage_timing(self, on: bool = True) -> None:
-        B.dl_enable_stage_timing(self.ctx, on)
+    def enable_stage_timing(self, on: bool = True, count_pairs: bool = True) -> None:
+        """CUDA events around each frame's stages; count_pairs also counts the
+        compositing pairs (the kernels' counting variant)."""
+        B.dl_enable_stage_timing(self.ctx, (1 if count_pairs else 2) if on else 0)
 
     def stats(self) -> dict:
         return B.dl_last_frame_stats(self.ctx)
