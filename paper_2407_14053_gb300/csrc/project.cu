@@ -69,7 +69,10 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
 #pragma unroll
             for (int c = 0; c < 3; ++c) sh[i][c] = to_f(G.sh[(g * NC + i) * 3 + c]);
 
-        for (int32_t v = 0; v < nv; ++v) {
+        // warps start at different views (and wrap around), so warps in
+        // flight add to the counters of different views' tiles
+        int32_t v = int32_t((g >> 5) % nv);
+        for (int32_t k = 0; k < nv; ++k, v = v + 1 == nv ? 0 : v + 1) {
             const Cam cam = load_cam(cams + v);
             const int64_t e = int64_t(v) * p.n + g;
             const float tx = cam.r[0] * mx + cam.r[1] * my + cam.r[2] * mz + cam.t[0];
