@@ -674,23 +674,35 @@ struct RayTable {
     uint4 mask[8];
 };
 
+// A warp's shared memory holds its group's keys while it sorts them and,
+// once sorted, only their low words (Gaussian index << 4 | quadrant nibble)
+// beside the record batches and the ray table: the two phases share the
+// space, which keeps the 1024-key class at six blocks per SM.
 template <int CAP>
-struct WarpSmem {
+struct WarpSort {
     static constexpr int kBuckets = CAP / 4;  // ~4 keys a bucket: insertion-sorted
     unsigned long long sk[CAP];
-    uint32_t bstart[kBuckets + 1];
-    uint32_t bfill[kBuckets];
+    uint32_t bstart[kBuckets];  // bucket sizes, starts, then (after the scatter) ends
+};
+template <int CAP>
+struct WarpStream {
+    uint32_t idx[CAP];
     float4 buf[2][3][32];
     RayTable rays;
+};
+template <int CAP>
+union WarpSmem {
+    WarpSort<CAP> s;
+    WarpStream<CAP> c;
 };
 
 // Warp-level version of block_sort (len <= CAP).  Lists of up to 512 keys
 // are held in registers; longer ones are re-read from global memory per pass.
 template <int CAP>
 __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t start, int len,
-                          WarpSmem<CAP>& W) {
+                          WarpSort<CAP>& W) {
     const int lane = threadIdx.x & 31;
-    constexpr int kWarpBuckets = WarpSmem<CAP>::kBuckets;
+    constexpr int kWarpBuckets = WarpSort<CAP>::kBuckets;
     constexpr int KPL = (CAP <= 512 ? CAP : 512) / 32;
     unsigned long long kr[KPL];
     uint32_t lo = 0xFFFFFFFFu, hi = 0u;
@@ -719,8 +731,7 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
     while (NB < len) NB <<= 1;
     NB >>= 1;
     if (NB > kWarpBuckets) NB = kWarpBuckets;
-    for (int b = lane; b <= NB; b += 32) W.bstart[b] = 0u;
-    for (int b = lane; b < NB; b += 32) W.bfill[b] = 0u;
+    for (int b = lane; b < NB; b += 32) W.bstart[b] = 0u;
     __syncwarp();
     const float scale = float(NB) / (float(hi - lo) + 1.0f);
     auto bucket = [&](unsigned long long k) {
@@ -751,27 +762,25 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
             W.bstart[b] = run;
             run += c;
         }
-        if (lane == 0) W.bstart[NB] = uint32_t(len);
     }
     __syncwarp();
+    // scatter: bstart[b] serves as bucket b's cursor, so afterwards it holds
+    // the bucket's end (= the start of bucket b + 1)
     if (in_regs) {
 #pragma unroll
         for (int j = 0; j < KPL; ++j)
-            if (j * 32 + lane < len) {
-                const int b = bucket(kr[j]);
-                W.sk[W.bstart[b] + atomicAdd(&W.bfill[b], 1u)] = kr[j];
-            }
+            if (j * 32 + lane < len) W.sk[atomicAdd(&W.bstart[bucket(kr[j])], 1u)] = kr[j];
     } else {
         for (int i = lane; i < len; i += 32) {
             const unsigned long long k = keys[start + i];
-            const int b = bucket(k);
-            W.sk[W.bstart[b] + atomicAdd(&W.bfill[b], 1u)] = k;
+            W.sk[atomicAdd(&W.bstart[bucket(k)], 1u)] = k;
         }
     }
     __syncwarp();
+    auto bucket_begin = [&](int b) { return b == 0 ? 0u : W.bstart[b - 1]; };
     bool big = false;
     for (int b = lane; b < NB; b += 32)
-        big |= W.bstart[b + 1] - W.bstart[b] > uint32_t(kBucketSortLimit);
+        big |= W.bstart[b] - bucket_begin(b) > uint32_t(kBucketSortLimit);
     if (__any_sync(0xffffffffu, big)) {
         int P = 1;
         while (P < len) P <<= 1;
@@ -793,7 +802,7 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
             }
     } else {
         for (int b = lane; b < NB; b += 32) {
-            const int b0 = int(W.bstart[b]), b1 = int(W.bstart[b + 1]);
+            const int b0 = int(bucket_begin(b)), b1 = int(W.bstart[b]);
             for (int i = b0 + 1; i < b1; ++i) {
                 const unsigned long long k = W.sk[i];
                 int j = i - 1;
@@ -804,6 +813,22 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
                 W.sk[j + 1] = k;
             }
         }
+        __syncwarp();
+    }
+}
+
+// Keeps the low words of the warp's sorted keys (Gaussian index << 4 |
+// nibble) in place of the keys: chunk by chunk, each chunk read whole before
+// it is written, and a chunk's 32 words land on keys already read (the words
+// of chunk c take bytes [128 c, 128 c + 128), below the chunk's own keys).
+template <int CAP>
+__device__ __forceinline__ void narrow_keys(WarpSmem<CAP>& W, int len) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < len; base += 32) {
+        const int i = base + lane;
+        const uint32_t lo = i < len ? uint32_t(W.s.sk[i]) : 0u;
+        __syncwarp();
+        if (i < len) W.c.idx[i] = lo;
         __syncwarp();
     }
 }
@@ -910,10 +935,10 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
     auto issue = [&](int b) {
         const int i = b * 32 + lane;
         if (i < len) {
-            const int64_t e = vbase + (uint32_t(W.sk[i]) >> 4);
-            cp_async16(&W.buf[b & 1][0][lane], rec + 3 * e);
-            cp_async16(&W.buf[b & 1][1][lane], rec + 3 * e + 1);
-            cp_async16(&W.buf[b & 1][2][lane], rec + 3 * e + 2);
+            const int64_t e = vbase + (W.c.idx[i] >> 4);
+            cp_async16(&W.c.buf[b & 1][0][lane], rec + 3 * e);
+            cp_async16(&W.c.buf[b & 1][1][lane], rec + 3 * e + 1);
+            cp_async16(&W.c.buf[b & 1][2][lane], rec + 3 * e + 2);
         }
         cp_async_commit();
     };
@@ -923,13 +948,14 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
         else cp_async_commit();
         cp_async_wait<1>();
         __syncwarp();
-        const float4* c0 = W.buf[b & 1][0];
-        const float4* c1 = W.buf[b & 1][1];
-        const float4* c2 = W.buf[b & 1][2];
+        const float4* c0 = W.c.buf[b & 1][0];
+        const float4* c1 = W.c.buf[b & 1][1];
+        const float4* c2 = W.c.buf[b & 1][2];
         const int n = len - b * 32 < 32 ? len - b * 32 : 32;
         float u, v, A, B, C, L;
         const bool hit = batch_conic(c0, c1, c2, n, bx0, bx1, by0, by1, u, v, A, B, C, L);
-        eval32<COUNT>(c0, c1, c2, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.rays, ox, oy);
+        eval32<COUNT>(c0, c1, c2, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.c.rays, ox,
+                      oy);
         if (__all_sync(0xffffffffu, done)) break;
     }
     cp_async_wait<0>();
@@ -1068,7 +1094,8 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
         const int rbeg = cur.z, nrays = int(uint32_t(cur.w) >> 16), len = cur.w & 0xFFFF;
         const int v = group / d.cp.ntiles;
         const float half_w = d.cp.half_w, half_h = d.cp.half_h;
-        warp_sort<CAP>(d.keys, start, len, W);
+        warp_sort<CAP>(d.keys, start, len, W.s);
+        narrow_keys<CAP>(W, len);
         if (nxt < n_items) {  // warm L2 for the next group
             const FrameDesc& dn = F[fnxt];
             const int nlen = next.w & 0xFFFF, nr = int(uint32_t(next.w) >> 16);
@@ -1085,7 +1112,7 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
             int bx0, bx1, by0, by1;
             warp_box(active, col, row, bx0, bx1, by0, by1);
             float ox, oy;
-            ray_table(W.rays, active, px, py, ox, oy, bx0, bx1, by0, by1, half_w, half_h);
+            ray_table(W.c.rays, active, px, py, ox, oy, bx0, bx1, by0, by1, half_w, half_h);
             Acc a{1.f, 0.f, 0.f, 0.f, 0u};
             bool done = !active;
             warp_stream<CAP, COUNT>(W, len, vbase, rec, a, done, evals, px, py, bx0, bx1, by0, by1,
