@@ -680,7 +680,10 @@ struct RayTable {
 // space, which keeps the 1024-key class at six blocks per SM.
 template <int CAP>
 struct WarpSort {
-    static constexpr int kBuckets = CAP / 4;  // ~4 keys a bucket: insertion-sorted
+    // about one key a bucket (buckets are insertion-sorted, and depths
+    // cluster); for CAP = 512 the 256 buckets still fit in the space the
+    // stream phase needs anyway
+    static constexpr int kBuckets = CAP <= 512 ? 256 : CAP / 4;
     unsigned long long sk[CAP];
     uint32_t bstart[kBuckets];  // bucket sizes, starts, then (after the scatter) ends
 };
@@ -695,6 +698,10 @@ union WarpSmem {
     WarpSort<CAP> s;
     WarpStream<CAP> c;
 };
+// six blocks of four warps per SM (228 KB of shared memory, 1 KB of it
+// reserved per block)
+static_assert(6 * (4 * sizeof(WarpSmem<1024>) + 1024) <= 228 * 1024, "1024-key class: 6 blocks");
+static_assert(6 * (4 * sizeof(WarpSmem<512>) + 1024) <= 228 * 1024, "512-key class: 6 blocks");
 
 // Warp-level version of block_sort (len <= CAP).  Lists of up to 512 keys
 // are held in registers; longer ones are re-read from global memory per pass.
@@ -729,7 +736,6 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
     hi = __reduce_max_sync(0xffffffffu, hi);
     int NB = 1;
     while (NB < len) NB <<= 1;
-    NB >>= 1;
     if (NB > kWarpBuckets) NB = kWarpBuckets;
     for (int b = lane; b < NB; b += 32) W.bstart[b] = 0u;
     __syncwarp();
