@@ -680,10 +680,11 @@ struct RayTable {
 // space, which keeps the 1024-key class at six blocks per SM.
 template <int CAP>
 struct WarpSort {
-    // about one key a bucket (buckets are insertion-sorted, and depths
-    // cluster); for CAP = 512 the 256 buckets still fit in the space the
-    // stream phase needs anyway
-    static constexpr int kBuckets = CAP <= 512 ? 256 : CAP / 4;
+    // at least one bucket a key up to 352 (or 320) keys: buckets are
+    // insertion-sorted and depths cluster; for CAP = 512 the buckets fit in
+    // the space the stream phase needs anyway, for CAP = 1024 the sort phase
+    // sets the size (six blocks per SM)
+    static constexpr int kBuckets = CAP <= 512 ? 352 : 320;
     unsigned long long sk[CAP];
     uint32_t bstart[kBuckets];  // bucket sizes, starts, then (after the scatter) ends
 };
