@@ -63,23 +63,26 @@ __device__ __forceinline__ float log2_alpha(float px, float py, float u, float v
 // alpha = min(0.99, 2^log2_alpha); skip alpha < 1/255 (CHECK_L2: tested
 // first on log2 alpha, which spares the ex2 for records that miss the ray,
 // then on alpha itself); stop before T (1 - alpha) = T - alpha T would drop
-// below 1e-4.  COUNT keeps the composited-pair statistic.
+// below 1e-4.  After the log2 test the steps are selects, not branches: a
+// skipped record adds 0 alpha T = 0 to the colour and leaves T (>= 1e-4) as
+// it is.  COUNT keeps the composited-pair statistic.
 template <bool CHECK_L2 = true, bool COUNT = true>
 __device__ __forceinline__ bool blend(Acc& a, float px, float py, const float4& q0,
                                       const float4& q1, float b) {
     const float l2 = log2_alpha(px, py, q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
     if (CHECK_L2 && l2 < kLog2MinAlpha) return true;
-    const float alpha = fminf(0.99f, ex2_approx(l2));
-    if (alpha < (1.0f / 255.0f)) return true;
-    const float w = alpha * a.T;
-    const float Tn = a.T - w;
-    if (Tn < 1e-4f) return false;
+    float alpha = fminf(0.99f, ex2_approx(l2));
+    alpha = alpha < (1.0f / 255.0f) ? 0.f : alpha;
+    const float w0 = alpha * a.T;
+    const float Tn = a.T - w0;
+    const bool go = Tn >= 1e-4f;
+    const float w = go ? w0 : 0.f;
     a.c0 = fmaf(w, q1.z, a.c0);
     a.c1 = fmaf(w, q1.w, a.c1);
     a.c2 = fmaf(w, b, a.c2);
-    a.T = Tn;
-    if (COUNT) ++a.blended;
-    return true;
+    a.T = go ? Tn : a.T;
+    if (COUNT && go && alpha > 0.f) ++a.blended;
+    return go;
 }
 
 // Adds the block's evaluated and composited pair counts to pairs[0..1].
@@ -704,8 +707,9 @@ union WarpSmem {
 static_assert(6 * (4 * sizeof(WarpSmem<1024>) + 1024) <= 228 * 1024, "1024-key class: 6 blocks");
 static_assert(6 * (4 * sizeof(WarpSmem<512>) + 1024) <= 228 * 1024, "512-key class: 6 blocks");
 
-// Warp-level version of block_sort (len <= CAP).  Lists of up to 512 keys
-// are held in registers; longer ones are re-read from global memory per pass.
+// Warp-level version of block_sort (len <= CAP).  The first 512 keys are
+// held in registers; the rest of a longer list is re-read from global memory
+// (L2) per pass.
 template <int CAP>
 __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t start, int len,
                           WarpSort<CAP>& W) {
@@ -744,13 +748,13 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
     auto bucket = [&](unsigned long long k) {
         return min(NB - 1, int(float(uint32_t(k >> 32) - lo) * scale));
     };
-    if (in_regs) {
+    // the first KPL * 32 keys are in registers, the rest are re-read
 #pragma unroll
-        for (int j = 0; j < KPL; ++j)
-            if (j * 32 + lane < len) atomicAdd(&W.bstart[bucket(kr[j])], 1u);
-    } else {
-        for (int i = lane; i < len; i += 32) atomicAdd(&W.bstart[bucket(keys[start + i])], 1u);
-    }
+    for (int j = 0; j < KPL; ++j)
+        if (j * 32 + lane < len) atomicAdd(&W.bstart[bucket(kr[j])], 1u);
+    if (!in_regs)
+        for (int i = KPL * 32 + lane; i < len; i += 32)
+            atomicAdd(&W.bstart[bucket(keys[start + i])], 1u);
     __syncwarp();
     {  // exclusive scan of bstart[0..NB)
         const int per = (NB + 31) / 32, b0 = lane * per;
@@ -773,16 +777,14 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
     __syncwarp();
     // scatter: bstart[b] serves as bucket b's cursor, so afterwards it holds
     // the bucket's end (= the start of bucket b + 1)
-    if (in_regs) {
 #pragma unroll
-        for (int j = 0; j < KPL; ++j)
-            if (j * 32 + lane < len) W.sk[atomicAdd(&W.bstart[bucket(kr[j])], 1u)] = kr[j];
-    } else {
-        for (int i = lane; i < len; i += 32) {
+    for (int j = 0; j < KPL; ++j)
+        if (j * 32 + lane < len) W.sk[atomicAdd(&W.bstart[bucket(kr[j])], 1u)] = kr[j];
+    if (!in_regs)
+        for (int i = KPL * 32 + lane; i < len; i += 32) {
             const unsigned long long k = keys[start + i];
             W.sk[atomicAdd(&W.bstart[bucket(k)], 1u)] = k;
         }
-    }
     __syncwarp();
     auto bucket_begin = [&](int b) { return b == 0 ? 0u : W.bstart[b - 1]; };
     bool big = false;
