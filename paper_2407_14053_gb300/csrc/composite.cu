@@ -693,8 +693,10 @@ struct WarpSort {
 };
 template <int CAP>
 struct WarpStream {
+    // record batches in flight: as many as six blocks of four warps leave room for
+    static constexpr int kSlots = CAP <= 512 ? 4 : 3;
     uint32_t idx[CAP];
-    float4 buf[2][3][32];
+    float4 buf[kSlots][3][32];
     RayTable rays;
 };
 template <int CAP>
@@ -931,8 +933,8 @@ __device__ __forceinline__ bool batch_conic(const float4* c0, const float4* c1, 
     return hit;
 }
 
-// Streams the warp's sorted list in batches of 32 records (cp.async double
-// buffering) and composites them, transposed, for the warp's rays.
+// Streams the warp's sorted list in batches of 32 records (cp.async, up to
+// three batches ahead) and composites them, transposed, for the warp's rays.
 template <int CAP, bool COUNT>
 __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t vbase,
                                             const float4* __restrict__ rec, Acc& a, bool& done,
@@ -941,25 +943,30 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
     const int lane = threadIdx.x & 31;
     const int nbatch = (len + 31) / 32;
     if (nbatch == 0) return;
-    auto issue = [&](int b) {
+    constexpr int S = WarpStream<CAP>::kSlots;
+    // batch b goes to slot b mod S; S - 1 batches are in flight ahead of the
+    // one being composited (one cp.async group per batch, empty past the end)
+    auto issue = [&](int b, int slot) {
         const int i = b * 32 + lane;
-        if (i < len) {
+        if (b < nbatch && i < len) {
             const int64_t e = vbase + (W.c.idx[i] >> 4);
-            cp_async16(&W.c.buf[b & 1][0][lane], rec + 3 * e);
-            cp_async16(&W.c.buf[b & 1][1][lane], rec + 3 * e + 1);
-            cp_async16(&W.c.buf[b & 1][2][lane], rec + 3 * e + 2);
+            cp_async16(&W.c.buf[slot][0][lane], rec + 3 * e);
+            cp_async16(&W.c.buf[slot][1][lane], rec + 3 * e + 1);
+            cp_async16(&W.c.buf[slot][2][lane], rec + 3 * e + 2);
         }
         cp_async_commit();
     };
-    issue(0);
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) issue(k, k);
+    int slot = 0;  // b mod S
     for (int b = 0; b < nbatch; ++b) {
-        if (b + 1 < nbatch) issue(b + 1);
-        else cp_async_commit();
-        cp_async_wait<1>();
+        issue(b + S - 1, slot == 0 ? S - 1 : slot - 1);
+        cp_async_wait<S - 1>();
         __syncwarp();
-        const float4* c0 = W.c.buf[b & 1][0];
-        const float4* c1 = W.c.buf[b & 1][1];
-        const float4* c2 = W.c.buf[b & 1][2];
+        const float4* c0 = W.c.buf[slot][0];
+        const float4* c1 = W.c.buf[slot][1];
+        const float4* c2 = W.c.buf[slot][2];
+        slot = slot + 1 == S ? 0 : slot + 1;
         const int n = len - b * 32 < 32 ? len - b * 32 : 32;
         float u, v, A, B, C, L;
         const bool hit = batch_conic(c0, c1, c2, n, bx0, bx1, by0, by1, u, v, A, B, C, L);
