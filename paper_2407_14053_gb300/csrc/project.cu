@@ -213,9 +213,9 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
 // depth << 32 | index << 4.  The low nibble stays free for the quadrant bits
 // that the block class sets after sorting; the index is unique in a group, so
 // they never decide the order.
-constexpr int kEmitRounds = 4;
+constexpr int kEmitRounds = 2;
 
-__global__ void emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
                                    const uint32_t* __restrict__ count,
                                    const uint32_t* __restrict__ gstart, uint32_t* __restrict__ gfill,
                                    unsigned long long* __restrict__ keys,
