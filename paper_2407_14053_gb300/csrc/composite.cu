@@ -231,8 +231,6 @@ composite_rays_kernel(CompositeParams p, const int4* __restrict__ work,
     __shared__ float4 s0[kRayThreads];
     __shared__ float4 s1[kRayThreads];
     __shared__ float4 s2[kRayThreads];
-    __shared__ int wbuf_all[kRayThreads / 32][64];
-    int* wbuf = wbuf_all[threadIdx.x >> 5];
     const int4 wi = work[blockIdx.x];
     const int v = wi.x / p.ntiles;
     const int rid = wi.y + int(threadIdx.x);
@@ -279,7 +277,6 @@ __global__ void composite_full_kernel(CompositeParams p, const uint2* __restrict
     float4* s0 = sm;
     float4* s1 = sm + nthr;
     float4* s2 = sm + 2 * nthr;
-    int* wbuf = reinterpret_cast<int*>(sm + 3 * nthr) + 64 * (threadIdx.x >> 5);
     const int group = blockIdx.x;
     const int v = group / p.ntiles;
     const int tile = group - v * p.ntiles;

@@ -259,6 +259,16 @@ def test_stage_timing_and_pair_counters(renderer):
     assert tot["n_launches"] >= 3 * 6
     # timing changes nothing in the image
     assert np.array_equal(img, ref)
+    # events only: the plain kernels run, no pair counts, the same image
+    renderer.enable_stage_timing(True, count_pairs=False)
+    try:
+        img2 = _frame(renderer, sid, did, L0, "directl")
+        tot2, n2 = renderer.stage_totals()
+    finally:
+        renderer.enable_stage_timing(False)
+    assert n2 == 1 and tot2["ms_composite"] > 0
+    assert tot2["pairs_evaluated"] == 0 and tot2["pairs_blended"] == 0
+    assert np.array_equal(img2, ref)
     renderer.free_display(did)
     renderer.free_scene(sid)
 
