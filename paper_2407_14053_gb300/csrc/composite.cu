@@ -662,8 +662,9 @@ composite_full_binned_kernel(CompositeParams p, const int32_t* __restrict__ list
 // DirectL tiles hold few rays (tens) and a few hundred Gaussians, so each
 // warp owns one (view, tile) group: it sorts the group's keys in its own
 // shared memory (warp-level bucket sort), streams the records in batches of
-// 32 with cp.async double buffering, and evaluates them transposed against
-// its rays.  Only __syncwarp is used, so warps never wait on each other.
+// 32 with cp.async (up to three batches ahead), and evaluates them transposed
+// against its rays.  Only __syncwarp is used, so warps never wait on each
+// other.
 constexpr int kWarpsPerBlock = 4;
 
 // Positions of the warp's rays about their box centre (x, y), written per
@@ -690,7 +691,8 @@ struct WarpSort {
 };
 template <int CAP>
 struct WarpStream {
-    // record batches in flight: as many as six blocks of four warps leave room for
+    // record batch slots (one being composited, the rest in flight): as
+    // many as six blocks of four warps per SM leave room for
     static constexpr int kSlots = CAP <= 512 ? 4 : 3;
     uint32_t idx[CAP];
     float4 buf[kSlots][3][32];
@@ -701,10 +703,12 @@ union WarpSmem {
     WarpSort<CAP> s;
     WarpStream<CAP> c;
 };
-// six blocks of four warps per SM (228 KB of shared memory, 1 KB of it
-// reserved per block)
-static_assert(6 * (4 * sizeof(WarpSmem<1024>) + 1024) <= 228 * 1024, "1024-key class: 6 blocks");
-static_assert(6 * (4 * sizeof(WarpSmem<512>) + 1024) <= 228 * 1024, "512-key class: 6 blocks");
+// six blocks of kWarpsPerBlock warps per SM (228 KB of shared memory, 1 KB
+// of it reserved per block)
+static_assert(6 * (kWarpsPerBlock * sizeof(WarpSmem<1024>) + 1024) <= 228 * 1024,
+              "1024-key class: 6 blocks");
+static_assert(6 * (kWarpsPerBlock * sizeof(WarpSmem<512>) + 1024) <= 228 * 1024,
+              "512-key class: 6 blocks");
 
 // Warp-level version of block_sort (len <= CAP).  The first 512 keys are
 // held in registers; the rest of a longer list is re-read from global memory
