@@ -691,9 +691,10 @@ struct WarpSort {
 };
 template <int CAP>
 struct WarpStream {
-    // record batch slots (one being composited, the rest in flight): as
-    // many as six blocks of four warps per SM leave room for
-    static constexpr int kSlots = CAP <= 512 ? 4 : 3;
+    // record batch slots (one being composited, the rest in flight): the
+    // 512-key class trades depth for occupancy (eight blocks per SM), the
+    // 1024-key class, held to six blocks by its sort phase, takes three
+    static constexpr int kSlots = CAP <= 512 ? 2 : 3;
     uint32_t idx[CAP];
     float4 buf[kSlots][3][32];
     RayTable rays;
@@ -703,22 +704,26 @@ union WarpSmem {
     WarpSort<CAP> s;
     WarpStream<CAP> c;
 };
-// six blocks of kWarpsPerBlock warps per SM (228 KB of shared memory, 1 KB
-// of it reserved per block)
-static_assert(6 * (kWarpsPerBlock * sizeof(WarpSmem<1024>) + 1024) <= 228 * 1024,
-              "1024-key class: 6 blocks");
-static_assert(6 * (kWarpsPerBlock * sizeof(WarpSmem<512>) + 1024) <= 228 * 1024,
-              "512-key class: 6 blocks");
+// blocks of kWarpsPerBlock warps per SM: eight (512-key class, 64
+// registers a thread) and six (1024-key class, 80 registers); 228 KB of
+// shared memory an SM, 1 KB of it reserved per block
+template <int CAP>
+constexpr int warp_class_blocks() { return CAP <= 512 ? 8 : 6; }
+static_assert(warp_class_blocks<1024>() * (kWarpsPerBlock * sizeof(WarpSmem<1024>) + 1024) <=
+                  228 * 1024, "1024-key class: 6 blocks");
+static_assert(warp_class_blocks<512>() * (kWarpsPerBlock * sizeof(WarpSmem<512>) + 1024) <=
+                  228 * 1024, "512-key class: 8 blocks");
 
-// Warp-level version of block_sort (len <= CAP).  The first 512 keys are
-// held in registers; the rest of a longer list is re-read from global memory
-// (L2) per pass.
+// Warp-level version of block_sort (len <= CAP).  The first KPL * 32 keys
+// (256 in the 512-key class, whose registers are held to 64 for eight blocks
+// per SM; 512 in the 1024-key class) are held in registers; the rest of a
+// longer list is re-read from global memory (L2) per pass.
 template <int CAP>
 __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t start, int len,
                           WarpSort<CAP>& W) {
     const int lane = threadIdx.x & 31;
     constexpr int kWarpBuckets = WarpSort<CAP>::kBuckets;
-    constexpr int KPL = (CAP <= 512 ? CAP : 512) / 32;
+    constexpr int KPL = CAP <= 512 ? 8 : 16;
     unsigned long long kr[KPL];
     uint32_t lo = 0xFFFFFFFFu, hi = 0u;
     const bool in_regs = len <= KPL * 32;
@@ -1082,7 +1087,7 @@ __device__ __forceinline__ int4 batch_item(const FrameDesc* __restrict__ F,
 // frame f.  While one group is composited, the next item is loaded and its
 // keys and rays are prefetched into L2.
 template <int CAP, bool COUNT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 6)  // 6 blocks (24 warps) a SM
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, warp_class_blocks<CAP>())
 composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __restrict__ prefix,
                            int n_frames, int cls, uint32_t* __restrict__ cursor,
                            unsigned long long* __restrict__ pairs) {
