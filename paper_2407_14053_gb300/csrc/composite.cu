@@ -1055,9 +1055,6 @@ __device__ void quadrant_stream(const unsigned long long* sk, int len, int q, in
     __syncwarp();
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
 
 // Index of the frame whose class range holds item i: the last f with
 // prefix[f] <= i (prefix ascending, prefix[0] = 0).
@@ -1084,8 +1081,9 @@ __device__ __forceinline__ int4 batch_item(const FrameDesc* __restrict__ F,
 // Persistent: resident warps take items until none is left (the first
 // n_warps by warp id, the rest claimed from *cursor: groups differ widely in
 // cost); an item is {group, first key, first ray, rays << 16 | keys} of
-// frame f.  While one group is composited, the next item is loaded and its
-// keys and rays are prefetched into L2.
+// frame f.  The next item is claimed and loaded before the current one is
+// composited.  (Prefetching its keys and rays into L2 as well measured
+// slower once eight blocks of the 512-key class were resident.)
 template <int CAP, bool COUNT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, warp_class_blocks<CAP>())
 composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __restrict__ prefix,
@@ -1118,12 +1116,6 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
         const float half_w = d.cp.half_w, half_h = d.cp.half_h;
         warp_sort<CAP>(d.keys, start, len, W.s);
         narrow_keys<CAP>(W, len);
-        if (nxt < n_items) {  // warm L2 for the next group
-            const FrameDesc& dn = F[fnxt];
-            const int nlen = next.w & 0xFFFF, nr = int(uint32_t(next.w) >> 16);
-            for (int i = lane * 16; i < nlen; i += 32 * 16) prefetch_l2(dn.keys + uint32_t(next.y) + i);
-            for (int i = lane * 16; i < nr; i += 32 * 16) prefetch_l2(dn.grouped + next.z + i);
-        }
         const int64_t vbase = int64_t(v) * d.cp.n;
         for (int r0 = 0; r0 < nrays; r0 += 32) {
             const int rid = r0 + lane;

@@ -376,3 +376,34 @@ def test_standard_below_panel_resolution(renderer, view):
         assert np.array_equal(img, _frame(renderer, sid, did, L0, "standard").reshape(-1))
     renderer.free_display(did)
     renderer.free_scene(sid)
+
+
+def test_every_list_class_matches_oracle(renderer):
+    """A dense cluster spreads the tiles' lists over every compositing class
+    (<= 256 keys, all in registers; <= 512; <= 1024; longer ones for the
+    block class): sampled subpixels match the oracle, and the frame does not
+    depend on which class composites a list (warp list caps 512, 1024 and
+    none)."""
+    scene = W.make_scene(W.SceneSpec(12000, 0, "clustered", "f32", seed=21))
+    scene["mean"] = (scene["mean"] * 0.6).astype(np.float32)
+    d = W.Display(192, 108, 5, 5.3, 1 / 6, view_span_deg=8.0)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 1.0)
+    try:
+        img = _frame(renderer, sid, did, L0, "directl")
+        st = renderer.stats()
+        assert st["max_list"] > 1024 and st["lists_large"] > 0 and st["lists_small"] > 0
+        sub = W.sample_subpixels(d, 600, windows=1, window_px=16, seed=5)
+        V, src = _sources(renderer, did, d, "directl")
+        ref = oracle.render_subpixels(oracle.Scene(scene), d, L0, sub, V, src)
+        ok, maxerr, nbad = _accept(img.reshape(-1)[sub], ref, TOL)
+        assert nbad == 0, f"{nbad} of {sub.size} subpixels outside tolerance; max |err| {maxerr:.3g}"
+        for cap in (1024, 0):
+            renderer.set_warp_cap(cap)
+            other = _frame(renderer, sid, did, L0, "directl")
+            assert np.abs(other - img).max() <= 1e-6, f"warp cap {cap}"
+    finally:
+        renderer.set_warp_cap(512)
+        renderer.free_display(did)
+        renderer.free_scene(sid)
