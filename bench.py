@@ -15,6 +15,9 @@ image.  The standard paradigm (every view rendered at panel resolution with
 the tile rasteriser, then interweaved) is timed the same way on the same GPU
 and reported under "standard".  Every step works on more than L2's worth of
 data (2.2 GB of per-view splat records alone), so no L2 flush is added.
+Timed frames run with stage events only (the compositing kernels' plain
+variant); the pair counts behind the roofline come from an untimed pass
+over the same poses with the counting variant.
 
 Two more sections follow on fresh contexts (skipped under torchrun):
 "graph_batched" renders the 8K panel (100 views, 3M Gaussians, BF16) from a
