@@ -681,10 +681,11 @@ struct RayTable {
 // space, which keeps the 1024-key class at six blocks per SM.
 template <int CAP>
 struct WarpSort {
-    // at least one bucket a key up to 352 (or 320) keys: buckets are
-    // insertion-sorted and depths cluster; for CAP = 512 the buckets fit in
-    // the space the stream phase needs anyway, for CAP = 1024 the sort phase
-    // sets the size (six blocks per SM)
+    // at least one bucket a key up to 352 (or 320) keys: the passes that
+    // order keys inside buckets grow with the most crowded bucket, and depths
+    // cluster; for CAP = 512 the buckets fit in the space the stream phase
+    // needs anyway, for CAP = 1024 the sort phase sets the size (six blocks
+    // per SM)
     static constexpr int kBuckets = CAP <= 512 ? 352 : 320;
     unsigned long long sk[CAP];
     uint32_t bstart[kBuckets];  // bucket sizes, starts, then (after the scatter) ends
@@ -818,19 +819,35 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
                 __syncwarp();
             }
     } else {
-        for (int b = lane; b < NB; b += 32) {
-            const int b0 = int(bucket_begin(b)), b1 = int(W.bstart[b]);
-            for (int i = b0 + 1; i < b1; ++i) {
-                const unsigned long long k = W.sk[i];
-                int j = i - 1;
-                while (j >= b0 && W.sk[j] > k) {
-                    W.sk[j + 1] = W.sk[j];
-                    --j;
+        // The buckets are in order, so only keys within a bucket are out of
+        // place, each by less than its bucket's size (<= kBucketSortLimit):
+        // odd-even transposition passes over the whole list (even pairs
+        // (2i, 2i + 1) as one 16-byte access, then odd pairs) sort it, and
+        // a pass without a swap ends the sort.  Every lane has work in every
+        // pass, unlike a lane-per-bucket insertion sort, where the warp waits
+        // for the most crowded of each 32 buckets.
+        ulonglong2* const pairs = reinterpret_cast<ulonglong2*>(W.sk);
+        for (;;) {
+            bool swapped = false;
+            for (int i = lane; 2 * i + 1 < len; i += 32) {
+                const ulonglong2 q = pairs[i];
+                if (q.x > q.y) {
+                    pairs[i] = make_ulonglong2(q.y, q.x);
+                    swapped = true;
                 }
-                W.sk[j + 1] = k;
             }
+            __syncwarp();
+            for (int i = 2 * lane + 1; i + 1 < len; i += 64) {
+                const unsigned long long x = W.sk[i], y = W.sk[i + 1];
+                if (x > y) {
+                    W.sk[i] = y;
+                    W.sk[i + 1] = x;
+                    swapped = true;
+                }
+            }
+            __syncwarp();
+            if (!__any_sync(0xffffffffu, swapped)) break;
         }
-        __syncwarp();
     }
 }
 
