@@ -781,7 +781,7 @@ dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, 
     const Scene& S = *si->second;
     const Display& D = *di->second;
     const size_t ne = size_t(D.q.nv) * size_t(S.n);
-    size_t b = ne * (48 + 8) + scan_tmp_bytes(int64_t(ne));
+    size_t b = ne * (48 + 16 + 8) + scan_tmp_bytes(int64_t(ne));  // records, metadata, counts, offsets
     // tile keys: about two tiles per (view, Gaussian) at the default shapes
     const size_t keys = 2 * ne;
     b += 2 * keys * 12 + radix_tmp_bytes(int64_t(keys));
@@ -866,7 +866,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     const int64_t ngroups = int64_t(nv) * ntiles;
     if (ngroups >= (int64_t(1) << 31) - 1) return fail(ctx, DL_ERR_CAPACITY, "too many tiles");
     DL_CK(W.rec.reserve(48 * size_t(ne)), "alloc records");
-    DL_CK(W.count.reserve(4 * size_t(ne)), "alloc counts");
+    DL_CK(W.meta.reserve(16 * size_t(ne)), "alloc tile metadata");
     DL_CK(W.gcount.reserve(4 * size_t(ngroups + 1)), "alloc group counts");
     DL_CK(W.gstart.reserve(4 * size_t(ngroups + 1)), "alloc group starts");
     DL_CK(W.gscan_tmp.reserve(scan_tmp_bytes(ngroups + 1)), "alloc scan");
@@ -877,7 +877,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     DL_CK(cudaMemsetAsync(W.small.p, 0, 256, s), "memset");
     DL_CK(cudaMemsetAsync(W.gcount.p, 0, 4 * size_t(ngroups + 1), s), "memset");
     const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
-    ProjectOut po{W.rec.as<float4>(), W.count.as<uint32_t>(), d_total64, W.gcount.as<uint32_t>()};
+    ProjectOut po{W.rec.as<float4>(), W.meta.as<uint4>(), d_total64, W.gcount.as<uint32_t>()};
     DL_CK(launch_project(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, s), "project");
     DL_CK(mark(1), "event");
     // group starts (one extra entry: gstart[ngroups] = number of keys) and the
@@ -963,7 +963,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         DL_CK(W.gfill.reserve(4 * size_t(ngroups)), "alloc");
         DL_CK(cudaMemsetAsync(W.gfill.p, 0, 4 * size_t(ngroups), s), "memset");
         DL_CK(mark(3), "event");
-        DL_CK(launch_emit_binned(pp, nv, W.rec.as<float4>(), W.count.as<uint32_t>(),
+        DL_CK(launch_emit_binned(pp, nv, W.meta.as<uint4>(),
                                  W.gstart.as<uint32_t>(), W.gfill.as<uint32_t>(),
                                  W.keys[0].as<unsigned long long>(), nullptr, 0u, nullptr, s),
               "emit binned");
@@ -1025,6 +1025,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         launches += 1 + (n_small > 0 ? 1 : 0) + (n_mid > 0 ? 1 : 0) + (n_large > 0 ? 1 : 0);
     } else {
         // ---- global tile keys and a stable LSD radix sort ----
+        DL_CK(W.count.reserve(4 * size_t(ne)), "alloc counts");
         DL_CK(W.offset.reserve(4 * size_t(ne)), "alloc offsets");
         DL_CK(W.scan_tmp.reserve(scan_tmp_bytes(ne)), "alloc scan");
         DL_CK(W.keys[1].reserve(8 * size_t(nk > 0 ? nk : 1)), "alloc keys");
@@ -1032,12 +1033,12 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         DL_CK(W.radix_tmp.reserve(radix_tmp_bytes(nk)), "alloc radix");
         DL_CK(W.ranges.reserve(8 * size_t(ngroups)), "alloc ranges");
         DL_CK(mark(3), "event");
+        DL_CK(launch_meta_counts(W.meta.as<uint4>(), ne, W.count.as<uint32_t>(), s), "counts");
         DL_CK(launch_exclusive_scan(W.count.as<uint32_t>(), W.offset.as<uint32_t>(), ne, nullptr,
                                     W.scan_tmp.p, s),
               "scan");
-        DL_CK(launch_emit_keys(pp, nv, W.rec.as<float4>(), W.count.as<uint32_t>(),
-                               W.offset.as<uint32_t>(), W.keys[0].as<unsigned long long>(),
-                               W.vals[0].as<uint32_t>(), s),
+        DL_CK(launch_emit_keys(pp, nv, W.meta.as<uint4>(), W.offset.as<uint32_t>(),
+                               W.keys[0].as<unsigned long long>(), W.vals[0].as<uint32_t>(), s),
               "emit keys");
         DL_CK(mark(4), "event");
         sort_bits = 28 + bits_for(ngroups);

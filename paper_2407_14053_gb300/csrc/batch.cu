@@ -28,7 +28,7 @@ struct Slot {
     int64_t ne_cap = 0, ng_cap = 0, nrays_cap = 0, nwork_cap = 0, key_cap = 0;
     int32_t nv_cap = 0;
     // offsets of the slot's device arrays in the arena
-    size_t o_rec = 0, o_count = 0, o_zero = 0, o_gstart = 0, o_keys = 0, o_lists = 0, o_raycol = 0;
+    size_t o_rec = 0, o_meta = 0, o_zero = 0, o_gstart = 0, o_keys = 0, o_lists = 0, o_raycol = 0;
     size_t zero_bytes = 0;  // gcount | gfill | meta, zeroed by every launch
     int64_t cam_first = 0;  // first camera of the slot in the staging cameras
     // assignment
@@ -160,13 +160,13 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
         const Scene& S = *z.S;
         const int32_t nv = z.D->q.nv;
         const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
-        ProjectOut po{b->at<float4>(z.o_rec), b->at<uint32_t>(z.o_count),
+        ProjectOut po{b->at<float4>(z.o_rec), b->at<uint4>(z.o_meta),
                       reinterpret_cast<unsigned long long*>(meta + 8), gcount};
         DL_CK(launch_project(S.dtype, attrs, z.pp, b->cams_d() + z.cam_first, nv, po, s), "project");
         uint32_t* gstart = b->at<uint32_t>(z.o_gstart);
         DL_CK(launch_exclusive_scan(gcount, gstart, z.ngroups + 1, nullptr, b->scan_tmp.p, s),
               "group scan");
-        DL_CK(launch_emit_binned(z.pp, nv, po.rec, po.count, gstart, gfill,
+        DL_CK(launch_emit_binned(z.pp, nv, po.meta, gstart, gfill,
                                  b->at<unsigned long long>(z.o_keys), gstart + z.ngroups,
                                  uint32_t(z.key_cap), fd.status, s),
               "emit binned");
@@ -294,7 +294,7 @@ dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plan
     };
     for (Slot& z : b->slots) {
         z.o_rec = take(48 * size_t(z.ne_cap));
-        z.o_count = take(4 * size_t(z.ne_cap));
+        z.o_meta = take(16 * size_t(z.ne_cap));
         z.zero_bytes = align_up(8 * size_t(z.ng_cap) + 4, 16) + 4 * kMetaWords;
         z.o_zero = take(z.zero_bytes);
         z.o_gstart = take(4 * size_t(z.ng_cap + 1));

@@ -70,10 +70,14 @@ struct ProjectParams {
 //       rect_c = c0 | c1 << 16, rect_r = r0 | r1 << 16 (bit patterns)
 // with log2 alpha = A dx^2 + B dx dy + C dy^2 + log2(opacity) at pixel offset
 // (dx, dy) from the mean (A, B, C are -log2(e)/2 times the conic's xx, 2xy, yy).
+// Per (view, Gaussian) tile metadata written beside the record, all that key
+// emission reads: {rect_c, rect_r (as in q2), depth key, tiles touched}; the
+// depth key is the FP32 bits of z minus those of 0.2 (z > 0.2), clamped to
+// 28 bits; tiles touched = 0 marks a culled Gaussian (the rest is then 0).
 struct ProjectOut {
     float4* rec;       // nv * n * 3
-    uint32_t* count;   // nv * n tiles touched (0 = culled)
-    unsigned long long* total;  // sum of count (atomic)
+    uint4* meta;       // nv * n
+    unsigned long long* total;  // sum of tiles touched (atomic)
     uint32_t* gcount;  // optional: keys per (view, tile) group (atomic; zeroed by caller)
 };
 
@@ -133,13 +137,15 @@ cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectPar
 // (gfill zeroed by the caller).
 // total_keys (optional) = gstart + n_groups: when it exceeds key_cap no key is
 // written and *status |= 1.
-cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const float4* rec,
-                               const uint32_t* count, const uint32_t* gstart, uint32_t* gfill,
+cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const uint4* meta,
+                               const uint32_t* gstart, uint32_t* gfill,
                                unsigned long long* keys, const uint32_t* total_keys,
                                uint32_t key_cap, uint32_t* status, cudaStream_t s);
-cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* rec,
-                             const uint32_t* count, const uint32_t* offset,
-                             unsigned long long* keys, uint32_t* vals, cudaStream_t s);
+// tiles touched per (view, Gaussian) out of the metadata (for the radix path's scan)
+cudaError_t launch_meta_counts(const uint4* meta, int64_t n, uint32_t* count, cudaStream_t s);
+cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const uint4* meta,
+                             const uint32_t* offset, unsigned long long* keys, uint32_t* vals,
+                             cudaStream_t s);
 
 // ---- ray-order 3DGS (raycast.cu) ------------------------------------------
 constexpr int kMaxHeap = 256;       // largest heap capacity c_h

@@ -94,7 +94,7 @@ struct PendingFrame {
 };
 
 struct Workspace {
-    DevBuf cams, rec, count, offset, scan_tmp, keys[2], vals[2], ranges, radix_tmp, Mm, out, small,
+    DevBuf cams, rec, meta, count, offset, scan_tmp, keys[2], vals[2], ranges, radix_tmp, Mm, out, small,
         pairs, gcount, gstart, gfill, lists, gscan_tmp, raycol, fdesc;
     unsigned long long* h_total = nullptr;  // pinned, 256 bytes (copy of `small`)
     size_t last_bytes = 0;
@@ -110,7 +110,8 @@ struct Workspace {
         }
     }
     size_t footprint() const {
-        size_t b = cams.bytes + rec.bytes + count.bytes + offset.bytes + scan_tmp.bytes + ranges.bytes +
+        size_t b = cams.bytes + rec.bytes + meta.bytes + count.bytes + offset.bytes + scan_tmp.bytes +
+                   ranges.bytes +
                    radix_tmp.bytes + Mm.bytes + out.bytes + small.bytes + gcount.bytes + gstart.bytes +
                    gfill.bytes + lists.bytes + gscan_tmp.bytes + raycol.bytes;
         for (int i = 0; i < 2; ++i) b += keys[i].bytes + vals[i].bytes;

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
             const float ty = cam.r[3] * mx + cam.r[4] * my + cam.r[5] * mz + cam.t[1];
             const float tz = cam.r[6] * mx + cam.r[7] * my + cam.r[8] * mz + cam.t[2];
             uint32_t cnt = 0;
+            uint4 meta = make_uint4(0u, 0u, 0u, 0u);
             if (tz > 0.2f && visible_alpha) {
                 // EWA (Eq. (9)): T = J W, Sigma' = T Sigma T^T + 0.3 I
                 const float iz = rcp_approx(tz);  // tz > 0.2
@@ -159,10 +160,13 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
                         rec[0] = make_float4(uc, vc, -0.5f * kLog2e * cyy * id, kLog2e * cxy * id);
                         rec[1] = make_float4(-0.5f * kLog2e * cxx * id, log2o, col[0], col[1]);
                         rec[2] = make_float4(col[2], tz, __uint_as_float(rect_c), __uint_as_float(rect_r));
+                        uint32_t dk = __float_as_uint(tz) - __float_as_uint(0.2f);
+                        if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
+                        meta = make_uint4(rect_c, rect_r, dk, cnt);
                     }
                 }
             }
-            out.count[e] = cnt;
+            out.meta[e] = meta;
             my_total += cnt;
         }
     }
@@ -175,24 +179,29 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
 // Key of a (view, tile, Gaussian) overlap: (view*ntiles + tile) << 28 | depth
 // key, the depth key being the float bits of z minus those of 0.2 (z > 0.2,
 // so the difference is positive and ordered like z; 28 bits reach z = 2^29).
-__global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
-                                 const uint32_t* __restrict__ count,
+
+// Tiles touched per (view, Gaussian), out of the metadata, for the scan that
+// places the radix path's keys.
+__global__ void meta_counts_kernel(const uint4* __restrict__ meta, int64_t n,
+                                   uint32_t* __restrict__ count) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n;
+         e += int64_t(gridDim.x) * blockDim.x)
+        count[e] = meta[e].w;
+}
+
+__global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const uint4* __restrict__ meta,
                                  const uint32_t* __restrict__ offset,
                                  unsigned long long* __restrict__ keys,
                                  uint32_t* __restrict__ vals) {
     const int64_t total = int64_t(nv) * p.n;
     const int ntiles = p.ntx * p.nty;
-    const uint32_t zbits0 = __float_as_uint(0.2f);
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
-        const uint32_t cnt = count[e];
-        if (!cnt) continue;
-        const float4 q2 = rec[3 * e + 2];
-        const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
+        const uint4 m = meta[e];
+        if (!m.w) continue;
+        const uint32_t rx = m.x, ry = m.y, dk = m.z;
         const int tx0 = int(rx & 0xFFFF) >> p.tile_sx, tx1 = int(rx >> 16) >> p.tile_sx;
         const int ty0 = int(ry & 0xFFFF) >> p.tile_sy, ty1 = int(ry >> 16) >> p.tile_sy;
-        uint32_t dk = __float_as_uint(q2.y) - zbits0;
-        if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
         const int64_t v = e / p.n;
         const uint32_t gidx = uint32_t(e - v * p.n);
         uint32_t o = offset[e];
@@ -215,8 +224,7 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const float4* __re
 // they never decide the order.
 constexpr int kEmitRounds = 2;
 
-__global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, int32_t nv, const float4* __restrict__ rec,
-                                   const uint32_t* __restrict__ count,
+__global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, int32_t nv, const uint4* __restrict__ meta,
                                    const uint32_t* __restrict__ gstart, uint32_t* __restrict__ gfill,
                                    unsigned long long* __restrict__ keys,
                                    const uint32_t* __restrict__ total_keys, uint32_t key_cap,
@@ -227,7 +235,6 @@ __global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, in
     }
     const int64_t total = int64_t(nv) * p.n;
     const int ntiles = p.ntx * p.nty;
-    const uint32_t zbits0 = __float_as_uint(0.2f);
     const float rn = 1.0f / float(p.n);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -235,35 +242,26 @@ __global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, in
     // each warp takes 32 consecutive records and expands their (record,
     // tile) pairs into dense rounds of 32, so every lane emits a key per
     // round and each round costs one cursor atomic per group it touches
-    // the next iteration's count and record tail are loaded one iteration
-    // ahead (the tail unconditionally: culled records are few)
+    // the next iteration's metadata is loaded one iteration ahead
     int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    uint32_t cnt_next = 0u;
-    float4 q2_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint4 m_next = make_uint4(0u, 0u, 0u, 0u);
     auto fetch = [&](int64_t ww) {
         const int64_t en = ww * 32 + lane;
-        if (en < total) {
-            cnt_next = __ldg(count + en);
-            q2_next = __ldg(rec + 3 * en + 2);
-        } else {
-            cnt_next = 0u;
-        }
+        m_next = en < total ? __ldg(meta + en) : make_uint4(0u, 0u, 0u, 0u);
     };
     fetch(w);
     for (; w * 32 < total; w += warps) {
         const int64_t e = w * 32 + lane;
-        const uint32_t cnt = cnt_next;
-        const float4 q2 = q2_next;
+        const uint4 m = m_next;
+        const uint32_t cnt = m.w;
         fetch(w + warps);
         int tx0 = 0, ty0 = 0, span = 1;
         uint32_t vb = 0, khi = 0, klo = 0;
         if (cnt) {
-            const uint32_t rx = __float_as_uint(q2.z), ry = __float_as_uint(q2.w);
+            const uint32_t rx = m.x, ry = m.y, dk = m.z;
             tx0 = int(rx & 0xFFFF) >> p.tile_sx;
             span = (int(rx >> 16) >> p.tile_sx) - tx0 + 1;
             ty0 = int(ry & 0xFFFF) >> p.tile_sy;
-            uint32_t dk = __float_as_uint(q2.y) - zbits0;
-            if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
             // view and Gaussian of record e: a float quotient, corrected
             int64_t v = int64_t(float(e) * rn);
             int64_t gi = e - v * p.n;
@@ -378,28 +376,35 @@ cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectPar
     return launch_project_t<float>(attrs, p, cams, nv, out, s);
 }
 
-cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const float4* rec,
-                               const uint32_t* count, const uint32_t* gstart, uint32_t* gfill,
+cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const uint4* meta,
+                               const uint32_t* gstart, uint32_t* gfill,
                                unsigned long long* keys, const uint32_t* total_keys,
                                uint32_t key_cap, uint32_t* status, cudaStream_t s) {
     const int64_t total = int64_t(nv) * p.n;
     int64_t grid = (total + 255) / 256;
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
-    emit_binned_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, rec, count, gstart, gfill,
-                                                                     keys, total_keys, key_cap, status);
+    emit_binned_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, meta, gstart, gfill, keys,
+                                                                     total_keys, key_cap, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const float4* rec,
-                             const uint32_t* count, const uint32_t* offset,
-                             unsigned long long* keys, uint32_t* vals, cudaStream_t s) {
+cudaError_t launch_meta_counts(const uint4* meta, int64_t n, uint32_t* count, cudaStream_t s) {
+    int64_t grid = (n + 255) / 256;
+    const int64_t cap = int64_t(num_sms()) * 32;
+    if (grid > cap) grid = cap;
+    meta_counts_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(meta, n, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const uint4* meta,
+                             const uint32_t* offset, unsigned long long* keys, uint32_t* vals,
+                             cudaStream_t s) {
     const int64_t total = int64_t(nv) * p.n;
     int64_t grid = (total + 255) / 256;
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
-    emit_keys_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, rec, count, offset, keys,
-                                                                   vals);
+    emit_keys_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, meta, offset, keys, vals);
     return cudaGetLastError();
 }
 
