@@ -193,3 +193,45 @@ def test_autotuner_picks_the_fastest_candidate(env):
         assert (st["tile_w"], st["tile_h"]) == best
     finally:
         r.set_tile("directl", 32, 32)
+
+
+def test_8k_graph_batch_matches_oracle_on_a_sample():
+    """The 8K panel (100 views, 3M Gaussians, BF16) in the launch
+    configuration the benchmark times: one batch slot, the tile shape from
+    the autotuner, frames replayed from a captured CUDA graph with a new
+    pose.  Sampled subpixels match the oracle run on the stored (BF16)
+    attributes within 2e-3."""
+    from paper_2407_14053_gb300 import Renderer
+    wl = W.WORKLOADS["8k"]
+    d = wl.display
+    scene = W.make_scene(wl.scene)
+    r = Renderer(0)
+    try:
+        sid = r.load_gaussians(scene, "bf16")
+        did = r.set_display(d)
+        poses = [W.light_field_centre(wl.camera_distance, y) for y in (0.0, 2.0)]
+        best, _ = r.autotune_tile(sid, did, poses[0], [(32, 32), (64, 32)], reps=1)
+        b = r.batch([(sid, did, best, poses[0])], margin=1.25)
+        out = torch.full((d.height, d.width, 3), np.nan, dtype=torch.float32, device="cuda")
+        st = torch.cuda.Stream()
+        try:
+            b.assign(0, sid, did, out, tile=best)
+            with torch.cuda.stream(st):
+                b.capture()
+                for pose in poses:  # the second launch replays the graph
+                    b.set_pose(0, pose)
+                    b.launch()
+                assert b.wait() == [0]
+            st.synchronize()
+            img = out.cpu().numpy().reshape(-1)
+        finally:
+            b.close()
+    finally:
+        r.close()
+    V = oracle.view_map(d)
+    src = oracle.repurpose(d, V)
+    sub = W.sample_subpixels(d, 96, windows=1, window_px=6, seed=21)
+    ref = oracle.render_subpixels(oracle.Scene(W.quantise_storage(scene, "bf16")), d, poses[1], sub,
+                                  V, src)
+    ok = (img[sub] >= ref["lo"] - 2e-3) & (img[sub] <= ref["hi"] + 2e-3)
+    assert ok.all(), f"{int((~ok).sum())} of {sub.size} subpixels outside 2e-3"
