@@ -407,3 +407,24 @@ def test_every_list_class_matches_oracle(renderer):
         renderer.set_warp_cap(512)
         renderer.free_display(did)
         renderer.free_scene(sid)
+
+
+def test_4k60_f16_sampled(renderer):
+    """The serving mix's 4K panel with 60 views and an FP16-stored scene
+    (300k Gaussians, SH degree 3): sampled subpixels match the oracle run on
+    the stored attributes within 2e-3."""
+    d = W.WORKLOADS["4k"].display.replace(num_views=60)
+    scene = W.make_scene(W.SceneSpec(300_000, 3, "clustered", "f16", seed=17))
+    sid = renderer.load_gaussians(scene, "f16")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 3.0)
+    try:
+        img = _frame(renderer, sid, did, L0, "directl").reshape(-1)
+    finally:
+        renderer.free_display(did)
+        renderer.free_scene(sid)
+    sub = W.sample_subpixels(d, 512, windows=1, window_px=8, seed=23)
+    V, src = _sources(renderer, did, d, "directl")
+    ref = oracle.render_subpixels(oracle.Scene(W.quantise_storage(scene, "f16")), d, L0, sub, V, src)
+    ok, maxerr, nbad = _accept(img[sub], ref, TOL)
+    assert nbad == 0, f"{nbad} of {sub.size} subpixels outside 2e-3; max |err| {maxerr:.3g}"

@@ -36,9 +36,14 @@ def _check_tables(renderer, d):
     renderer.free_display(did)
 
 
-@pytest.mark.parametrize("name", ["tiny", "1080p", "4k"])
+@pytest.mark.parametrize("name", ["tiny", "1080p", "4k", "8k"])
 def test_workload_tables(renderer, name):
     _check_tables(renderer, W.WORKLOADS[name].display)
+
+
+def test_serving_4k60_tables(renderer):
+    # the serving mix's third panel: the 4K lens with 60 views
+    _check_tables(renderer, W.WORKLOADS["4k"].display.replace(num_views=60))
 
 
 @pytest.mark.parametrize("name", list(W.PAPER_PANELS))
