@@ -56,6 +56,25 @@ FLOP_PER_EVAL = 13
 FLOP_PER_BLEND = 9
 SMS = 152
 FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16  # ex2 results an SM produces per clock
+# algorithmic bytes of the compositing stage (see the roofline section)
+KEY_BYTES = 8
+RECORD_BYTES = 40
+RAY_COLOUR_BYTES = 12
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_hbm_gbs():
+    """The copy bandwidth measured on the GB300s (driver-written
+    peaks file), else the earlier single measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(path))["hbm_gbs"])
+        if v > 0:
+            return v, "measured: STREAM-style copy on this pool's GB300s (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return HBM_FALLBACK_GBS, "fallback: 6.8 TB/s, one earlier copy measurement on a GB300"
 
 
 def parse():
@@ -556,25 +575,54 @@ def main():
         e2e = {"value": reduce_sum(args.steps, world, dev) / wall, "unit": "frames/s",
                "h2d_bytes_per_step": cam_bytes, "d2h_bytes_per_step": 12 * d.width * d.height}
 
-    # ---- roofline of the compositing stage (ALU bound) ----
+    # ---- roofline of the compositing stage ----
     # The stage is the persistent warp-per-tile kernel's two classes (lists
     # of <= 512 and <= 1024 keys; longer lists would add the block class),
     # timed with CUDA events on the launching stream around the launches.
+    # Lower bounds on its time from the algorithmic work:
+    #   FP32: FLOP_PER_EVAL ops per evaluated (ray, Gaussian) pair plus
+    #         FLOP_PER_BLEND per composited pair, against 152 SMs x 128 lanes
+    #         x 2 (FMA) x 2070 MHz;
+    #   MUFU: one ex2 per evaluated pair, against 152 SMs x 16 x 2070 MHz;
+    #   HBM:  per key its 8-byte sort key and a 40-byte record (the nine
+    #         floats the test and blend need, padded), per ray 12 bytes of
+    #         colour, against the measured copy bandwidth.
+    # The roofline is the largest of the three (the binding one); its
+    # fraction is that bound's time over the stage's time.
     comp_ms = dl_stages["composite"]
-    flops = FLOP_PER_EVAL * dl_stages["pairs_evaluated"] + FLOP_PER_BLEND * dl_stages["pairs_blended"]
+    comp_s = comp_ms / 1e3 if comp_ms > 0 else float("inf")
     clk = 2070.0
+    flops = FLOP_PER_EVAL * dl_stages["pairs_evaluated"] + FLOP_PER_BLEND * dl_stages["pairs_blended"]
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
-    achieved = flops / (comp_ms / 1e3) / 1e12 if comp_ms > 0 else 0.0
+    mufu_peak = SMS * MUFU_LANES_PER_SM * clk * 1e6
+    bytes_alg = dl_stages["keys"] * (KEY_BYTES + RECORD_BYTES) + n_rays * RAY_COLOUR_BYTES
+    hbm_gbs, hbm_source = measured_hbm_gbs()
+    bounds_ms = {"hbm": 1e3 * bytes_alg / (hbm_gbs * 1e9),
+                 "alu": 1e3 * flops / (peak_tflops * 1e12),
+                 "mufu": 1e3 * dl_stages["pairs_evaluated"] / mufu_peak}
+    bound = max(bounds_ms, key=bounds_ms.get)
     src_file = os.path.join(ROOT, "paper_2407_14053_gb300", "csrc", "composite.cu")
     kname = "composite_rays_warp_kernel"
-    roofline = {"kernel": kname + " (512- and 1024-key classes: the compositing stage)",
-                "bound": "alu", "achieved": achieved,
-                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+    alu = {"achieved": flops / comp_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+           "frac": flops / comp_s / 1e12 / peak_tflops,
+           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+           "flop_per_launch": flops,
+           "flop_model": f"{FLOP_PER_EVAL} per evaluated (ray, Gaussian) pair + "
+                         f"{FLOP_PER_BLEND} per composited pair"}
+    if bound == "hbm":
+        head = {"bound": "hbm", "achieved": bytes_alg / comp_s / 1e9, "peak": hbm_gbs,
+                "unit": "GB/s", "frac": bytes_alg / comp_s / 1e9 / hbm_gbs,
+                "peak_source": hbm_source}
+    else:  # FP32 or MUFU arithmetic binds: reported against the FP32 peak
+        head = {"bound": "alu", "achieved": alu["achieved"], "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": bounds_ms[bound] / comp_ms,
+                "peak_source": alu["peak_source"] + f" ({bound} binds)"}
+    roofline = {"kernel": kname + " (512- and 1024-key classes: the compositing stage)", **head,
                 "traffic": load_traffic(kname, args.workload, src_file),
-                "flop_per_launch": flops, "ms_per_launch": comp_ms,
-                "flop_model": f"{FLOP_PER_EVAL} per evaluated (ray, Gaussian) pair + "
-                              f"{FLOP_PER_BLEND} per composited pair"}
+                "bytes_per_launch": bytes_alg, "ms_per_launch": comp_ms,
+                "byte_model": f"{KEY_BYTES} B key + {RECORD_BYTES} B record per key, "
+                              f"{RAY_COLOUR_BYTES} B per ray",
+                "bounds_ms": bounds_ms, "alu": alu}
 
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
