@@ -59,7 +59,7 @@ FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16  # ex2 results an SM produces per clock
 # algorithmic bytes of the compositing stage (see the roofline section)
 KEY_BYTES = 8
-RECORD_BYTES = 40
+RECORD_BYTES = 36
 RAY_COLOUR_BYTES = 12
 HBM_FALLBACK_GBS = 6800.0
 
@@ -584,8 +584,8 @@ def main():
     #         FLOP_PER_BLEND per composited pair, against 152 SMs x 128 lanes
     #         x 2 (FMA) x 2070 MHz;
     #   MUFU: one ex2 per evaluated pair, against 152 SMs x 16 x 2070 MHz;
-    #   HBM:  per key its 8-byte sort key and a 40-byte record (the nine
-    #         floats the test and blend need, padded), per ray 12 bytes of
+    #   HBM:  per key its 8-byte sort key and the nine floats of its record
+    #         that the test and the blend need (36 bytes), per ray 12 bytes of
     #         colour, against the measured copy bandwidth.
     # The roofline is the largest of the three (the binding one); its
     # fraction is that bound's time over the stage's time.
