@@ -59,8 +59,15 @@ enum {
     DL_STANDARD = 1,      /* all N_v views at panel resolution + Alg. 1   */
     DL_REQUIRED_ONLY = 2, /* identity ray assignment: blend only the pixels
                              the panel shows (Table 3, "Required Only")   */
-    DL_RAYCAST = 3        /* the rays of DL_DIRECTL cast through the scene:
+    DL_RAYCAST = 3,       /* the rays of DL_DIRECTL cast through the scene:
                              ray-order 3DGS (Sec. 7, Alg. 3)              */
+    DL_STANDARD_SR = 4    /* the paper's "HR w SR" baseline: all N_v views
+                             at panel resolution as DL_STANDARD, then each
+                             subpixel takes channel k of its view at its
+                             repurposed source pixel (Sec. 5) instead of its
+                             own pixel; equals DL_DIRECTL's image, computed
+                             the standard way.  Tiles: DL_STANDARD's; the
+                             DL_OPT_STANDARD_VIEW_SIZE option does not apply */
 };
 
 typedef struct dl_ctx dl_ctx;
@@ -171,7 +178,8 @@ dl_status dl_get_ray_table(dl_ctx* ctx, int32_t display_id, uint32_t* ray_of, in
  * camera axes x right, y down, z forward (host memory, read during the
  * call).  View v's camera is T_v = R_y(-theta_v) L0 with theta_v =
  * -theta_d/2 + v theta_d/(N_v-1) (Eq. (17)).
- * mode: DL_DIRECTL, DL_STANDARD or DL_REQUIRED_ONLY.
+ * mode: DL_DIRECTL, DL_STANDARD, DL_REQUIRED_ONLY, DL_RAYCAST or
+ * DL_STANDARD_SR (see the mode enum).
  * out: h*w*3 floats, device memory if out_on_device else host memory (the
  * call then copies the frame back and returns once it is there).
  * Synchronises `stream` once per frame to size the tile-key buffers.

@@ -24,7 +24,7 @@ DL_ERR_DEVICE_CHECK = -6
 DL_ERR_CAPACITY = -7
 
 DL_F32, DL_BF16, DL_F16 = 0, 1, 2
-DL_DIRECTL, DL_STANDARD, DL_REQUIRED_ONLY, DL_RAYCAST = 0, 1, 2, 3
+DL_DIRECTL, DL_STANDARD, DL_REQUIRED_ONLY, DL_RAYCAST, DL_STANDARD_SR = 0, 1, 2, 3, 4
 DL_OPT_SORT_MODE, DL_OPT_EVAL_DIRECTL, DL_OPT_EVAL_STANDARD, DL_OPT_WARP_LIST_CAP = 1, 2, 3, 4
 DL_OPT_STANDARD_VIEW_SIZE, DL_OPT_HEAP_CAPACITY = 5, 6
 DL_SORT_AUTO, DL_SORT_RADIX, DL_SORT_BINNED = 0, 1, 2

@@ -654,6 +654,7 @@ dl_status dl_encode_rays(dl_ctx* ctx, int32_t display_id, const float* ray_rgb, 
 dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h) {
     dl_status st = check_ctx(ctx);
     if (st) return st;
+    if (mode == DL_STANDARD_SR) mode = DL_STANDARD;  // the same rendering
     if (mode < 0 || mode > 2) return fail(ctx, DL_ERR_INVALID_ARG, "mode %d", mode);
     if (!pow2_in(tile_w, 8, 256) || !pow2_in(tile_h, 8, 256))
         return fail(ctx, DL_ERR_INVALID_ARG, "tile %dx%d: powers of two in [8, 256]", tile_w, tile_h);
@@ -785,7 +786,7 @@ dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, 
     // tile keys: about two tiles per (view, Gaussian) at the default shapes
     const size_t keys = 2 * ne;
     b += 2 * keys * 12 + radix_tmp_bytes(int64_t(keys));
-    if (mode == DL_STANDARD) b += size_t(D.q.nv) * D.q.w * D.q.h * 12;
+    if (mode == DL_STANDARD || mode == DL_STANDARD_SR) b += size_t(D.q.nv) * D.q.w * D.q.h * 12;
     *bytes = std::max(b, ctx->ws.last_bytes);
     return DL_OK;
 }
@@ -796,7 +797,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     dl_status st = check_ctx(ctx);
     if (st) return st;
     if (!L0_c2w || !out) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
-    if (mode < 0 || mode > DL_RAYCAST) return fail(ctx, DL_ERR_INVALID_ARG, "mode %d", mode);
+    if (mode < 0 || mode > DL_STANDARD_SR) return fail(ctx, DL_ERR_INVALID_ARG, "mode %d", mode);
     auto si = ctx->scenes.find(scene_id);
     if (si == ctx->scenes.end()) return fail(ctx, DL_ERR_NOT_FOUND, "scene %d", scene_id);
     auto di = ctx->displays.find(display_id);
@@ -823,12 +824,16 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     };
     DL_CK(mark(0), "event");
     if (mode == DL_RAYCAST) return render_raycast(ctx, S, D, L0_c2w, out, out_on_device, s, E);
+    // "HR w SR" renders as DL_STANDARD (views at panel resolution) and
+    // gathers each subpixel from its repurposed source pixel at the end
+    const bool sr = mode == DL_STANDARD_SR;
+    if (sr) mode = DL_STANDARD;
 
     const int32_t nv = D.q.nv, w = D.q.w, h = D.q.h;
     const int32_t tw = ctx->tile[mode][0], th = ctx->tile[mode][1];
     // the standard paradigm's views: panel resolution, or LR / MR upsampled
     // while interweaving
-    const bool lowres = mode == DL_STANDARD && ctx->std_view_w > 0 &&
+    const bool lowres = mode == DL_STANDARD && !sr && ctx->std_view_w > 0 &&
                         (ctx->std_view_w != w || ctx->std_view_h != h);
     const int32_t rw = lowres ? ctx->std_view_w : w, rh = lowres ? ctx->std_view_h : h;
     RaySet* R = nullptr;
@@ -1070,6 +1075,9 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     if (lowres) {
         DL_CK(launch_resize_interweave(w, h, rw, rh, D.V.as<uint16_t>(), Mm, dst, s),
               "upsample and interweave");
+    } else if (sr) {
+        DL_CK(launch_repurposed_interweave(w, h, D.V.as<uint16_t>(), D.rep.src.as<uint32_t>(), Mm, dst, s),
+              "repurposed interweave");
     } else if (mode == DL_STANDARD) {
         DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), Mm, dst, s), "interweave");
     } else {

@@ -1330,6 +1330,25 @@ __global__ void interweave_kernel(int32_t w, int32_t h, const uint16_t* __restri
     }
 }
 
+// The paper's "HR w SR" assembly: subpixel (x, y, k) takes channel k of view
+// V(x, 3y + k) at its repurposed source pixel src = (x' << 16 | y') (Sec. 5)
+// rather than at (x, y); a source outside the panel (never produced by the
+// repurposing) reads the subpixel's own pixel.
+__global__ void repurposed_interweave_kernel(int32_t w, int32_t h, const uint16_t* __restrict__ V,
+                                             const uint32_t* __restrict__ src,
+                                             const float* __restrict__ Mm,
+                                             float* __restrict__ out) {
+    const int64_t total = 3 * int64_t(w) * h;
+    const int64_t plane = int64_t(h) * w * 3;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t sp = src[i];
+        const uint32_t sr = sp >> 16, sc = sp & 0xFFFFu;
+        const int64_t p = (sr < uint32_t(h) && sc < uint32_t(w)) ? int64_t(sr) * w + sc : i / 3;
+        out[i] = Mm[int64_t(V[i]) * plane + 3 * p + (i - 3 * (i / 3))];
+    }
+}
+
 // Alg. 1 with views rendered at rw x rh and upsampled while interweaving:
 // subpixel (x, y, k) takes channel k of view V(x, 3y + k) bilinearly at
 // column y rw / w, row x rh / h of that view (pixel (r, c) of a view samples
@@ -1529,6 +1548,16 @@ cudaError_t launch_resize_interweave(int32_t w, int32_t h, int32_t rw, int32_t r
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
     resize_interweave_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(w, h, rw, rh, V, Mm, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repurposed_interweave(int32_t w, int32_t h, const uint16_t* V, const uint32_t* src,
+                                        const float* Mm, float* out, cudaStream_t s) {
+    const int64_t total = 3 * int64_t(w) * h;
+    int64_t grid = (total + 255) / 256;
+    const int64_t cap = int64_t(num_sms()) * 32;
+    if (grid > cap) grid = cap;
+    repurposed_interweave_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(w, h, V, src, Mm, out);
     return cudaGetLastError();
 }
 

@@ -289,6 +289,9 @@ cudaError_t launch_partition(const int4* gwork, int64_t n_work, const uint32_t* 
 cudaError_t launch_resize_interweave(int32_t w, int32_t h, int32_t rw, int32_t rh,
                                      const uint16_t* V, const float* Mm, float* out,
                                      cudaStream_t s);
+// "HR w SR": out[i] = channel k of view V[i] at the repurposed source pixel src[i].
+cudaError_t launch_repurposed_interweave(int32_t w, int32_t h, const uint16_t* V, const uint32_t* src,
+                                        const float* Mm, float* out, cudaStream_t s);
 cudaError_t launch_interweave(int32_t w, int32_t h, int32_t nv, const uint16_t* V, const float* Mm,
                               float* out, cudaStream_t s);
 

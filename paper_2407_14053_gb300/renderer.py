@@ -10,7 +10,7 @@ import torch
 from . import _binding as B
 
 MODES = {"directl": B.DL_DIRECTL, "standard": B.DL_STANDARD, "required_only": B.DL_REQUIRED_ONLY,
-         "raycast": B.DL_RAYCAST}
+         "raycast": B.DL_RAYCAST, "standard_sr": B.DL_STANDARD_SR}
 DTYPES = {"f32": (B.DL_F32, torch.float32), "bf16": (B.DL_BF16, torch.bfloat16),
           "f16": (B.DL_F16, torch.float16)}
 
