@@ -99,11 +99,6 @@ __device__ __forceinline__ float slab_enter(const float4& lo, const float4& hi, 
     return (tn <= tf && tf > kNearT) ? tn : INFINITY;
 }
 
-// (t, index) order of heap entries
-__device__ __forceinline__ bool before(float ta, int ia, float tb, int ib) {
-    return ta < tb || (ta == tb && ia < ib);
-}
-
 // Highest-density point and alpha of Gaussian g along the ray.
 __device__ __forceinline__ float rc_alpha(const float4* __restrict__ gauss, int64_t g, float ox,
                                           float oy, float oz, float dx, float dy, float dz, float& t) {
@@ -132,8 +127,9 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
     constexpr int NC = (DEG + 1) * (DEG + 1);
     const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (r >= n_rays) return;
-    float ht[kMaxHeap];
-    int hi[kMaxHeap];
+    // heap entries packed as t's FP32 bits << 32 | Gaussian index: t > 0, so
+    // the integer order of the packed key is the (t, index) order
+    unsigned long long hk[kMaxHeap];
     int hn = 0;
     const uint32_t px = ray_pix[r];
     const Cam& cam = cams[ray_view[r]];
@@ -156,37 +152,34 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
         const uint32_t e = stack[--sp];
         const int lv = int(e >> 28);
         const int64_t i = int64_t(e & 0x0FFFFFFFu);
-        const float bound = hn == heap_cap ? ht[0] : INFINITY;
+        const float bound = hn == heap_cap ? __uint_as_float(uint32_t(hk[0] >> 32)) : INFINITY;
         if (lv == 0) {  // leaf: Gaussians 8i..8i+7
             for (int64_t g = 8 * i; g < 8 * i + 8 && g < n; ++g) {
                 float t;
                 const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
                 if (!(a >= kMinAlpha) || !(t > kNearT)) continue;
-                const int gi = int(g);
+                const unsigned long long key =
+                    (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | uint32_t(g);
                 if (hn < heap_cap) {  // insert and sift up
                     int k = hn++;
                     while (k > 0) {
                         const int p = (k - 1) >> 1;
-                        if (!before(ht[p], hi[p], t, gi)) break;
-                        ht[k] = ht[p];
-                        hi[k] = hi[p];
+                        if (!(hk[p] < key)) break;
+                        hk[k] = hk[p];
                         k = p;
                     }
-                    ht[k] = t;
-                    hi[k] = gi;
-                } else if (before(t, gi, ht[0], hi[0])) {  // replace the farthest
+                    hk[k] = key;
+                } else if (key < hk[0]) {  // replace the farthest
                     int k = 0;
                     for (;;) {
                         int c = 2 * k + 1;
                         if (c >= hn) break;
-                        if (c + 1 < hn && before(ht[c], hi[c], ht[c + 1], hi[c + 1])) ++c;
-                        if (!before(t, gi, ht[c], hi[c])) break;
-                        ht[k] = ht[c];
-                        hi[k] = hi[c];
+                        if (c + 1 < hn && hk[c] < hk[c + 1]) ++c;
+                        if (!(key < hk[c])) break;
+                        hk[k] = hk[c];
                         k = c;
                     }
-                    ht[k] = t;
-                    hi[k] = gi;
+                    hk[k] = key;
                 }
             }
         } else {  // children 8i..8i+7 of the level below, nearest first
@@ -212,24 +205,18 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
     }
     // pop the heap from its farthest entry: list in ascending (t, index)
     for (int k = hn - 1; k > 0; --k) {
-        const float t0 = ht[0];
-        const int i0 = hi[0];
-        const float tl = ht[k];
-        const int il = hi[k];
+        const unsigned long long top = hk[0], last = hk[k];
         int j = 0;
         for (;;) {
             int c = 2 * j + 1;
             if (c >= k) break;
-            if (c + 1 < k && before(ht[c], hi[c], ht[c + 1], hi[c + 1])) ++c;
-            if (!before(tl, il, ht[c], hi[c])) break;
-            ht[j] = ht[c];
-            hi[j] = hi[c];
+            if (c + 1 < k && hk[c] < hk[c + 1]) ++c;
+            if (!(last < hk[c])) break;
+            hk[j] = hk[c];
             j = c;
         }
-        ht[j] = tl;
-        hi[j] = il;
-        ht[k] = t0;
-        hi[k] = i0;
+        hk[j] = last;
+        hk[k] = top;
     }
     // blend front to back, colour from the SH at the ray direction
     float Y[16];
@@ -237,7 +224,7 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
     float tr = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;  // transmittance, colour
     for (int k = 0; k < hn; ++k) {
         float t;
-        const int64_t g = hi[k];
+        const int64_t g = int64_t(uint32_t(hk[k]));
         const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
         const float tn = tr * (1.f - a);
         if (tn < 1e-4f) break;
