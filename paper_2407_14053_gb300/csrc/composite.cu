@@ -371,7 +371,9 @@ __device__ void block_scan_counts(uint32_t* c, int n) {
     __syncthreads();
 }
 
-constexpr int kBucketSortLimit = 64;  // largest bucket sorted by one thread
+// largest bucket sorted inside its list (by one thread in the block sort, by
+// odd-even passes in the warp sort); a larger one sends the list to a bitonic sort
+constexpr int kBucketSortLimit = 64;
 
 // Sorts the group's keys (depth << 32 | Gaussian, all distinct) into sk:
 // a counting sort on the depth bucket floor((d - dmin) NB / (dmax - dmin + 1))
