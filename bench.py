@@ -64,6 +64,50 @@ RAY_COLOUR_BYTES = 12
 HBM_FALLBACK_GBS = 6800.0
 
 
+def compositing_roofline(comp_ms: float, keys: float, n_rays: float, evaluated: float,
+                         blended: float, hbm_gbs: float, hbm_source: str) -> dict:
+    """Roofline of the compositing stage from its algorithmic work.
+
+    Three lower bounds on the stage's time:
+      FP32: FLOP_PER_EVAL ops per evaluated (ray, Gaussian) pair plus
+            FLOP_PER_BLEND per composited pair, against 152 SMs x 128 lanes
+            x 2 (FMA) x 2070 MHz;
+      MUFU: one ex2 per evaluated pair, against 152 SMs x 16 x 2070 MHz;
+      HBM:  per key its 8-byte sort key and the nine floats of its record
+            that the test and the blend need (36 bytes), per ray 12 bytes of
+            colour, against the measured copy bandwidth.
+    The roofline is the largest of the three (the binding one); its fraction
+    is that bound's time over the stage's time."""
+    comp_s = comp_ms / 1e3 if comp_ms > 0 else float("inf")
+    clk = 2070.0
+    flops = FLOP_PER_EVAL * evaluated + FLOP_PER_BLEND * blended
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    mufu_peak = SMS * MUFU_LANES_PER_SM * clk * 1e6
+    bytes_alg = keys * (KEY_BYTES + RECORD_BYTES) + n_rays * RAY_COLOUR_BYTES
+    bounds_ms = {"hbm": 1e3 * bytes_alg / (hbm_gbs * 1e9),
+                 "alu": 1e3 * flops / (peak_tflops * 1e12),
+                 "mufu": 1e3 * evaluated / mufu_peak}
+    bound = max(bounds_ms, key=bounds_ms.get)
+    alu = {"achieved": flops / comp_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+           "frac": flops / comp_s / 1e12 / peak_tflops,
+           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+           "flop_per_launch": flops,
+           "flop_model": f"{FLOP_PER_EVAL} per evaluated (ray, Gaussian) pair + "
+                         f"{FLOP_PER_BLEND} per composited pair"}
+    if bound == "hbm":
+        head = {"bound": "hbm", "achieved": bytes_alg / comp_s / 1e9, "peak": hbm_gbs,
+                "unit": "GB/s", "frac": bytes_alg / comp_s / 1e9 / hbm_gbs,
+                "peak_source": hbm_source}
+    else:  # FP32 or MUFU arithmetic binds: reported against the FP32 peak
+        head = {"bound": "alu", "achieved": alu["achieved"], "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": bounds_ms[bound] / comp_ms if comp_ms > 0 else 0.0,
+                "peak_source": alu["peak_source"] + f" ({bound} binds)"}
+    return {**head, "bytes_per_launch": bytes_alg, "ms_per_launch": comp_ms,
+            "byte_model": f"{KEY_BYTES} B key + {RECORD_BYTES} B record per key, "
+                          f"{RAY_COLOUR_BYTES} B per ray",
+            "bounds_ms": bounds_ms, "alu": alu}
+
+
 def measured_hbm_gbs():
     """The copy bandwidth measured on the GB300s (driver-written
     peaks file), else the earlier single measurement."""
@@ -590,50 +634,14 @@ def main():
     # The stage is the persistent warp-per-tile kernel's two classes (lists
     # of <= 512 and <= 1024 keys; longer lists would add the block class),
     # timed with CUDA events on the launching stream around the launches.
-    # Lower bounds on its time from the algorithmic work:
-    #   FP32: FLOP_PER_EVAL ops per evaluated (ray, Gaussian) pair plus
-    #         FLOP_PER_BLEND per composited pair, against 152 SMs x 128 lanes
-    #         x 2 (FMA) x 2070 MHz;
-    #   MUFU: one ex2 per evaluated pair, against 152 SMs x 16 x 2070 MHz;
-    #   HBM:  per key its 8-byte sort key and the nine floats of its record
-    #         that the test and the blend need (36 bytes), per ray 12 bytes of
-    #         colour, against the measured copy bandwidth.
-    # The roofline is the largest of the three (the binding one); its
-    # fraction is that bound's time over the stage's time.
-    comp_ms = dl_stages["composite"]
-    comp_s = comp_ms / 1e3 if comp_ms > 0 else float("inf")
-    clk = 2070.0
-    flops = FLOP_PER_EVAL * dl_stages["pairs_evaluated"] + FLOP_PER_BLEND * dl_stages["pairs_blended"]
-    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
-    mufu_peak = SMS * MUFU_LANES_PER_SM * clk * 1e6
-    bytes_alg = dl_stages["keys"] * (KEY_BYTES + RECORD_BYTES) + n_rays * RAY_COLOUR_BYTES
-    hbm_gbs, hbm_source = measured_hbm_gbs()
-    bounds_ms = {"hbm": 1e3 * bytes_alg / (hbm_gbs * 1e9),
-                 "alu": 1e3 * flops / (peak_tflops * 1e12),
-                 "mufu": 1e3 * dl_stages["pairs_evaluated"] / mufu_peak}
-    bound = max(bounds_ms, key=bounds_ms.get)
     src_file = os.path.join(ROOT, "paper_2407_14053_gb300", "csrc", "composite.cu")
     kname = "composite_rays_warp_kernel"
-    alu = {"achieved": flops / comp_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
-           "frac": flops / comp_s / 1e12 / peak_tflops,
-           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
-           "flop_per_launch": flops,
-           "flop_model": f"{FLOP_PER_EVAL} per evaluated (ray, Gaussian) pair + "
-                         f"{FLOP_PER_BLEND} per composited pair"}
-    if bound == "hbm":
-        head = {"bound": "hbm", "achieved": bytes_alg / comp_s / 1e9, "peak": hbm_gbs,
-                "unit": "GB/s", "frac": bytes_alg / comp_s / 1e9 / hbm_gbs,
-                "peak_source": hbm_source}
-    else:  # FP32 or MUFU arithmetic binds: reported against the FP32 peak
-        head = {"bound": "alu", "achieved": alu["achieved"], "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": bounds_ms[bound] / comp_ms,
-                "peak_source": alu["peak_source"] + f" ({bound} binds)"}
-    roofline = {"kernel": kname + " (512- and 1024-key classes: the compositing stage)", **head,
-                "traffic": load_traffic(kname, args.workload, src_file),
-                "bytes_per_launch": bytes_alg, "ms_per_launch": comp_ms,
-                "byte_model": f"{KEY_BYTES} B key + {RECORD_BYTES} B record per key, "
-                              f"{RAY_COLOUR_BYTES} B per ray",
-                "bounds_ms": bounds_ms, "alu": alu}
+    hbm_gbs, hbm_source = measured_hbm_gbs()
+    roofline = {"kernel": kname + " (512- and 1024-key classes: the compositing stage)",
+                **compositing_roofline(dl_stages["composite"], dl_stages["keys"], n_rays,
+                                       dl_stages["pairs_evaluated"], dl_stages["pairs_blended"],
+                                       hbm_gbs, hbm_source),
+                "traffic": load_traffic(kname, args.workload, src_file)}
 
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
