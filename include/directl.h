@@ -188,6 +188,24 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                           const double L0_c2w[16], int32_t mode, float* out,
                           int32_t out_on_device, void* stream);
 
+/*
+ * The frame of dl_render_frame, delivered to host memory without waiting for
+ * it (Sec. 4 steps (2)-(3), as dl_render_frame): the frame's kernels run on
+ * `stream`; its copy to `out` (host, h*w*3 floats; pinned, or the copy is
+ * not asynchronous) is enqueued on `copy_stream` behind them, so it overlaps
+ * the caller's next frame on `stream`.  `out` holds the frame once
+ * `copy_stream` has reached that point (cudaStreamSynchronize or an event);
+ * the caller keeps `out` alive and untouched until then.  The library writes
+ * the frame into one of two device frames used in turn; `stream` waits for
+ * the copy that read the same device frame two calls earlier.  Like
+ * dl_render_frame it synchronises `stream` once per frame to size the
+ * tile-key buffers.  DL_ERR_INVALID_ARG when `copy_stream` equals `stream`
+ * or a pointer is NULL.
+ */
+dl_status dl_render_frame_async_host(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
+                                     const double L0_c2w[16], int32_t mode, float* out,
+                                     void* stream, void* copy_stream);
+
 /* Encoded image from per-ray colours (Sec. 4 step (3) and Sec. 6: the rays
  * of U_rays are rendered by any renderer, then the subpixels take their
  * channel by the precomputed ray indices): out[i] = ray_rgb[3 ray_of[i] +

@@ -76,6 +76,8 @@ SIGNATURES = {
     "dl_get_ray_table": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     "dl_render_frame": (c_int32, [c_void_p, c_int32, c_int32, P(c_double), c_int32, c_void_p,
                                   c_int32, c_void_p]),
+    "dl_render_frame_async_host": (c_int32, [c_void_p, c_int32, c_int32, P(c_double), c_int32,
+                                             c_void_p, c_void_p, c_void_p]),
     "dl_query_footprint": (c_int32, [c_void_p, c_int32, c_int32, c_int32, P(ctypes.c_size_t)]),
     "dl_set_tile": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
     "dl_encode_rays": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -215,6 +217,15 @@ def dl_render_frame(ctx, scene_id: int, display_id: int, L0_c2w, mode: int, out_
     _check("dl_render_frame", ctx,
            lib().dl_render_frame(ctx, int(scene_id), int(display_id), L0, int(mode),
                                  c_void_p(out_ptr), int(out_on_device), c_void_p(stream)))
+
+
+def dl_render_frame_async_host(ctx, scene_id: int, display_id: int, L0_c2w, mode: int,
+                               out_ptr: int, stream: int, copy_stream: int) -> None:
+    L0 = (c_double * 16)(*[float(x) for x in L0_c2w])
+    _check("dl_render_frame_async_host", ctx,
+           lib().dl_render_frame_async_host(ctx, int(scene_id), int(display_id), L0, int(mode),
+                                            c_void_p(out_ptr), c_void_p(stream),
+                                            c_void_p(copy_stream)))
 
 
 def dl_query_footprint(ctx, scene_id: int, display_id: int, mode: int) -> int:

@@ -344,11 +344,66 @@ dl_status build_raycast(dl_ctx* ctx, Scene& S, cudaStream_t s) {
     return DL_OK;
 }
 
+// Where a frame's last kernel writes it, by output kind: the caller's device
+// buffer; the workspace frame, copied to the host on `s` (the call waits for
+// it); or one of two device frames used in turn, copied to the host on the
+// caller's copy stream so that the copy overlaps the next frame.  A frame
+// reused by the asynchronous kind waits (on `s`) for the copy that read it two
+// calls earlier.
+enum OutKind : int32_t { kOutHost = 0, kOutDevice = 1, kOutHostAsync = 2 };
+
+dl_status out_target(dl_ctx* ctx, float* out, int32_t kind, size_t bytes, cudaStream_t s,
+                     float** dst) {
+    Workspace& W = ctx->ws;
+    if (kind == kOutDevice) {
+        *dst = out;
+        return DL_OK;
+    }
+    if (kind == kOutHost) {
+        DL_CK(W.out.reserve(bytes), "alloc out");
+        *dst = W.out.as<float>();
+        return DL_OK;
+    }
+    const int k = W.aslot;
+    for (int i = 0; i < 2; ++i) {
+        if (!W.ev_frame[i]) DL_CK(cudaEventCreateWithFlags(&W.ev_frame[i], cudaEventDisableTiming), "event");
+        if (!W.ev_copied[i]) DL_CK(cudaEventCreateWithFlags(&W.ev_copied[i], cudaEventDisableTiming), "event");
+    }
+    if (W.copy_pending[k]) {
+        if (W.aout[k].bytes < bytes)  // the frame is replaced: its copy must have ended
+            DL_CK(cudaEventSynchronize(W.ev_copied[k]), "wait for an earlier copy");
+        else
+            DL_CK(cudaStreamWaitEvent(s, W.ev_copied[k], 0), "order after an earlier copy");
+    }
+    DL_CK(W.aout[k].reserve(bytes), "alloc out");
+    *dst = W.aout[k].as<float>();
+    return DL_OK;
+}
+
+// After the frame's last kernel: the copy to the host (kinds kOutHost and
+// kOutHostAsync); kOutHost's synchronisation is the caller's last step.
+dl_status out_finish(dl_ctx* ctx, float* out, int32_t kind, const float* dst, size_t bytes,
+                     cudaStream_t s, cudaStream_t cs) {
+    Workspace& W = ctx->ws;
+    if (kind == kOutHost) {
+        DL_CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s), "copy frame");
+    } else if (kind == kOutHostAsync) {
+        const int k = W.aslot;
+        DL_CK(cudaEventRecord(W.ev_frame[k], s), "event");
+        DL_CK(cudaStreamWaitEvent(cs, W.ev_frame[k], 0), "order the copy after the frame");
+        DL_CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, cs), "copy frame");
+        DL_CK(cudaEventRecord(W.ev_copied[k], cs), "event");
+        W.copy_pending[k] = true;
+        W.aslot = k ^ 1;
+    }
+    return DL_OK;
+}
+
 // DL_RAYCAST frame: the DirectL rays cast through the scene (Alg. 3), then
 // the ray colours gathered into the encoded image.  E: stage events (when
 // stage timing is on), the unused stages recorded empty.
 dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[16], float* out,
-                         int32_t out_on_device, cudaStream_t s, StageEvents* E) {
+                         int32_t kind, cudaStream_t s, cudaStream_t cs, StageEvents* E) {
     Workspace& W = ctx->ws;
     auto mark = [&](int i) -> cudaError_t { return E ? cudaEventRecord(E->e[i], s) : cudaSuccess; };
     RaySet& R = D.rep;
@@ -374,17 +429,15 @@ dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[
           "ray-order rendering");
     DL_CK(mark(7), "event");
     const size_t out_bytes = 12 * size_t(w) * size_t(h);
-    float* dst = out;
-    if (!out_on_device) {
-        DL_CK(W.out.reserve(out_bytes), "alloc out");
-        dst = W.out.as<float>();
-    }
+    float* dst = nullptr;
+    st = out_target(ctx, out, kind, out_bytes, s, &dst);
+    if (st) return st;
     DL_CK(launch_reorder(R.ray_of.as<uint32_t>(), W.raycol.as<float>(), 3 * int64_t(w) * h, dst,
                          nullptr, s),
           "reorder");
     DL_CK(mark(8), "event");
-    if (!out_on_device)
-        DL_CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, s), "copy frame");
+    st = out_finish(ctx, out, kind, dst, out_bytes, s, cs);
+    if (st) return st;
     dl_frame_stats& fs = ctx->stats;
     fs = dl_frame_stats{};
     fs.n_rays = R.n_rays;
@@ -395,9 +448,14 @@ dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[
         pf.launches = fs.n_launches;
     }
     W.last_bytes = W.footprint();
-    if (!out_on_device) DL_CK(cudaStreamSynchronize(s), "sync");
+    if (kind == kOutHost) DL_CK(cudaStreamSynchronize(s), "sync");
     return DL_OK;
 }
+
+// One frame of dl_render_frame / dl_render_frame_async_host (output kinds
+// above; `cs` is the copy stream of kOutHostAsync).
+dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const double L0_c2w[16],
+                       int32_t mode, float* out, int32_t kind, cudaStream_t s, cudaStream_t cs);
 
 }  // namespace dl
 
@@ -794,6 +852,26 @@ dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, 
 dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                           const double L0_c2w[16], int32_t mode, float* out, int32_t out_on_device,
                           void* stream) {
+    return render_frame(ctx, scene_id, display_id, L0_c2w, mode, out,
+                        out_on_device ? kOutDevice : kOutHost, static_cast<cudaStream_t>(stream),
+                        nullptr);
+}
+
+dl_status dl_render_frame_async_host(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
+                                     const double L0_c2w[16], int32_t mode, float* out,
+                                     void* stream, void* copy_stream) {
+    if (ctx && stream == copy_stream)
+        return fail(ctx, DL_ERR_INVALID_ARG, "copy_stream must differ from stream");
+    return render_frame(ctx, scene_id, display_id, L0_c2w, mode, out, kOutHostAsync,
+                        static_cast<cudaStream_t>(stream), static_cast<cudaStream_t>(copy_stream));
+}
+
+}  // extern "C"
+
+namespace dl {
+
+dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const double L0_c2w[16],
+                       int32_t mode, float* out, int32_t kind, cudaStream_t s, cudaStream_t cs) {
     dl_status st = check_ctx(ctx);
     if (st) return st;
     if (!L0_c2w || !out) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
@@ -805,7 +883,6 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     Scene& S = *si->second;
     Display& D = *di->second;
     Workspace& W = ctx->ws;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool timing = ctx->timing;
     StageEvents* E = nullptr;
     if (timing) {
@@ -823,7 +900,7 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         return timing ? cudaEventRecord(E->e[i], s) : cudaSuccess;
     };
     DL_CK(mark(0), "event");
-    if (mode == DL_RAYCAST) return render_raycast(ctx, S, D, L0_c2w, out, out_on_device, s, E);
+    if (mode == DL_RAYCAST) return render_raycast(ctx, S, D, L0_c2w, out, kind, s, cs, E);
     // "HR w SR" renders as DL_STANDARD (views at panel resolution) and
     // gathers each subpixel from its repurposed source pixel at the end
     const bool sr = mode == DL_STANDARD_SR;
@@ -946,11 +1023,9 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     cp.ntx = pp.ntx;
     cp.ntiles = int32_t(ntiles);
     const size_t out_bytes = 12 * size_t(w) * size_t(h);
-    float* dst = out;
-    if (!out_on_device) {
-        DL_CK(W.out.reserve(out_bytes), "alloc out");
-        dst = W.out.as<float>();
-    }
+    float* dst = nullptr;
+    st = out_target(ctx, out, kind, out_bytes, s, &dst);
+    if (st) return st;
     float* Mm = nullptr;
     float* raycol = nullptr;
     if (mode == DL_STANDARD) {
@@ -1086,8 +1161,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
     }
     launches += 1;
     DL_CK(mark(8), "event");
-    if (!out_on_device)
-        DL_CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, s), "copy frame");
+    st = out_finish(ctx, out, kind, dst, out_bytes, s, cs);
+    if (st) return st;
 
     dl_frame_stats& fs = ctx->stats;
     fs = dl_frame_stats{};
@@ -1110,8 +1185,8 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
         pf.max_list = fs.max_list;
     }
     W.last_bytes = W.footprint();
-    if (!out_on_device) DL_CK(cudaStreamSynchronize(s), "sync");
+    if (kind == kOutHost) DL_CK(cudaStreamSynchronize(s), "sync");
     return DL_OK;
 }
 
-}  // extern "C"
+}  // namespace dl

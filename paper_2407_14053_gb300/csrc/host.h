@@ -100,8 +100,19 @@ struct Workspace {
     size_t last_bytes = 0;
     std::vector<StageEvents*> ev_free;
     std::vector<PendingFrame> pending;
+    // frames copied to the host on the caller's copy stream
+    // (dl_render_frame_async_host): two device frames used in turn, the
+    // frame-written and copy-done events of each, and the next one to use
+    DevBuf aout[2];
+    cudaEvent_t ev_frame[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    bool copy_pending[2] = {false, false};
+    int aslot = 0;
     ~Workspace() {
         if (h_total) cudaFreeHost(h_total);
+        for (int i = 0; i < 2; ++i) {
+            if (ev_frame[i]) cudaEventDestroy(ev_frame[i]);
+            if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
+        }
         for (auto& f : pending) ev_free.push_back(f.ev);
         for (StageEvents* s : ev_free) {
             for (auto& e : s->e)
@@ -114,7 +125,7 @@ struct Workspace {
                    ranges.bytes +
                    radix_tmp.bytes + Mm.bytes + out.bytes + small.bytes + gcount.bytes + gstart.bytes +
                    gfill.bytes + lists.bytes + gscan_tmp.bytes + raycol.bytes;
-        for (int i = 0; i < 2; ++i) b += keys[i].bytes + vals[i].bytes;
+        for (int i = 0; i < 2; ++i) b += keys[i].bytes + vals[i].bytes + aout[i].bytes;
         return b;
     }
 };

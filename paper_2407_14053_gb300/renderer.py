@@ -138,6 +138,18 @@ class Renderer:
                           out.data_ptr(), 0, _stream())
         return out
 
+    def render_to_host_async(self, sid: int, did: int, L0, out: torch.Tensor,
+                             copy_stream: torch.cuda.Stream, mode: str = "directl"):
+        """Same frame written into a pinned host tensor by a copy on
+        `copy_stream`, which overlaps the next frame rendered on the current
+        stream; `out` holds the frame once `copy_stream` has reached the copy
+        (e.g. copy_stream.synchronize())."""
+        assert not out.is_cuda and out.is_contiguous() and out.is_pinned()
+        B.dl_render_frame_async_host(self.ctx, sid, did, np.asarray(L0, np.float64).ravel(),
+                                     MODES[mode], out.data_ptr(), _stream(),
+                                     copy_stream.cuda_stream)
+        return out
+
     def set_sort_mode(self, mode: str) -> None:
         """'auto', 'radix' or 'binned' (see DL_OPT_SORT_MODE)."""
         B.dl_set_option(self.ctx, B.DL_OPT_SORT_MODE,

@@ -222,6 +222,43 @@ def test_host_output_matches_device_output(renderer):
     renderer.free_scene(sid)
 
 
+def test_async_host_output_matches_device_output(renderer):
+    """Frames copied to the host on a second stream (two device frames used
+    in turn, each copy overlapping the next frame) equal the frames rendered
+    into device memory: across modes and poses, with a device-output frame in
+    between, and with a larger display whose frames replace the device frames
+    while earlier copies may still be pending."""
+    from paper_2407_14053_gb300 import DirectLError
+    d, scene = _tiny_case()
+    sid = renderer.load_gaussians(scene, "f32")
+    dids = {"small": renderer.set_display(d),
+            "big": renderer.set_display(d.replace(width=3 * d.width, height=3 * d.height))}
+    dims = {"small": (d.height, d.width), "big": (3 * d.height, 3 * d.width)}
+    plan = [("small", "directl", 0.0), ("small", "standard", 1.5), ("small", "raycast", -2.0),
+            ("big", "directl", 3.0), ("small", "required_only", 0.5), ("big", "standard", -1.0),
+            ("big", "directl", 2.0), ("small", "directl", -3.0)]
+    poses = [W.light_field_centre(4.0, a) for _, _, a in plan]
+    refs = [_frame(renderer, sid, dids[k], L0, m) for (k, m, _), L0 in zip(plan, poses)]
+    hosts = [torch.empty((*dims[k], 3), dtype=torch.float32).pin_memory() for k, _, _ in plan]
+    copy_stream = torch.cuda.Stream()
+    mid = None
+    for i, ((k, m, _), L0) in enumerate(zip(plan, poses)):
+        renderer.render_to_host_async(sid, dids[k], L0, hosts[i], copy_stream, m)
+        if i == 3:  # a device-output frame between asynchronous ones
+            mid = renderer.render(sid, dids["small"], poses[0], "directl")
+    copy_stream.synchronize()
+    torch.cuda.synchronize()
+    for i, (host, ref) in enumerate(zip(hosts, refs)):
+        assert np.array_equal(host.numpy(), ref), f"frame {i} {plan[i]}"
+    assert np.array_equal(mid.cpu().numpy(), refs[0])
+    with pytest.raises(DirectLError):  # the copy stream must be another stream
+        renderer.render_to_host_async(sid, dids["small"], poses[0], hosts[0],
+                                      torch.cuda.current_stream())
+    for did in dids.values():
+        renderer.free_display(did)
+    renderer.free_scene(sid)
+
+
 def test_invalid_arguments_are_reported(renderer):
     from paper_2407_14053_gb300 import DirectLError
     with pytest.raises(DirectLError):
