@@ -417,6 +417,10 @@ dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[
         st = build_raycast(ctx, S, s);
         if (st) return st;
     }
+    // the rays in DirectL's (view, tile) grouping: coherent warps
+    TileGroups* G = nullptr;
+    st = get_groups(ctx, D, R, ctx->tile[DL_DIRECTL][0], ctx->tile[DL_DIRECTL][1], s, &G);
+    if (st) return st;
     for (int i = 1; i <= 6; ++i) DL_CK(mark(i), "event");
     DL_CK(W.raycol.reserve(12 * size_t(R.n_rays > 0 ? R.n_rays : 1)), "alloc ray colours");
     const double pi = 3.14159265358979323846;
@@ -424,7 +428,7 @@ dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[
     const int64_t* meta = S.rc_meta.as<int64_t>();
     DL_CK(launch_raycast(S.dtype, S.sh_degree, S.rc_gauss.as<float4>(), S.rc_nodes.as<float4>(), meta,
                          meta + S.rc_levels, S.rc_levels, S.n, S.sh.p, R.ray_view.as<uint32_t>(),
-                         R.ray_pix.as<uint32_t>(), R.n_rays, W.cams.as<Cam>(), float(focal),
+                         R.ray_pix.as<uint32_t>(), G->grouped.as<int2>(), R.n_rays, W.cams.as<Cam>(), float(focal),
                          0.5f * float(w), 0.5f * float(h), ctx->heap_cap, W.raycol.as<float>(), s),
           "ray-order rendering");
     DL_CK(mark(7), "event");

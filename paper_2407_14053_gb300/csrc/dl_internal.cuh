@@ -161,12 +161,15 @@ cudaError_t launch_raycast_prepare(int dtype, const void* const* attrs, int64_t 
                                    float4* gbox, float4* nodes, const int64_t* level_off,
                                    const int64_t* level_n, int n_levels, cudaStream_t s);
 // One thread per ray (view ray_view, pixel ray_pix): ray colours into raycol
-// (3 floats per ray); level_off_dev / level_n_dev in device memory.
+// (3 floats per ray); level_off_dev / level_n_dev in device memory.  Thread i
+// casts ray order[i].y (order: a permutation of the rays as {pixel, ray id},
+// e.g. a tile grouping), or ray i when order is null.
 cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const float4* nodes,
                            const int64_t* level_off_dev, const int64_t* level_n_dev, int n_levels,
                            int64_t n, const void* sh, const uint32_t* ray_view,
-                           const uint32_t* ray_pix, int64_t n_rays, const Cam* cams, float focal,
-                           float half_w, float half_h, int heap_cap, float* raycol, cudaStream_t s);
+                           const uint32_t* ray_pix, const int2* order, int64_t n_rays,
+                           const Cam* cams, float focal, float half_w, float half_h, int heap_cap,
+                           float* raycol, cudaStream_t s);
 
 // ---- scan / radix sort / ranges (sort.cu) ---------------------------------
 size_t scan_tmp_bytes(int64_t n);

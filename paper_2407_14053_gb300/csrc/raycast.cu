@@ -121,12 +121,16 @@ __global__ void __launch_bounds__(128)
 rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nodes,
                 const int64_t* __restrict__ level_off, int n_levels, const int64_t* __restrict__ level_n,
                 int64_t n, const T* __restrict__ sh, const uint32_t* __restrict__ ray_view,
-                const uint32_t* __restrict__ ray_pix, int64_t n_rays, const Cam* __restrict__ cams,
-                float focal, float half_w, float half_h, int heap_cap,
-                float* __restrict__ raycol) {
+                const uint32_t* __restrict__ ray_pix, const int2* __restrict__ order,
+                int64_t n_rays, const Cam* __restrict__ cams, float focal, float half_w,
+                float half_h, int heap_cap, float* __restrict__ raycol) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
-    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (r >= n_rays) return;
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n_rays) return;
+    // thread i casts ray order[i].y: the rays grouped by (view, tile) and
+    // Morton-ordered inside a tile, so a warp's rays share a camera centre and
+    // nearly share a direction, and traverse the tree alike
+    const int64_t r = order ? int64_t(order[i].y) : i;
     // heap entries packed as t's FP32 bits << 32 | Gaussian index: t > 0, so
     // the integer order of the packed key is the (t, index) order
     unsigned long long hk[kMaxHeap];
@@ -307,15 +311,16 @@ cudaError_t launch_raycast_prepare(int dtype, const void* const* attrs, int64_t 
 cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const float4* nodes,
                            const int64_t* level_off_dev, const int64_t* level_n_dev, int n_levels,
                            int64_t n, const void* sh, const uint32_t* ray_view,
-                           const uint32_t* ray_pix, int64_t n_rays, const Cam* cams, float focal,
-                           float half_w, float half_h, int heap_cap, float* raycol, cudaStream_t s) {
+                           const uint32_t* ray_pix, const int2* order, int64_t n_rays,
+                           const Cam* cams, float focal, float half_w, float half_h, int heap_cap,
+                           float* raycol, cudaStream_t s) {
     if (n_rays <= 0) return cudaSuccess;
     const unsigned grid = unsigned((n_rays + 127) / 128);
 #define DL_RC(T, D)                                                                          \
     rc_trace_kernel<T, D><<<grid, 128, 0, s>>>(gauss, nodes, level_off_dev, n_levels,         \
                                                level_n_dev, n, static_cast<const T*>(sh),      \
-                                               ray_view, ray_pix, n_rays, cams, focal, half_w, \
-                                               half_h, heap_cap, raycol)
+                                               ray_view, ray_pix, order, n_rays, cams, focal,  \
+                                               half_w, half_h, heap_cap, raycol)
 #define DL_RC_DEG(T)                  \
     switch (sh_degree) {              \
         case 0: DL_RC(T, 0); break;   \
