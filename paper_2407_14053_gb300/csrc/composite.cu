@@ -372,7 +372,7 @@ __device__ void block_scan_counts(uint32_t* c, int n) {
 }
 
 // largest bucket sorted inside its list (by one thread in the block sort, by
-// odd-even passes in the warp sort); a larger one sends the list to a bitonic sort
+// odd-even phases in the warp sort); a larger one sends the list to a bitonic sort
 constexpr int kBucketSortLimit = 64;
 
 // Sorts the group's keys (depth << 32 | Gaussian, all distinct) into sk:
@@ -798,10 +798,10 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
         }
     __syncwarp();
     auto bucket_begin = [&](int b) { return b == 0 ? 0u : W.bstart[b - 1]; };
-    bool big = false;
-    for (int b = lane; b < NB; b += 32)
-        big |= W.bstart[b] - bucket_begin(b) > uint32_t(kBucketSortLimit);
-    if (__any_sync(0xffffffffu, big)) {
+    uint32_t most = 0u;  // the most crowded bucket's size
+    for (int b = lane; b < NB; b += 32) most = max(most, W.bstart[b] - bucket_begin(b));
+    most = __reduce_max_sync(0xffffffffu, most);
+    if (most > uint32_t(kBucketSortLimit)) {
         int P = 1;
         while (P < len) P <<= 1;
         for (int i = len + lane; i < P; i += 32) W.sk[i] = ~0ull;
@@ -822,33 +822,32 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
             }
     } else {
         // The buckets are in order, so only keys within a bucket are out of
-        // place, each by less than its bucket's size (<= kBucketSortLimit):
-        // odd-even transposition passes over the whole list (even pairs
-        // (2i, 2i + 1) as one 16-byte access, then odd pairs) sort it, and
-        // a pass without a swap ends the sort.  Every lane has work in every
-        // pass, unlike a lane-per-bucket insertion sort, where the warp waits
-        // for the most crowded of each 32 buckets.
+        // place, and no compared pair that straddles two buckets is ever
+        // swapped: odd-even transposition phases over the whole list (even
+        // pairs (2i, 2i + 1) as one 16-byte access, odd pairs (2i + 1,
+        // 2i + 2)) sort every bucket at once, and s phases sort s keys
+        // whichever phase comes first, so the most crowded bucket's size is
+        // the phase count (none when every bucket holds at most one key).
+        // Every lane has work in every phase, unlike a lane-per-bucket
+        // insertion sort, where the warp waits for the most crowded of each
+        // 32 buckets.
         ulonglong2* const pairs = reinterpret_cast<ulonglong2*>(W.sk);
-        for (;;) {
-            bool swapped = false;
-            for (int i = lane; 2 * i + 1 < len; i += 32) {
-                const ulonglong2 q = pairs[i];
-                if (q.x > q.y) {
-                    pairs[i] = make_ulonglong2(q.y, q.x);
-                    swapped = true;
+        for (uint32_t ph = 0; ph < most; ++ph) {
+            if ((ph & 1u) == 0u) {
+                for (int i = lane; 2 * i + 1 < len; i += 32) {
+                    const ulonglong2 q = pairs[i];
+                    if (q.x > q.y) pairs[i] = make_ulonglong2(q.y, q.x);
+                }
+            } else {
+                for (int i = 2 * lane + 1; i + 1 < len; i += 64) {
+                    const unsigned long long x = W.sk[i], y = W.sk[i + 1];
+                    if (x > y) {
+                        W.sk[i] = y;
+                        W.sk[i + 1] = x;
+                    }
                 }
             }
             __syncwarp();
-            for (int i = 2 * lane + 1; i + 1 < len; i += 64) {
-                const unsigned long long x = W.sk[i], y = W.sk[i + 1];
-                if (x > y) {
-                    W.sk[i] = y;
-                    W.sk[i + 1] = x;
-                    swapped = true;
-                }
-            }
-            __syncwarp();
-            if (!__any_sync(0xffffffffu, swapped)) break;
         }
     }
 }
