@@ -767,10 +767,16 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
         for (int i = KPL * 32 + lane; i < len; i += 32)
             atomicAdd(&W.bstart[bucket(keys[start + i])], 1u);
     __syncwarp();
+    uint32_t most = 0u;  // the most crowded bucket's size
     {  // exclusive scan of bstart[0..NB)
         const int per = (NB + 31) / 32, b0 = lane * per;
         uint32_t sum = 0;
-        for (int b = b0; b < b0 + per && b < NB; ++b) sum += W.bstart[b];
+        for (int b = b0; b < b0 + per && b < NB; ++b) {
+            const uint32_t c = W.bstart[b];
+            sum += c;
+            most = max(most, c);
+        }
+        most = __reduce_max_sync(0xffffffffu, most);
         uint32_t inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -797,10 +803,6 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
             W.sk[atomicAdd(&W.bstart[bucket(k)], 1u)] = k;
         }
     __syncwarp();
-    auto bucket_begin = [&](int b) { return b == 0 ? 0u : W.bstart[b - 1]; };
-    uint32_t most = 0u;  // the most crowded bucket's size
-    for (int b = lane; b < NB; b += 32) most = max(most, W.bstart[b] - bucket_begin(b));
-    most = __reduce_max_sync(0xffffffffu, most);
     if (most > uint32_t(kBucketSortLimit)) {
         int P = 1;
         while (P < len) P <<= 1;
