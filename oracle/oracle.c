@@ -8,8 +8,9 @@
  * follows.  Where the paper is silent or ambiguous the reading taken is
  * stated next to the code (and listed in the repository's design notes).
  *
- * Parity status: see oracle.h (the repurposing assignment's exact
- * tie-breaking is "parity unpinned"; everything else is pinned by tests).
+ * Parity status: see oracle.h (every function is pinned by tests; the
+ * repurposing assignment is pinned under stated readings of the choices
+ * Alg. 2 leaves open).
  */
 #include "oracle.h"
 

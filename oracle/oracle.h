@@ -9,10 +9,11 @@
  * Parity status per function (see the pins in tests/test_oracle_*.py):
  *   or_view_map            pinned (periodicity, row-shift identity, offset
  *                          shift, hand-worked values, per-lens balance).
- *   or_repurpose           pinned by invariants only; the exact assignment
- *                          depends on readings of Alg. 2 the paper leaves open
- *                          (iteration order, search order, buffer capacity):
- *                          parity unpinned for the exact tie-breaking.
+ *   or_repurpose           pinned by invariants and by two small panels
+ *                          worked through Alg. 2 by hand under the readings
+ *                          of the choices the paper leaves open (iteration
+ *                          order, search order, buffer capacity); those
+ *                          readings themselves are not fixed by the paper.
  *   or_ray_table           pinned by invariants (R-first order, uniqueness).
  *   or_raycast_rays        pinned (closed-form t and alpha of isotropic
  *                          Gaussians, t maximises the density along the ray,

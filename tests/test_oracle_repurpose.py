@@ -1,10 +1,15 @@
 """Pins of the oracle's subpixel repurposing (Sec. 5, Alg. 2) and ray table.
 
-The exact assignment depends on readings the paper leaves open (iteration
-order, search order, buffer capacity), so the exact tables are parity
-unpinned.  What Alg. 2 and the ray-set construction fix is checked here as
-invariants, plus the rendered-pixel ratio beta against the paper's ablation
-table for P_w = 2 as a sanity band."""
+The exact assignment depends on readings of choices the paper leaves open
+(iteration order, search order, buffer capacity), so the exact tables are
+fixed by those readings, not by the paper itself.  What Alg. 2 and the ray-set
+construction fix is checked here as invariants, plus the rendered-pixel
+ratio beta against the paper's ablation table for P_w = 2 as a sanity band,
+and two small panels worked through Alg. 2 by hand under the stated
+readings (tests/golden/repurpose_hand.txt) pin the implementation of those
+readings."""
+import os
+
 import numpy as np
 import pytest
 
@@ -134,3 +139,34 @@ def test_ray_order_when_views_repeat_within_a_pixel():
     assert np.array_equal(r[..., 1], (src >> 16).astype(np.int64))
     assert np.array_equal(r[..., 2], (src & 0xFFFF).astype(np.int64))
     assert len(np.unique(ray_of[..., 0])) < h * w   # R subpixels do share rays here
+
+
+HAND = os.path.join(os.path.dirname(__file__), "golden", "repurpose_hand.txt")
+
+
+def _hand_panels():
+    panels, cur = [], None
+    for line in open(HAND):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("panel"):
+            w, h, nv, lx, tan, k, pw = line.split()[1:]
+            cur = {"display": W.Display(int(w), int(h), int(nv), float(lx), float(tan), float(k),
+                                        p_w=int(pw)),
+                   "rows": {}}
+            panels.append(cur)
+        else:
+            head, vals = line.split(":")
+            cur["rows"][int(head.split()[1])] = [tuple(int(t) for t in v.split("."))
+                                                 for v in vals.split()]
+    return panels
+
+
+@pytest.mark.parametrize("panel", _hand_panels(), ids=["A", "B"])
+def test_hand_worked_assignment(panel):
+    d = panel["display"]
+    src = oracle.repurpose(d, oracle.view_map(d)).reshape(d.height, 3 * d.width)
+    for x, vals in panel["rows"].items():
+        got = [(int(v) >> 16, int(v) & 0xFFFF) for v in src[x]]
+        assert got == vals, f"row {x}"
