@@ -14,7 +14,8 @@
  *                          of the choices the paper leaves open (iteration
  *                          order, search order, buffer capacity); those
  *                          readings themselves are not fixed by the paper.
- *   or_ray_table           pinned by invariants (R-first order, uniqueness).
+ *   or_ray_table           pinned by invariants (R-first order, uniqueness)
+ *                          and by the two hand-worked panels' ray tables.
  *   or_raycast_rays        pinned (closed-form t and alpha of isotropic
  *                          Gaussians, t maximises the density along the ray,
  *                          heap capacity, SH at the ray direction).

@@ -170,3 +170,37 @@ def test_hand_worked_assignment(panel):
     for x, vals in panel["rows"].items():
         got = [(int(v) >> 16, int(v) & 0xFFFF) for v in src[x]]
         assert got == vals, f"row {x}"
+
+
+RAYS_HAND = os.path.join(os.path.dirname(__file__), "golden", "raytable_hand.txt")
+
+
+def _hand_ray_tables():
+    panels, cur = [], None
+    for line in open(RAYS_HAND):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("panel"):
+            w, h, nv, lx, tan, k, pw = line.split()[1:]
+            cur = {"display": W.Display(int(w), int(h), int(nv), float(lx), float(tan), float(k),
+                                        p_w=int(pw)),
+                   "ray_of": {}, "rays": []}
+            panels.append(cur)
+        elif line.startswith("ray_of"):
+            head, vals = line.split(":")
+            cur["ray_of"][int(head.split()[1])] = [int(v) for v in vals.split()]
+        else:
+            cur["rays"] = [tuple(int(t) for t in v.split(".")) for v in line.split(":")[1].split()]
+    return panels
+
+
+@pytest.mark.parametrize("panel", _hand_ray_tables(), ids=["A", "B"])
+def test_hand_worked_ray_table(panel):
+    d = panel["display"]
+    V = oracle.view_map(d)
+    ray_of, rays = oracle.ray_table(d, V, oracle.repurpose(d, V))
+    ray_of = ray_of.reshape(d.height, 3 * d.width)
+    for x, vals in panel["ray_of"].items():
+        assert ray_of[x].tolist() == vals, f"row {x}"
+    assert [tuple(r) for r in rays.tolist()] == panel["rays"]
