@@ -518,44 +518,6 @@ __device__ __forceinline__ void stream_list(const unsigned long long* sk, int le
     }
 }
 
-// Variant of stream_list with two batches: cp.async fetches batch b+1 while
-// batch b is blended.
-template <bool TRANSPOSED>
-__device__ __forceinline__ void stream_list_db(const unsigned long long* sk, int len, int64_t vbase,
-                                               const float4* __restrict__ rec, float4* buf,
-                                               int* wbuf, Acc& a, bool& done, uint32_t& evals,
-                                               float px, float py, int bx0, int bx1, int by0,
-                                               int by1) {
-    const int nthr = blockDim.x, t = threadIdx.x;
-    const int nbatch = (len + nthr - 1) / nthr;
-    if (nbatch == 0) return;
-    auto issue = [&](int b) {
-        float4* dst = buf + (b & 1) * 3 * nthr;
-        const int i = b * nthr + t;
-        if (i < len) {
-            const int64_t e = vbase + (uint32_t(sk[i]) >> 4);
-            cp_async16(dst + t, rec + 3 * e);
-            cp_async16(dst + nthr + t, rec + 3 * e + 1);
-            cp_async16(dst + 2 * nthr + t, rec + 3 * e + 2);
-        }
-        cp_async_commit();
-    };
-    issue(0);
-    for (int b = 0; b < nbatch; ++b) {
-        if (b + 1 < nbatch) issue(b + 1);
-        else cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        const float4* cur = buf + (b & 1) * 3 * nthr;
-        const int nb = len - b * nthr < nthr ? len - b * nthr : nthr;
-        eval_batch<TRANSPOSED>(a, done, evals, px, py, bx0, bx1, by0, by1, cur, cur + nthr,
-                               cur + 2 * nthr, nb, wbuf);
-        if (__syncthreads_count(done) == nthr) break;
-    }
-    cp_async_wait<0>();
-    __syncthreads();
-}
-
 // Shared memory of a binned block: keys (cap), bucket counters (cap + 2),
 // a record batch (3 x nthr float4), compaction buffers (64 ints per warp).
 struct BinnedSmem {
