@@ -361,6 +361,7 @@ def render_subpixels_lowres(scene: Scene, display, L0: np.ndarray, subpixels: np
     out = {}
     for key, name in (("value", "rgb"), ("lo", "lo"), ("hi", "hi")):
         out[key] = sum(wt * res[name][inv[t], k] for t, (_, _, wt) in enumerate(taps))
+    out["flags"] = np.bitwise_or.reduce(res["flags"][inv], axis=0)
     out["n_rays"] = int(uniq.shape[0])
     return out
 

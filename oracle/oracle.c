@@ -548,9 +548,15 @@ static void or_render_one(const or_splat* sp, int64_t n, int32_t r, int32_t c, d
     for (int k = 0; k < 3; ++k) rgb[k] = lo[k] = hi[k] = base[k];
     int32_t f = 0;
     double alt[3];
-    int64_t lim = stop + 1 < m ? stop + 1 : m;
+    /* A contributor's own alpha decision can change the result only up to
+     * the Gaussian that stops compositing (index stop - 1).  A depth swap can
+     * also bring the first included contributor after that one in front of
+     * it, so the tie check reaches one past that contributor. */
+    int64_t lim = stop;
+    while (lim < m && !L[lim].include) ++lim;
+    lim = lim < m ? lim + 1 : m;
     /* alpha within 1e-6 of 1/255: either decision is an acceptable result */
-    for (int64_t i = 0; i < lim; ++i) {
+    for (int64_t i = 0; i < stop; ++i) {
         if (fabs(L[i].alpha - OR_ALPHA_MIN) < 1e-6) {
             f |= 2;
             L[i].include = !L[i].include;
@@ -581,7 +587,7 @@ static void or_render_one(const or_splat* sp, int64_t n, int32_t r, int32_t c, d
     /* transmittance within 1e-8 of the 1e-4 stop */
     {
         double T = 1.0;
-        for (int64_t i = 0; i < lim; ++i) {
+        for (int64_t i = 0; i < stop; ++i) {
             if (!L[i].include) continue;
             double Tn = T * (1.0 - L[i].alpha);
             if (fabs(Tn - OR_T_STOP) < 1e-8) {

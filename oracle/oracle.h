@@ -25,6 +25,11 @@
  *   or_project_splat /     pinned (isotropic closed form, finite-difference
  *   or_render_rays         Jacobian, 1-3 Gaussian brute force, back-to-front
  *                          identity, SH addition theorem and orthonormality).
+ *   or_render_rays lo/hi/  pinned (hand-built on-axis stacks: alpha inside and
+ *   flags (the envelope)   outside its 1e-6 window, depth near-ties and a
+ *                          chain of them, T inside and outside its 1e-8
+ *                          window, the stop as the end of the examined
+ *                          contributors; flags == 0 gives lo == hi == value).
  */
 #ifndef DIRECTL_ORACLE_H
 #define DIRECTL_ORACLE_H
@@ -125,7 +130,11 @@ int or_raycast_rays(const or_scene* sc, const or_display* p, const double L0[16]
 /* Colour of rays (view, row, col) by front-to-back compositing over every
  * Gaussian.  rgb/lo/hi are n_rays*3; lo/hi bound the results of the
  * alternative decisions at FP32-resolution ties and thresholds (flags bit 0:
- * depth near-tie, bit 1: alpha near 1/255, bit 2: T near 1e-4).  n_contrib
+ * depth near-tie between consecutive included contributors, bit 1: alpha
+ * within 1e-6 of 1/255, bit 2: T within 1e-8 of 1e-4).  Only contributors up
+ * to the one that stops compositing are examined for the alpha and T
+ * windows; the depth check also reaches the first included contributor
+ * after it, which a swap can bring in front of it.  n_contrib
  * (optional) receives the number of composited Gaussians per ray.
  * n_threads <= 0 uses every core. */
 int or_render_rays(const or_scene* sc, const or_display* p, const double L0[16],
