@@ -59,13 +59,14 @@ FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16  # ex2 results an SM produces per clock
 # algorithmic bytes of the compositing stage (see the roofline section)
 KEY_BYTES = 8
-RECORD_BYTES = 36
+RECORD_BYTES = 32   # conic (6 floats) and packed colour (64 bits): the whole stored record
 RAY_COLOUR_BYTES = 12
 HBM_FALLBACK_GBS = 6800.0
 
 
 def compositing_roofline(comp_ms: float, keys: float, n_rays: float, evaluated: float,
-                         blended: float, hbm_gbs: float, hbm_source: str) -> dict:
+                         blended: float, hbm_gbs: float, hbm_source: str,
+                         alu_peaks: dict | None = None) -> dict:
     """Roofline of the compositing stage from its algorithmic work.
 
     Three lower bounds on the stage's time:
@@ -73,16 +74,27 @@ def compositing_roofline(comp_ms: float, keys: float, n_rays: float, evaluated: 
             FLOP_PER_BLEND per composited pair, against 152 SMs x 128 lanes
             x 2 (FMA) x 2070 MHz;
       MUFU: one ex2 per evaluated pair, against 152 SMs x 16 x 2070 MHz;
-      HBM:  per key its 8-byte sort key and the nine floats of its record
-            that the test and the blend need (36 bytes), per ray 12 bytes of
-            colour, against the measured copy bandwidth.
+      HBM:  per key its 8-byte sort key and its 32-byte record (the six
+            conic floats the test and blend need and the packed colour), per
+            ray 12 bytes of colour, against the measured copy bandwidth.
     The roofline is the largest of the three (the binding one); its fraction
-    is that bound's time over the stage's time."""
+    is that bound's time over the stage's time.  alu_peaks (from
+    dl_measure_peaks on the same GPU) replaces the derived FP32 and ex2 peaks
+    by measured ones: the larger of the scalar and packed FP32 FMA rates."""
     comp_s = comp_ms / 1e3 if comp_ms > 0 else float("inf")
     clk = 2070.0
     flops = FLOP_PER_EVAL * evaluated + FLOP_PER_BLEND * blended
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
     mufu_peak = SMS * MUFU_LANES_PER_SM * clk * 1e6
+    alu_source = "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"
+    mufu_source = "derived: 152 SMs x 16 ex2 a clock x 2070 MHz"
+    if alu_peaks:
+        peak_tflops = max(alu_peaks["fp32_tflops"], alu_peaks["fp32x2_tflops"])
+        mufu_peak = alu_peaks["ex2_per_s"]
+        alu_source = ("measured: FP32 FMA microbenchmark on this GPU (dl_measure_peaks; "
+                      f"scalar {alu_peaks['fp32_tflops']:.1f}, packed FP32x2 "
+                      f"{alu_peaks['fp32x2_tflops']:.1f} TFLOP/s)")
+        mufu_source = "measured: ex2.approx microbenchmark on this GPU (dl_measure_peaks)"
     bytes_alg = keys * (KEY_BYTES + RECORD_BYTES) + n_rays * RAY_COLOUR_BYTES
     bounds_ms = {"hbm": 1e3 * bytes_alg / (hbm_gbs * 1e9),
                  "alu": 1e3 * flops / (peak_tflops * 1e12),
@@ -90,7 +102,7 @@ def compositing_roofline(comp_ms: float, keys: float, n_rays: float, evaluated: 
     bound = max(bounds_ms, key=bounds_ms.get)
     alu = {"achieved": flops / comp_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
            "frac": flops / comp_s / 1e12 / peak_tflops,
-           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+           "peak_source": alu_source, "mufu_peak_per_s": mufu_peak, "mufu_source": mufu_source,
            "flop_per_launch": flops,
            "flop_model": f"{FLOP_PER_EVAL} per evaluated (ray, Gaussian) pair + "
                          f"{FLOP_PER_BLEND} per composited pair"}
@@ -106,6 +118,46 @@ def compositing_roofline(comp_ms: float, keys: float, n_rays: float, evaluated: 
             "byte_model": f"{KEY_BYTES} B key + {RECORD_BYTES} B record per key, "
                           f"{RAY_COLOUR_BYTES} B per ray",
             "bounds_ms": bounds_ms, "alu": alu}
+
+
+def stage_roofline(name: str, ms: float, bytes_alg: float, model: str, hbm_gbs: float,
+                   hbm_source: str) -> dict:
+    """HBM roofline of a bandwidth-bound stage: algorithmic bytes over the
+    stage's CUDA-event time against the measured copy bandwidth."""
+    s = ms / 1e3 if ms > 0 else float("inf")
+    return {"kernel": name, "bound": "hbm", "achieved": bytes_alg / s / 1e9, "peak": hbm_gbs,
+            "unit": "GB/s", "frac": bytes_alg / s / 1e9 / hbm_gbs, "peak_source": hbm_source,
+            "bytes_per_launch": bytes_alg, "ms_per_launch": ms, "byte_model": model}
+
+
+def attribute_bytes(spec: W.SceneSpec) -> int:
+    """Bytes of one stored Gaussian: FP32 mean, then log-scale (3), rotation
+    (4), opacity (1) and SH (3 (d+1)^2) in the storage type."""
+    elem = 4 if spec.dtype == "f32" else 2
+    return 12 + elem * (3 + 4 + 1 + 3 * (spec.sh_degree + 1) ** 2)
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), and its ISA."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu model")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return f"{name or 'unknown'} ({platform.machine()})"
 
 
 def measured_hbm_gbs():
@@ -319,22 +371,29 @@ def run_reference(args):
     n_rays = int(rays.shape[0])
     sc = W.make_scene(wl.scene)
     scene = oracle.Scene(W.quantise_storage(sc, wl.scene.dtype))
-    frame_times, last = [], None
+    frame_times, walls, last = [], [], None
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         est = oracle_frame_estimate(wl, 4, 100 + i, n_rays, scene, (V, src))
+        wall = time.perf_counter() - t0
         if i >= args.warmup:
             frame_times.append(est["frame_s"])
+            walls.append(wall)
         last = est
-    ms = 1e3 * statistics.mean(frame_times)
-    fps = 1e3 / ms
+    frame_ms = 1e3 * statistics.mean(frame_times)
+    fps = 1e3 / frame_ms
     cores = int(last["threads"])
+    # a step is one bounded ray sample (its wall time is ms_per_step); the
+    # value is the frame rate extrapolated from the samples
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(walls), "extrapolated_ms_per_frame": frame_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
             "config": {"workload": workload_desc(wl), "global_batch": 1, "parallelism": "none"},
             "subpixels_per_s": fps * 3 * d.width * d.height,
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "cpu": cpu_model(),
                              "sample": ("per step: one ray per view, then 4 rays per view "
                                         f"({last['rays_sampled']} rays, all 45 views projected "
                                         "twice); frame time extrapolated as N_v*T_project + "
@@ -366,6 +425,7 @@ def per_frame(totals: dict, n: int) -> dict:
             "ms_interweave", "ms_total")
     out = {k[3:]: totals[k] / max(n, 1) for k in keys}
     out["keys"] = totals["n_keys"] / max(n, 1)
+    out["visible"] = totals["n_visible"] / max(n, 1)
     out["pairs_evaluated"] = totals["pairs_evaluated"] / max(n, 1)
     out["pairs_blended"] = totals["pairs_blended"] / max(n, 1)
     return out
@@ -453,6 +513,76 @@ def run_graph_batched(device: int, steps: int) -> dict:
         torch.cuda.empty_cache()
 
 
+def run_multislot(device: int, steps: int) -> dict:
+    """Uneven frames in one batch: a 4K/45-view frame of 1M Gaussians (BF16),
+    a 1080p/45-view frame of 200k (FP32) and a 4K/60-view frame of 300k
+    (FP16), rendered together by one launch sequence (one persistent launch
+    per compositing class over all three frames' tile lists) replayed from a
+    captured CUDA graph, against the same three frames through three
+    dl_render_frame calls."""
+    import torch
+
+    from paper_2407_14053_gb300 import Renderer
+    p4k, p1080 = W.WORKLOADS["4k"].display, W.WORKLOADS["1080p"].display
+    specs = [(W.WORKLOADS["4k"].scene, p4k),
+             (W.WORKLOADS["1080p"].scene, p1080),
+             (W.SceneSpec(300_000, 3, "clustered", "f16", seed=5), p4k.replace(num_views=60))]
+    r = Renderer(device)
+    try:
+        S, D, outs = [], [], []
+        for spec, disp in specs:
+            S.append(r.load_gaussians(W.make_scene(spec), spec.dtype))
+            D.append(r.set_display(disp))
+            outs.append(torch.empty((disp.height, disp.width, 3), dtype=torch.float32,
+                                    device=f"cuda:{device}"))
+        poses = W.camera_path(200, 4.0, 10.0)
+        b = r.batch([(S[k], D[k], None, poses[0]) for k in range(3)], margin=1.25)
+        st = torch.cuda.Stream()
+        for k in range(3):
+            b.assign(k, S[k], D[k], outs[k])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            b.capture()
+            for i in range(3):
+                for k in range(3):
+                    b.set_pose(k, poses[(i + 40 * k) % 200])
+                b.launch()
+            b.wait()
+            e0.record()
+            for i in range(steps):
+                for k in range(3):
+                    b.set_pose(k, poses[(7 * i + 40 * k) % 200])
+                b.launch()
+            e1.record()
+            status = b.wait(raise_on_capacity=False)
+        st.synchronize()
+        graph_ms = e0.elapsed_time(e1) / steps
+        torch.cuda.synchronize()
+        for i in range(2):
+            for k in range(3):
+                r.render(S[k], D[k], poses[(i + 40 * k) % 200], "directl", outs[k])
+        torch.cuda.synchronize()
+        e0.record()
+        for i in range(steps):
+            for k in range(3):
+                r.render(S[k], D[k], poses[(7 * i + 40 * k) % 200], "directl", outs[k])
+        e1.record()
+        torch.cuda.synchronize()
+        single_ms = e0.elapsed_time(e1) / steps
+        bytes_, _ = b.info()
+        b.close()
+        return {"frames": ["4k/45 views, 1M Gaussians bf16", "1080p/45 views, 200k f32",
+                           "4k/60 views, 300k f16"],
+                "ms_per_launch": graph_ms, "frames_per_s": 3e3 / graph_ms,
+                "render_frame_ms_for_the_three": single_ms,
+                "speedup_over_render_frame": single_ms / graph_ms, "steps": steps,
+                "status": status, "batch_bytes": bytes_,
+                "note": "three uneven frames per launch, captured graph replayed with new poses"}
+    finally:
+        r.close()
+        torch.cuda.empty_cache()
+
+
 def run_serving(device: int, n_requests: int = 256, n_scenes: int = 8, util: float = 0.7,
                 seed: int = 0) -> dict:
     """Serving mix: Poisson arrivals, scenes of 100k-3M Gaussians
@@ -476,7 +606,9 @@ def run_serving(device: int, n_requests: int = 256, n_scenes: int = 8, util: flo
     try:
         L0 = W.light_field_centre(4.0, 0.0)
         plans = [("s0", "4k60"), ("s0", "4k60"), ("s0", "1080p45"), ("s0", "1080p45")]
-        srv = Server(r, scenes, displays, plans, L0, lanes=2, hbm_budget=150e9, margin=1.3)
+        keep = set(range(1000, 1000 + n_requests, 32))  # a seeded sample re-rendered alone below
+        srv = Server(r, scenes, displays, plans, L0, lanes=2, hbm_budget=150e9, margin=1.3,
+                     keep_outputs=keep)
 
         def mix(n, arrivals, base):
             keys, dkeys = sorted(scenes), sorted(displays)
@@ -484,11 +616,29 @@ def run_serving(device: int, n_requests: int = 256, n_scenes: int = 8, util: flo
                             W.light_field_centre(4.0, float(rng.uniform(-5, 5))), float(a))
                     for i, a in enumerate(arrivals)]
 
-        burst = srv.run(mix(32, np.zeros(32), 0))            # warm-up + service rate
+        # the first burst loads scenes and displays and builds their tables
+        # (its rate varies with which of them it meets first); the service
+        # rate is taken from a second burst of the same mix, all resident
+        cold = srv.run(mix(32, np.zeros(32), 0))
+        burst = srv.run(mix(32, np.zeros(32), 100))
         rate = util * burst["frames_per_s"]
         reqs = mix(n_requests, poisson_arrivals(n_requests, rate, seed + 1), 1000)
         summary = srv.run(reqs)
+        # served frames against the same frames rendered alone
+        same = compared = 0
+        for q in reqs:
+            ks, kd = ("scene", q.scene), ("display", q.display)
+            if q.rid not in keep or q.out is None or ks not in srv.cache.items or \
+                    kd not in srv.cache.items:
+                continue  # (a scene evicted since cannot be re-rendered here)
+            alone = torch.empty_like(q.out)
+            r.render(srv.cache.handle(ks), srv.cache.handle(kd), q.L0, "directl", alone)
+            torch.cuda.synchronize()
+            compared += 1
+            same += int(torch.equal(alone, q.out))
+        summary["alone_vs_mix"] = {"compared": compared, "bit_equal": same}
         summary.update({"arrival_rate_per_s": rate, "burst_frames_per_s": burst["frames_per_s"],
+                        "cold_burst_frames_per_s": cold["frames_per_s"],
                         "target_utilisation": util, "hbm_budget_gb": 150.0,
                         "hbm_reserved_gb": srv.cache.reserved / 1e9,
                         "hbm_used_gb": srv.cache.used / 1e9, "scene_loads": srv.cache.loads,
@@ -514,6 +664,8 @@ def main():
     rank, world, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    from paper_2407_14053_gb300 import _binding as B
+    alu_peaks = B.dl_measure_peaks(local)  # FP32 and ex2 rates for the roofline
     wl = W.WORKLOADS[args.workload]
     d = wl.display
     scene = W.make_scene(wl.scene)
@@ -565,8 +717,17 @@ def main():
         tot_s, nf_s = r.stage_totals()
         ms_s = reduce_max(ms_s, world, dev)
         fps_s = reduce_sum(k_std, world, dev) / (ms_s / 1e3)
+        std_stages = per_frame(tot_s, nf_s)
+        # pair counts of two of the same poses (counting kernels, untimed)
+        r.enable_stage_timing(True, count_pairs=True)
+        for i in range(2):
+            r.render(sid, did, poses[(7 * i) % 200], "standard", out)
+        cnt_s = per_frame(*r.stage_totals())
+        std_stages["pairs_evaluated"] = cnt_s["pairs_evaluated"]
+        std_stages["pairs_blended"] = cnt_s["pairs_blended"]
+        r.enable_stage_timing(True, count_pairs=False)
         std = {"frames_per_s": fps_s, "subpixels_per_s": fps_s * subpix, "ms_per_frame": ms_s / k_std,
-               "steps": k_std, "stages_ms": per_frame(tot_s, nf_s),
+               "steps": k_std, "stages_ms": std_stages,
                "speedup_directl_over_standard": fps / fps_s}
         # the paper's LR / MR configurations of the standard paradigm (views
         # rendered smaller, upsampled while interweaving); 4K panel sizes
@@ -660,15 +821,42 @@ def main():
     roofline = {"kernel": kname + " (512- and 1024-key classes: the compositing stage)",
                 **compositing_roofline(dl_stages["composite"], dl_stages["keys"], n_rays,
                                        dl_stages["pairs_evaluated"], dl_stages["pairs_blended"],
-                                       hbm_gbs, hbm_source),
+                                       hbm_gbs, hbm_source, alu_peaks),
                 "traffic": load_traffic(kname, args.workload, src_file)}
+
+    # ---- rooflines of the other stages (HBM-bound; per frame) ----
+    ne = d.num_views * wl.scene.n
+    stages_roof = {
+        "project": stage_roofline(
+            "project_kernel (with the camera upload and counter resets before it)",
+            dl_stages["project"],
+            wl.scene.n * attribute_bytes(wl.scene) + 16 * ne + RECORD_BYTES * dl_stages["visible"],
+            f"{attribute_bytes(wl.scene)} B of attributes read once per Gaussian, 16 B tile "
+            f"metadata written per (view, Gaussian), {RECORD_BYTES} B record written per "
+            "visible (view, Gaussian)", hbm_gbs, hbm_source),
+        "emit": stage_roofline(
+            "emit_binned_kernel", dl_stages["emit"], 16 * ne + 8 * dl_stages["keys"],
+            "16 B tile metadata read per (view, Gaussian), 8 B key written per key",
+            hbm_gbs, hbm_source),
+    }
+    if std is not None:
+        ss = std["stages_ms"]
+        pix = d.num_views * d.width * d.height
+        stages_roof["standard_composite"] = {
+            "kernel": "composite_full_binned_kernel (every pixel of every view into M_m)",
+            **compositing_roofline(ss["composite"], ss["keys"], pix, ss["pairs_evaluated"],
+                                   ss["pairs_blended"], hbm_gbs, hbm_source, alu_peaks)}
+        stages_roof["standard_interweave"] = stage_roofline(
+            "interweave_kernel", ss["interweave"], subpix * (2 + 4 + 4),
+            "2 B view index read, 4 B gathered from M_m and 4 B written per subpixel",
+            hbm_gbs, hbm_source)
 
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est = oracle_frame_estimate(wl, 4, 7, int(n_rays))
         cpu = {"value": 1.0 / est["frame_s"], "unit": "frames/s", "cores": int(est["threads"]),
-               "kind": "oracle",
+               "kind": "oracle", "cpu": cpu_model(),
                "sample": (f"one ray per view then 4 rays per view ({est['rays_sampled']} rays; "
                           f"every view's {wl.scene.n} Gaussians projected in FP64), frame time "
                           f"extrapolated as N_v*T_project + N_rays*T_ray, N_rays={n_rays}; "
@@ -683,6 +871,7 @@ def main():
     graph = None
     if not args.no_graph and world == 1:
         graph = run_graph_batched(local, max(3, args.steps // 4))
+        graph["uneven_multislot"] = run_multislot(local, max(3, args.steps // 2))
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(local)
@@ -698,6 +887,8 @@ def main():
                        "l2": "no flush: each frame streams > 2 GB (inputs larger than L2)",
                        "storage": wl.scene.dtype, "beta": beta, "n_rays": int(n_rays)},
             "subpixels_per_s": fps * subpix,
+            "standard_frames_per_s": std["frames_per_s"] if std else None,
+            "speedup_vs_standard": fps / std["frames_per_s"] if std else None,
             "stages_ms": dl_stages,
             "offline_tables_s": offline_s,
             "standard": std,
@@ -706,6 +897,8 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "roofline": roofline,
+            "roofline_stages": stages_roof,
+            "alu_peaks_measured": alu_peaks,
             "cpu_baseline": cpu,
             "graph_batched": graph,
             "serving": serving,

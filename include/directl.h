@@ -182,7 +182,18 @@ dl_status dl_get_ray_table(dl_ctx* ctx, int32_t display_id, uint32_t* ray_of, in
  * DL_STANDARD_SR (see the mode enum).
  * out: h*w*3 floats, device memory if out_on_device else host memory (the
  * call then copies the frame back and returns once it is there).
- * Synchronises `stream` once per frame to size the tile-key buffers.
+ * Host synchronisation: the first DL_DIRECTL / DL_REQUIRED_ONLY frame of a
+ * (scene, display, mode, tile shape) reads its key totals back to size the
+ * tile-key buffer and the long-list capacity (one synchronisation of
+ * `stream` in mid-frame); later frames of it are enqueued without any host
+ * synchronisation, their launches sized from device counters.  Such a frame
+ * that needs more tile keys or a longer list than those capacities is
+ * dropped on the device: its output is left untouched and its status word
+ * (dl_frame_stats.status, read by dl_last_frame_stats) is set; with a host
+ * `out` the call sees this and renders the frame again, sized.  The next
+ * frame after a dropped one, or after one that used more than 85 % of a
+ * capacity, is sized again.  DL_STANDARD, DL_STANDARD_SR and frames on the
+ * radix-sort fallback synchronise once per frame.
  */
 dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                           const double L0_c2w[16], int32_t mode, float* out,
@@ -197,10 +208,11 @@ dl_status dl_render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
  * `copy_stream` has reached that point (cudaStreamSynchronize or an event);
  * the caller keeps `out` alive and untouched until then.  The library writes
  * the frame into one of two device frames used in turn; `stream` waits for
- * the copy that read the same device frame two calls earlier.  Like
- * dl_render_frame it synchronises `stream` once per frame to size the
- * tile-key buffers.  DL_ERR_INVALID_ARG when `copy_stream` equals `stream`
- * or a pointer is NULL.
+ * the copy that read the same device frame two calls earlier.  Host
+ * synchronisation and dropped frames as for dl_render_frame with a device
+ * `out` (a dropped frame's copy delivers the device frame's earlier
+ * contents).  DL_ERR_INVALID_ARG when `copy_stream` equals `stream` or a
+ * pointer is NULL.
  */
 dl_status dl_render_frame_async_host(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                                      const double L0_c2w[16], int32_t mode, float* out,
@@ -308,8 +320,16 @@ typedef struct {
     int64_t lists_small;     /* tile lists composited by the small class     */
     int64_t lists_large;     /* tile lists composited by the large class     */
     int64_t max_list;        /* longest tile list (keys)                     */
+    int64_t n_visible;       /* (view, Gaussian) records the projection wrote
+                                (in front of the near plane, alpha can reach
+                                1/255 inside the view)                       */
     float ms_project, ms_scan, ms_sync, ms_emit, ms_sort, ms_ranges, ms_composite,
         ms_interweave, ms_total; /* stage durations (CUDA events)        */
+    int32_t status;          /* last frame: 0 when complete, else the frame was
+                                dropped (output left untouched): bit 0 its tile
+                                keys exceeded the key capacity, bit 1 a tile
+                                list exceeded the long-list capacity.  In
+                                dl_stage_totals: the number of dropped frames */
 } dl_frame_stats;
 
 /* While enabled, every dl_render_frame records CUDA events around its
@@ -318,7 +338,8 @@ typedef struct {
  * then run their counting variant), enable = 2 records the events only,
  * enable = 0 turns both off (the default). */
 dl_status dl_enable_stage_timing(dl_ctx* ctx, int32_t enable);
-/* Counters of the last frame (stage times are 0: see dl_stage_totals). */
+/* Counters of the last frame (stage times are 0: see dl_stage_totals);
+ * waits for the last frame when its counters are still on the device. */
 dl_status dl_last_frame_stats(dl_ctx* ctx, dl_frame_stats* out);
 /* Sums of every field over the frames rendered with stage timing on since
  * the previous call (waits for those frames to finish), and their number.
@@ -399,6 +420,15 @@ dl_status dl_batch_info(dl_batch* b, size_t* bytes, int32_t* long_list_cap);
 dl_status dl_autotune_tile(dl_ctx* ctx, int32_t scene_id, int32_t display_id,
                            const double L0_c2w[16], const int32_t* candidates, int32_t n_candidates,
                            int32_t reps, void* stream, int32_t* best, float* ms);
+
+/* Arithmetic peaks of `device` measured by microbenchmarks (no counterpart
+ * in the paper; the benchmark's compositing roofline divides by them): FP32
+ * fused multiply-adds as scalar and as packed FP32x2 instructions (TFLOP/s,
+ * 2 FLOP per FMA) and ex2.approx results per second, each the best of three
+ * timed launches that fill every SM.  Synchronous; allocates 1 KB of device
+ * memory and one stream for the call. */
+dl_status dl_measure_peaks(int32_t device, double* fp32_tflops, double* fp32x2_tflops,
+                           double* ex2_per_s);
 
 #ifdef __cplusplus
 }

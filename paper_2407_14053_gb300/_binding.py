@@ -50,9 +50,10 @@ class dl_frame_stats(ctypes.Structure):
     _fields_ = [("n_keys", c_int64), ("n_rays", c_int64), ("pairs_evaluated", c_int64),
                 ("pairs_blended", c_int64), ("tile_w", c_int32), ("tile_h", c_int32),
                 ("sort_bits", c_int32), ("n_launches", c_int32), ("lists_small", c_int64),
-                ("lists_large", c_int64), ("max_list", c_int64)] + [
+                ("lists_large", c_int64), ("max_list", c_int64), ("n_visible", c_int64)] + [
         (f, ctypes.c_float) for f in ("ms_project", "ms_scan", "ms_sync", "ms_emit", "ms_sort",
-                                      "ms_ranges", "ms_composite", "ms_interweave", "ms_total")]
+                                      "ms_ranges", "ms_composite", "ms_interweave", "ms_total")] + [
+        ("status", c_int32)]
 
 
 class dl_slot_plan(ctypes.Structure):
@@ -99,6 +100,7 @@ SIGNATURES = {
     "dl_batch_info": (c_int32, [c_void_p, P(ctypes.c_size_t), P(c_int32)]),
     "dl_autotune_tile": (c_int32, [c_void_p, c_int32, c_int32, P(c_double), P(c_int32), c_int32,
                                    c_int32, c_void_p, P(c_int32), P(ctypes.c_float)]),
+    "dl_measure_peaks": (c_int32, [c_int32, P(c_double), P(c_double), P(c_double)]),
 }
 
 _lock = threading.Lock()
@@ -347,3 +349,11 @@ def dl_autotune_tile(ctx, scene_id: int, display_id: int, L0_c2w, candidates, re
            lib().dl_autotune_tile(ctx, int(scene_id), int(display_id), L0, cand, len(candidates),
                                   int(reps), c_void_p(stream), best, ms))
     return (best[0], best[1]), list(ms)
+
+
+def dl_measure_peaks(device: int = 0) -> dict:
+    """Measured FP32 (scalar and packed FP32x2) TFLOP/s and ex2 results/s."""
+    a, b, c = c_double(), c_double(), c_double()
+    _check("dl_measure_peaks", None,
+           lib().dl_measure_peaks(int(device), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"fp32_tflops": a.value, "fp32x2_tflops": b.value, "ex2_per_s": c.value}

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdirectl.so")
 SOURCES = ["api.cu", "batch.cu", "display.cu", "project.cu", "sort.cu", "composite.cu", "scene.cu",
-           "raycast.cu"]
+           "raycast.cu", "peaks.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

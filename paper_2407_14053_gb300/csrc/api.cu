@@ -344,6 +344,63 @@ dl_status build_raycast(dl_ctx* ctx, Scene& S, cudaStream_t s) {
     return DL_OK;
 }
 
+// The counter block of a frame run on device counters (copied from the
+// workspace's 256-byte block: keys and visible records as u64 at bytes 0 and
+// 8, the list-class words {warp items, block items, longest list, -, 1024-key
+// items, cursors, status} from byte 128): fills the frame's statistics and
+// resets its signature's sizing when the frame was dropped or used more than
+// 85 % of a capacity.
+static void apply_readback(dl_ctx* ctx, Readback& r) {
+    Workspace& W = ctx->ws;
+    const unsigned long long* h = r.h;
+    const uint32_t* m = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(h) + 128);
+    const int64_t nkeys = int64_t(h[0]), vis = int64_t(h[1]);
+    const int64_t lists_small = int64_t(m[0]) + int64_t(m[4]), lists_large = m[1], longest = m[2];
+    const int32_t status = int32_t(m[7]);
+    if (r.hint && (status != 0 || nkeys * 100 > r.hint->key_cap * 85 ||
+                   longest * 100 > int64_t(r.hint->block_cap) * 85))
+        r.hint->sized = false;
+    if (status != 0) ++W.dropped;
+    for (PendingFrame& f : W.pending)
+        if (f.frame == r.frame) {
+            f.n_keys = nkeys;
+            f.n_visible = vis;
+            f.lists_small = lists_small;
+            f.lists_large = lists_large;
+            f.max_list = longest;
+            f.status = status;
+        }
+    if (W.last_async == r.frame) {
+        dl_frame_stats& fs = ctx->stats;
+        fs.n_keys = nkeys;
+        fs.n_visible = vis;
+        fs.lists_small = lists_small;
+        fs.lists_large = lists_large;
+        fs.max_list = longest;
+        fs.status = status;
+        W.last_async = -1;
+    }
+    r.busy = false;
+}
+
+dl_status harvest_readbacks(dl_ctx* ctx, bool wait) {
+    for (Readback& r : ctx->ws.rb) {
+        if (!r.busy) continue;
+        if (wait) {
+            DL_CK(cudaEventSynchronize(r.done), "wait for frame counters");
+        } else {
+            const cudaError_t e = cudaEventQuery(r.done);
+            if (e == cudaErrorNotReady) {
+                cudaGetLastError();
+                continue;
+            }
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "frame counters");
+        }
+        apply_readback(ctx, r);
+    }
+    return DL_OK;
+}
+
 // Where a frame's last kernel writes it, by output kind: the caller's device
 // buffer; the workspace frame, copied to the host on `s` (the call waits for
 // it); or one of two device frames used in turn, copied to the host on the
@@ -444,6 +501,7 @@ dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[
     if (st) return st;
     dl_frame_stats& fs = ctx->stats;
     fs = dl_frame_stats{};
+    W.last_async = -1;
     fs.n_rays = R.n_rays;
     fs.n_launches = int32_t((D.q.nv + kCamBatch - 1) / kCamBatch) + 2;
     if (E) {
@@ -498,6 +556,14 @@ dl_status dl_create(dl_ctx** out, int32_t device) {
         cudaGetLastError();
         delete c;
         return DL_ERR_OOM;
+    }
+    for (dl::Readback& r : c->ws.rb) {
+        if (cudaMallocHost(&r.h, 256) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return DL_ERR_OOM;
+        }
     }
     *out = c;
     return DL_OK;
@@ -786,6 +852,12 @@ dl_status dl_enable_stage_timing(dl_ctx* ctx, int32_t enable) {
 
 dl_status dl_last_frame_stats(dl_ctx* ctx, dl_frame_stats* out) {
     if (!ctx || !out) return DL_ERR_INVALID_ARG;
+    if (ctx->ws.last_async >= 0) {
+        dl_status st = check_ctx(ctx);
+        if (st) return st;
+        st = harvest_readbacks(ctx, true);
+        if (st) return st;
+    }
     *out = ctx->stats;
     return DL_OK;
 }
@@ -794,6 +866,8 @@ dl_status dl_stage_totals(dl_ctx* ctx, dl_frame_stats* sum, int32_t* n_frames) {
     dl_status st = check_ctx(ctx);
     if (st) return st;
     if (!sum || !n_frames) return fail(ctx, DL_ERR_INVALID_ARG, "null argument");
+    st = harvest_readbacks(ctx, true);
+    if (st) return st;
     dl_frame_stats t{};
     t.tile_w = ctx->stats.tile_w;
     t.tile_h = ctx->stats.tile_h;
@@ -812,11 +886,13 @@ dl_status dl_stage_totals(dl_ctx* ctx, dl_frame_stats* sum, int32_t* n_frames) {
         t.ms_interweave += elapsed(e[7], e[8]);
         t.ms_total += elapsed(e[0], e[8]);
         t.n_keys += f.n_keys;
+        t.n_visible += f.n_visible;
         t.n_rays += f.n_rays;
         t.n_launches += f.launches;
         t.lists_small += f.lists_small;
         t.lists_large += f.lists_large;
         t.max_list = std::max(t.max_list, f.max_list);
+        t.status += f.status != 0 ? 1 : 0;
         W.ev_free.push_back(f.ev);
     }
     *n_frames = int32_t(W.pending.size());
@@ -844,7 +920,7 @@ dl_status dl_query_footprint(dl_ctx* ctx, int32_t scene_id, int32_t display_id, 
     const Scene& S = *si->second;
     const Display& D = *di->second;
     const size_t ne = size_t(D.q.nv) * size_t(S.n);
-    size_t b = ne * (48 + 16 + 8) + scan_tmp_bytes(int64_t(ne));  // records, metadata, counts, offsets
+    size_t b = ne * (16 * kRecordFloat4 + 16 + 8) + scan_tmp_bytes(int64_t(ne));  // records, metadata, counts, offsets
     // tile keys: about two tiles per (view, Gaussian) at the default shapes
     const size_t keys = 2 * ne;
     b += 2 * keys * 12 + radix_tmp_bytes(int64_t(keys));
@@ -887,6 +963,11 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     Scene& S = *si->second;
     Display& D = *di->second;
     Workspace& W = ctx->ws;
+    // counters of earlier frames that have arrived update their signatures'
+    // capacities before this frame is sized
+    st = harvest_readbacks(ctx, false);
+    if (st) return st;
+    const int64_t frame = W.frame_no++;
     const bool timing = ctx->timing;
     StageEvents* E = nullptr;
     if (timing) {
@@ -898,7 +979,8 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
         }
         E = W.ev_free.back();
         W.ev_free.pop_back();
-        W.pending.push_back(PendingFrame{E, 0, 0, 0, 0, 0, 0});
+        W.pending.push_back(PendingFrame{E, 0, 0, 0, 0, 0, 0, 0});
+        W.pending.back().frame = frame;
     }
     auto mark = [&](int i) -> cudaError_t {
         return timing ? cudaEventRecord(E->e[i], s) : cudaSuccess;
@@ -951,7 +1033,7 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     if (ne >= (int64_t(1) << 31)) return fail(ctx, DL_ERR_CAPACITY, "views x Gaussians >= 2^31");
     const int64_t ngroups = int64_t(nv) * ntiles;
     if (ngroups >= (int64_t(1) << 31) - 1) return fail(ctx, DL_ERR_CAPACITY, "too many tiles");
-    DL_CK(W.rec.reserve(48 * size_t(ne)), "alloc records");
+    DL_CK(W.rec.reserve(16 * kRecordFloat4 * size_t(ne)), "alloc records");
     DL_CK(W.meta.reserve(16 * size_t(ne)), "alloc tile metadata");
     DL_CK(W.gcount.reserve(4 * size_t(ngroups + 1)), "alloc group counts");
     DL_CK(W.gstart.reserve(4 * size_t(ngroups + 1)), "alloc group starts");
@@ -963,7 +1045,8 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     DL_CK(cudaMemsetAsync(W.small.p, 0, 256, s), "memset");
     DL_CK(cudaMemsetAsync(W.gcount.p, 0, 4 * size_t(ngroups + 1), s), "memset");
     const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
-    ProjectOut po{W.rec.as<float4>(), W.meta.as<uint4>(), d_total64, W.gcount.as<uint32_t>()};
+    ProjectOut po{W.rec.as<float4>(), W.meta.as<uint4>(), d_total64, W.gcount.as<uint32_t>(),
+                  d_total64 + 1};
     DL_CK(launch_project(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, s), "project");
     DL_CK(mark(1), "event");
     // group starts (one extra entry: gstart[ngroups] = number of keys) and the
@@ -981,10 +1064,22 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     // DirectL: lists of up to warp_cap keys become warp items, longer ones go
     // to the block kernel; standard: small / large block classes.
     const bool warp_path = mode != DL_STANDARD && ctx->warp_cap > 0;
+    // Sizing: the totals are read back (one host synchronisation) until a
+    // frame of this signature has been sized; later frames run on the
+    // signature's capacities and device counters, and are dropped on the
+    // device (status word, output untouched) when they exceed them.
+    FrameHint& hint = ctx->hints[FrameSig{scene_id, display_id, mode, tw, th, rw, rh}];
+    const bool on_device = warp_path && hint.sized && ctx->sort_mode != DL_SORT_RADIX;
+    uint32_t* d_status = d_meta + 7;
+    const uint32_t* d_nkeys = W.gstart.as<uint32_t>() + ngroups;
+    // the key buffer only grows, so its capacity covers every earlier sizing
+    const uint32_t key_cap =
+        on_device ? uint32_t(std::min<size_t>(W.keys[0].bytes / 8, size_t((1u << 31) - 2))) : 0u;
     if (warp_path) {
         DL_CK(launch_partition_warp(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(ctx->warp_cap),
                                     ctx->warp_cap < 1024 ? 1024u : 0u, items, large_list, d_meta,
-                                    nullptr, 0u, nullptr, s),
+                                    on_device ? d_nkeys : nullptr, key_cap,
+                                    on_device ? d_status : nullptr, s),
               "partition");
     } else {
         DL_CK(launch_partition(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(kSmallCap), small_list,
@@ -992,27 +1087,53 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
               "partition");
     }
     DL_CK(mark(2), "event");
-    DL_CK(cudaMemcpyAsync(W.h_total, W.small.p, 256, cudaMemcpyDeviceToHost, s), "copy totals");
-    DL_CK(cudaStreamSynchronize(s), "sync");
-    const unsigned long long nkeys = W.h_total[0];
-    const uint32_t* h_meta = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(W.h_total) + 128);
-    const int64_t n_small = h_meta[0], n_large = h_meta[1];
-    const int64_t n_mid = warp_path ? int64_t(h_meta[4]) : 0;  // 1024-key warp class
-    const int64_t max_len = h_meta[2];
-    if (nkeys >= (1ull << 31) - 1)
-        return fail(ctx, DL_ERR_CAPACITY, "frame needs %llu tile keys (limit 2^31-1)", nkeys);
-    const int64_t nk = int64_t(nkeys);
+    int64_t nk = 0, n_visible = 0, n_small = 0, n_large = 0, n_mid = 0, max_len = 0;
     int cap_large = warp_path ? 2048 : 1;
-    while (cap_large < max_len) cap_large <<= 1;
-    const int binned_threads = mode == DL_STANDARD ? tw * th : kBinnedThreads;
-    const size_t class_smem = warp_path ? block_smem_bytes(cap_large)
-                                        : binned_smem_bytes(std::max(cap_large, kSmallCap),
-                                                            binned_threads);
-    bool binned = ctx->sort_mode != DL_SORT_RADIX && max_len <= kLargeCap &&
-                  class_smem <= max_smem_optin(ctx->device);
-    if (ctx->sort_mode == DL_SORT_BINNED && !binned)
-        return fail(ctx, DL_ERR_CAPACITY, "a tile list holds %lld keys (binned limit %d)",
-                    (long long)max_len, kLargeCap);
+    bool binned = true;
+    if (on_device) {
+        // upper bounds: the persistent kernels read the item counts on the device
+        n_small = n_mid = n_large = n_work;
+        cap_large = hint.block_cap;
+        nk = int64_t(key_cap);
+    } else {
+        DL_CK(cudaMemcpyAsync(W.h_total, W.small.p, 256, cudaMemcpyDeviceToHost, s), "copy totals");
+        DL_CK(cudaStreamSynchronize(s), "sync");
+        const unsigned long long nkeys = W.h_total[0];
+        n_visible = int64_t(W.h_total[1]);
+        const uint32_t* h_meta =
+            reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(W.h_total) + 128);
+        n_small = h_meta[0];
+        n_large = h_meta[1];
+        n_mid = warp_path ? int64_t(h_meta[4]) : 0;  // 1024-key warp class
+        max_len = h_meta[2];
+        if (nkeys >= (1ull << 31) - 1)
+            return fail(ctx, DL_ERR_CAPACITY, "frame needs %llu tile keys (limit 2^31-1)", nkeys);
+        nk = int64_t(nkeys);
+        while (cap_large < max_len) cap_large <<= 1;
+        const int binned_threads = mode == DL_STANDARD ? tw * th : kBinnedThreads;
+        const size_t class_smem = warp_path ? block_smem_bytes(cap_large)
+                                            : binned_smem_bytes(std::max(cap_large, kSmallCap),
+                                                                binned_threads);
+        binned = ctx->sort_mode != DL_SORT_RADIX && max_len <= kLargeCap &&
+                 class_smem <= max_smem_optin(ctx->device);
+        if (ctx->sort_mode == DL_SORT_BINNED && !binned)
+            return fail(ctx, DL_ERR_CAPACITY, "a tile list holds %lld keys (binned limit %d)",
+                        (long long)max_len, kLargeCap);
+        // capacities for the signature's later frames: a quarter more keys
+        // (and 65,536) than this frame, lists up to 1.25 times its longest
+        hint.sized = false;
+        if (warp_path && binned) {
+            const int64_t want = nk + nk / 4 + 65536;
+            int bc = 2048;
+            while (bc < kLargeCap && bc < max_len + max_len / 4) bc <<= 1;
+            if (want < (int64_t(1) << 31) - 2 && block_smem_bytes(bc) <= max_smem_optin(ctx->device)) {
+                DL_CK(W.keys[0].reserve(8 * size_t(want)), "alloc keys");
+                hint.sized = true;
+                hint.key_cap = want;
+                hint.block_cap = bc;
+            }
+        }
+    }
     unsigned long long* pairs =
         timing && ctx->count_pairs ? W.pairs.as<unsigned long long>() : nullptr;
 
@@ -1026,6 +1147,7 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     cp.tile_h = th;
     cp.ntx = pp.ntx;
     cp.ntiles = int32_t(ntiles);
+    cp.meta = W.meta.as<uint4>();
     const size_t out_bytes = 12 * size_t(w) * size_t(h);
     float* dst = nullptr;
     st = out_target(ctx, out, kind, out_bytes, s, &dst);
@@ -1049,7 +1171,8 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
         DL_CK(mark(3), "event");
         DL_CK(launch_emit_binned(pp, nv, W.meta.as<uint4>(),
                                  W.gstart.as<uint32_t>(), W.gfill.as<uint32_t>(),
-                                 W.keys[0].as<unsigned long long>(), nullptr, 0u, nullptr, s),
+                                 W.keys[0].as<unsigned long long>(), on_device ? d_nkeys : nullptr,
+                                 key_cap, on_device ? d_status : nullptr, s),
               "emit binned");
         DL_CK(mark(4), "event");
         DL_CK(mark(5), "event");
@@ -1160,28 +1283,51 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     } else if (mode == DL_STANDARD) {
         DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), Mm, dst, s), "interweave");
     } else {
-        DL_CK(launch_reorder(R->ray_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst, nullptr, s),
+        // a dropped frame (status set) leaves the output untouched
+        DL_CK(launch_reorder(R->ray_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst,
+                             on_device ? d_status : nullptr, s),
               "reorder");
+    }
+    Readback* rbk = nullptr;
+    if (on_device) {  // the frame's counter block, read when it has arrived
+        rbk = &W.rb[W.rb_next];
+        if (rbk->busy) {
+            DL_CK(cudaEventSynchronize(rbk->done), "wait for frame counters");
+            apply_readback(ctx, *rbk);
+        }
+        DL_CK(cudaMemcpyAsync(rbk->h, W.small.p, 256, cudaMemcpyDeviceToHost, s), "copy counters");
+        DL_CK(cudaEventRecord(rbk->done, s), "event");
+        rbk->busy = true;
+        rbk->frame = frame;
+        rbk->hint = &hint;
+        W.rb_next = (W.rb_next + 1) % kReadbacks;
     }
     launches += 1;
     DL_CK(mark(8), "event");
     st = out_finish(ctx, out, kind, dst, out_bytes, s, cs);
     if (st) return st;
 
+    // statistics: the counts of a frame run on device counters arrive with
+    // its counter block (apply_readback)
     dl_frame_stats& fs = ctx->stats;
     fs = dl_frame_stats{};
-    fs.n_keys = nk;
     fs.n_rays = mode == DL_STANDARD ? int64_t(nv) * rw * rh : R->n_rays;
     fs.tile_w = tw;
     fs.tile_h = th;
     fs.sort_bits = sort_bits;
     fs.n_launches = launches;
-    fs.lists_small = n_small + n_mid;
-    fs.lists_large = n_large;
-    fs.max_list = max_len;
+    if (!on_device) {
+        fs.n_keys = nk;
+        fs.n_visible = n_visible;
+        fs.lists_small = n_small + n_mid;
+        fs.lists_large = n_large;
+        fs.max_list = max_len;
+    }
+    W.last_async = on_device ? frame : -1;
     if (timing) {
         PendingFrame& pf = W.pending.back();
         pf.n_keys = fs.n_keys;
+        pf.n_visible = fs.n_visible;
         pf.n_rays = fs.n_rays;
         pf.launches = fs.n_launches;
         pf.lists_small = fs.lists_small;
@@ -1189,7 +1335,16 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
         pf.max_list = fs.max_list;
     }
     W.last_bytes = W.footprint();
-    if (kind == kOutHost) DL_CK(cudaStreamSynchronize(s), "sync");
+    if (kind == kOutHost) {
+        DL_CK(cudaStreamSynchronize(s), "sync");
+        if (rbk && rbk->busy && rbk->frame == frame) {
+            apply_readback(ctx, *rbk);
+            // a dropped frame is rendered again, sized (its signature's
+            // capacities were reset by apply_readback)
+            if (fs.status != 0)
+                return render_frame(ctx, scene_id, display_id, L0_c2w, mode, out, kind, s, cs);
+        }
+    }
     return DL_OK;
 }
 

@@ -132,6 +132,7 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
         fd.cp.tile_h = z.th;
         fd.cp.ntx = z.pp.ntx;
         fd.cp.ntiles = z.pp.ntx * z.pp.nty;
+        fd.cp.meta = b->at<uint4>(z.o_meta);
         fd.grouped = z.G->grouped.as<int2>();
         fd.keys = b->at<unsigned long long>(z.o_keys);
         fd.rec = b->at<float4>(z.o_rec);
@@ -263,6 +264,8 @@ dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plan
             st = cuda_fail(ctx, cudaGetLastError(), "sizing frame");
             break;
         }
+        st = harvest_readbacks(ctx, true);  // the frame's counts, if read back on the device path
+        if (st) break;
         TileGroups* G = nullptr;
         st = get_groups(ctx, *D, D->rep, tw, th, s, &G);
         if (st) break;
@@ -293,7 +296,7 @@ dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plan
         return o;
     };
     for (Slot& z : b->slots) {
-        z.o_rec = take(48 * size_t(z.ne_cap));
+        z.o_rec = take(16 * kRecordFloat4 * size_t(z.ne_cap));
         z.o_meta = take(16 * size_t(z.ne_cap));
         z.zero_bytes = align_up(8 * size_t(z.ng_cap) + 4, 16) + 4 * kMetaWords;
         z.o_zero = take(z.zero_bytes);

@@ -65,7 +65,11 @@ __device__ __forceinline__ float log2_alpha(float px, float py, float u, float v
 // then on alpha itself); stop before T (1 - alpha) = T - alpha T would drop
 // below 1e-4.  After the log2 test the steps are selects, not branches: a
 // skipped record adds 0 alpha T = 0 to the colour and leaves T (>= 1e-4) as
-// it is.  COUNT keeps the composited-pair statistic.
+// it is.  COUNT keeps the composited-pair statistic.  The colour is
+// (q1.z, q1.w, b): kernels that load a batch thread by thread decode the
+// packed colour once per record when they store it in shared memory (the
+// standard paradigm blends tens of times per record); blend_rec below takes
+// a record as stored.
 template <bool CHECK_L2 = true, bool COUNT = true>
 __device__ __forceinline__ bool blend(Acc& a, float px, float py, const float4& q0,
                                       const float4& q1, float b) {
@@ -83,6 +87,26 @@ __device__ __forceinline__ bool blend(Acc& a, float px, float py, const float4& 
     a.T = go ? Tn : a.T;
     if (COUNT && go && alpha > 0.f) ++a.blended;
     return go;
+}
+
+// blend() on a record as the projection stored it (packed colour).
+template <bool CHECK_L2 = true, bool COUNT = true>
+__device__ __forceinline__ bool blend_rec(Acc& a, float px, float py, const float4& q0,
+                                          const float4& q1) {
+    float r, g, b;
+    unpack_rgb(q1.z, q1.w, r, g, b);
+    return blend<CHECK_L2, COUNT>(a, px, py, q0, make_float4(q1.x, q1.y, r, g), b);
+}
+
+// A record and its pixel box in the shared-memory layout of the batch
+// loaders: s0 = (u, v, A, B), s1 = (C, L, r, g), s2 = (b, -, rect_c, rect_r).
+__device__ __forceinline__ void store_decoded(const float4& q0, const float4& q1, uint2 rect,
+                                              float4& s0, float4& s1, float4& s2) {
+    float r, g, b;
+    unpack_rgb(q1.z, q1.w, r, g, b);
+    s0 = q0;
+    s1 = make_float4(q1.x, q1.y, r, g);
+    s2 = make_float4(b, 0.f, __uint_as_float(rect.x), __uint_as_float(rect.y));
 }
 
 // Adds the block's evaluated and composited pair counts to pairs[0..1].
@@ -250,9 +274,10 @@ composite_rays_kernel(CompositeParams p, const int4* __restrict__ work,
         const uint32_t i = b + threadIdx.x;
         if (i < rg.y) {
             const int64_t e = vbase + vals[i];
-            s0[threadIdx.x] = rec[3 * e];
-            s1[threadIdx.x] = rec[3 * e + 1];
-            s2[threadIdx.x] = rec[3 * e + 2];
+            const float4 q0 = rec[kRecordFloat4 * e], q1 = rec[kRecordFloat4 * e + 1];
+            const uint4 m = p.meta[e];
+            store_decoded(q0, q1, make_uint2(m.x, m.y), s0[threadIdx.x], s1[threadIdx.x],
+                          s2[threadIdx.x]);
         }
         __syncthreads();
         const int nb = int(rg.y - b < kRayThreads ? rg.y - b : kRayThreads);
@@ -296,9 +321,10 @@ __global__ void composite_full_kernel(CompositeParams p, const uint2* __restrict
         const uint32_t i = b + threadIdx.x;
         if (i < rg.y) {
             const int64_t e = vbase + vals[i];
-            s0[threadIdx.x] = rec[3 * e];
-            s1[threadIdx.x] = rec[3 * e + 1];
-            s2[threadIdx.x] = rec[3 * e + 2];
+            const float4 q0 = rec[kRecordFloat4 * e], q1 = rec[kRecordFloat4 * e + 1];
+            const uint4 m = p.meta[e];
+            store_decoded(q0, q1, make_uint2(m.x, m.y), s0[threadIdx.x], s1[threadIdx.x],
+                          s2[threadIdx.x]);
         }
         __syncthreads();
         const int nb = int(rg.y - b < uint32_t(nthr) ? rg.y - b : uint32_t(nthr));
@@ -496,19 +522,21 @@ __device__ void block_sort(const unsigned long long* __restrict__ keys, uint32_t
 // blockDim.x records (cp.async prefetch of batch b+1 while batch b is
 // blended) until every ray of the block is finished.
 template <bool TRANSPOSED>
-__device__ __forceinline__ void stream_list(const unsigned long long* sk, int len, int64_t vbase,
-                                            const float4* __restrict__ rec, float4* buf, int* wbuf,
-                                            Acc& a, bool& done, uint32_t& evals, float px, float py,
-                                            int bx0, int bx1, int by0, int by1) {
+__device__ __forceinline__ void stream_list(const CompositeParams& p, const unsigned long long* sk,
+                                            int len, int64_t vbase, const float4* __restrict__ rec,
+                                            float4* buf, int* wbuf, Acc& a, bool& done,
+                                            uint32_t& evals, float px, float py, int bx0, int bx1,
+                                            int by0, int by1) {
     const int nthr = blockDim.x, t = threadIdx.x;
-    // single shared batch: load, barrier, blend, vote
+    // single shared batch: load (the record and, from the tile metadata, its
+    // pixel box), barrier, blend, vote
     for (int b = 0; b < len; b += nthr) {
         const int i = b + t;
         if (i < len) {
             const int64_t e = vbase + (uint32_t(sk[i]) >> 4);
-            buf[t] = rec[3 * e];
-            buf[nthr + t] = rec[3 * e + 1];
-            buf[2 * nthr + t] = rec[3 * e + 2];
+            const float4 q0 = rec[kRecordFloat4 * e], q1 = rec[kRecordFloat4 * e + 1];
+            const uint4 m = p.meta[e];
+            store_decoded(q0, q1, make_uint2(m.x, m.y), buf[t], buf[nthr + t], buf[2 * nthr + t]);
         }
         __syncthreads();
         const int nb = len - b < nthr ? len - b : nthr;
@@ -571,8 +599,8 @@ composite_rays_binned_kernel(CompositeParams p, const int4* __restrict__ gwork,
         warp_box(active, col, row, bx0, bx1, by0, by1);
         Acc a{1.f, 0.f, 0.f, 0.f, 0u};
         bool done = !active;
-        stream_list<TRANSPOSED>(S.sk, len, vbase, rec, S.buf, S.wbuf, a, done, evals, px, py, bx0,
-                                bx1, by0, by1);
+        stream_list<TRANSPOSED>(p, S.sk, len, vbase, rec, S.buf, S.wbuf, a, done, evals, px, py,
+                                bx0, bx1, by0, by1);
         if (active) {
             float* o = raycol + 3 * int64_t(ray.y);
             o[0] = a.c0;
@@ -584,8 +612,11 @@ composite_rays_binned_kernel(CompositeParams p, const int4* __restrict__ gwork,
     if (pairs) count_pairs(pairs, evals, blended);
 }
 
+// Direct evaluation at 32 registers a thread: the standard paradigm's blocks
+// (a thread per pixel, 256 for its 16 x 16 tiles) then run eight to an SM,
+// which its latency-bound per-pixel blend loop needs
 template <bool TRANSPOSED, int KPT>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, TRANSPOSED ? 1 : 2)
 composite_full_binned_kernel(CompositeParams p, const int32_t* __restrict__ list, int cap,
                              const uint32_t* __restrict__ gstart,
                              const unsigned long long* __restrict__ keys,
@@ -611,8 +642,8 @@ composite_full_binned_kernel(CompositeParams p, const int32_t* __restrict__ list
     Acc a{1.f, 0.f, 0.f, 0.f, 0u};
     uint32_t evals = 0;
     bool done = !inside;
-    stream_list<TRANSPOSED>(S.sk, len, vbase, rec, S.buf, S.wbuf, a, done, evals, px, py, bx0, bx1,
-                            by0, by1);
+    stream_list<TRANSPOSED>(p, S.sk, len, vbase, rec, S.buf, S.wbuf, a, done, evals, px, py, bx0,
+                            bx1, by0, by1);
     if (pairs) count_pairs(pairs, evals, a.blended);
     if (inside) {
         float* o = Mm + ((int64_t(v) * p.height + row) * p.width + col) * 3;
@@ -656,12 +687,13 @@ struct WarpSort {
 };
 template <int CAP>
 struct WarpStream {
-    // record batch slots (one being composited, the rest in flight): the
-    // 512-key class trades depth for occupancy (eight blocks per SM), the
-    // 1024-key class, held to six blocks by its sort phase, takes three
-    static constexpr int kSlots = CAP <= 512 ? 2 : 3;
+    // record batch slots (one being composited, the rest in flight): as many
+    // 32-record batches of 32-byte records as fit in the space the sort phase
+    // needs anyway (the 512-key class at eight blocks per SM, the 1024-key
+    // class at six)
+    static constexpr int kSlots = CAP <= 512 ? 3 : 4;
     uint32_t idx[CAP];
-    float4 buf[kSlots][3][32];
+    float4 buf[kSlots][kRecordFloat4][32];
     RayTable rays;
 };
 template <int CAP>
@@ -669,6 +701,8 @@ union WarpSmem {
     WarpSort<CAP> s;
     WarpStream<CAP> c;
 };
+static_assert(sizeof(WarpStream<512>) <= sizeof(WarpSort<512>), "stream phase fits the sort's space");
+static_assert(sizeof(WarpStream<1024>) <= sizeof(WarpSort<1024>), "stream phase fits the sort's space");
 // blocks of kWarpsPerBlock warps per SM: eight (512-key class, 64
 // registers a thread) and six (1024-key class, 80 registers); 228 KB of
 // shared memory an SM, 1 KB of it reserved per block
@@ -840,8 +874,8 @@ __device__ __forceinline__ void narrow_keys(WarpSmem<CAP>& W, int len) {
 constexpr float kTestMargin = 0.05f;
 
 // Transposed evaluation of a batch of n <= 32 records held in shared memory
-// (c0, c1, c2) for the warp's rays: lane j holds record j's conic (u, v, A,
-// B, C, L) when `hit` (its pixel box meets the rays' box).  The lane expands
+// (c0, c1: the two halves of each record) for the warp's rays: lane j holds
+// record j's conic (u, v, A, B, C, L) when `hit` (j < n).  The lane expands
 // the quadratic about the box centre (ox, oy) into
 // l2(x, y) = x (A x + B y + D) + y (C y + E) + F and tests it against every
 // ray (5 FMAs per pair, ray positions from the table), four rays per step
@@ -849,10 +883,10 @@ constexpr float kTestMargin = 0.05f;
 // same rounding as fmaf); ray r's mask of candidate records goes to
 // T.mask[r].  Then every lane blends its candidates in list order.
 template <bool COUNT>
-__device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const float4* c2, int n,
-                                       bool hit, float u, float v, float A, float B, float C,
-                                       float L, Acc& a, bool& done, uint32_t& evals, float px,
-                                       float py, RayTable& T, float ox, float oy) {
+__device__ __forceinline__ void eval32(const float4* c0, const float4* c1, int n, bool hit, float u,
+                                       float v, float A, float B, float C, float L, Acc& a,
+                                       bool& done, uint32_t& evals, float px, float py,
+                                       RayTable& T, float ox, float oy) {
     const int lane = threadIdx.x & 31;
     if (!__any_sync(0xffffffffu, hit)) return;
     const unsigned act = __ballot_sync(0xffffffffu, !done);
@@ -884,7 +918,7 @@ __device__ __forceinline__ void eval32(const float4* c0, const float4* c1, const
     while (mine && !done) {  // candidates passed the (widened) test: alpha decides
         const int sidx = __ffs(mine) - 1;
         mine &= mine - 1;
-        if (!blend<false, COUNT>(a, px, py, c0[sidx], c1[sidx], c2[sidx].x)) done = true;
+        if (!blend_rec<false, COUNT>(a, px, py, c0[sidx], c1[sidx])) done = true;
     }
     __syncwarp();
 }
@@ -901,24 +935,20 @@ __device__ __forceinline__ void ray_table(RayTable& T, bool active, float px, fl
     __syncwarp();
 }
 
-// Lane's record of a shared-memory batch against the warp's ray box:
-// returns `hit` and loads the conic into registers when it does.
-__device__ __forceinline__ bool batch_conic(const float4* c0, const float4* c1, const float4* c2,
-                                            int n, int bx0, int bx1, int by0, int by1, float& u,
+// Lane's record of a shared-memory batch: loads its conic into registers
+// (lanes past the batch hold one that no ray passes).  A tile list holds
+// only records whose pixel box meets the tile, and the warp's rays spread
+// over the tile, so no box pre-test is made: the widened test below sorts
+// the records out at a few FMAs per pair.
+__device__ __forceinline__ bool batch_conic(const float4* c0, const float4* c1, int n, float& u,
                                             float& v, float& A, float& B, float& C, float& L) {
     const int lane = threadIdx.x & 31;
     u = 0.f; v = 0.f; A = 0.f; B = 0.f; C = 0.f; L = -1e30f;
     if (lane >= n) return false;
-    const float4 q2 = c2[lane];
-    const uint32_t rc = __float_as_uint(q2.z), rr = __float_as_uint(q2.w);
-    const bool hit = int(rc & 0xFFFFu) <= bx1 && int(rc >> 16) >= bx0 && int(rr & 0xFFFFu) <= by1 &&
-                     int(rr >> 16) >= by0;
-    if (hit) {
-        const float4 q0 = c0[lane];
-        const float2 q1 = *reinterpret_cast<const float2*>(c1 + lane);
-        u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y;
-    }
-    return hit;
+    const float4 q0 = c0[lane];
+    const float2 q1 = *reinterpret_cast<const float2*>(c1 + lane);
+    u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y;
+    return true;
 }
 
 // Streams the warp's sorted list in batches of 32 records (cp.async, up to
@@ -938,9 +968,8 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
         const int i = b * 32 + lane;
         if (b < nbatch && i < len) {
             const int64_t e = vbase + (W.c.idx[i] >> 4);
-            cp_async16(&W.c.buf[slot][0][lane], rec + 3 * e);
-            cp_async16(&W.c.buf[slot][1][lane], rec + 3 * e + 1);
-            cp_async16(&W.c.buf[slot][2][lane], rec + 3 * e + 2);
+            cp_async16(&W.c.buf[slot][0][lane], rec + kRecordFloat4 * e);
+            cp_async16(&W.c.buf[slot][1][lane], rec + kRecordFloat4 * e + 1);
         }
         cp_async_commit();
     };
@@ -953,13 +982,11 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
         __syncwarp();
         const float4* c0 = W.c.buf[slot][0];
         const float4* c1 = W.c.buf[slot][1];
-        const float4* c2 = W.c.buf[slot][2];
         slot = slot + 1 == S ? 0 : slot + 1;
         const int n = len - b * 32 < 32 ? len - b * 32 : 32;
         float u, v, A, B, C, L;
-        const bool hit = batch_conic(c0, c1, c2, n, bx0, bx1, by0, by1, u, v, A, B, C, L);
-        eval32<COUNT>(c0, c1, c2, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.c.rays, ox,
-                      oy);
+        const bool hit = batch_conic(c0, c1, n, u, v, A, B, C, L);
+        eval32<COUNT>(c0, c1, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.c.rays, ox, oy);
         if (__all_sync(0xffffffffu, done)) break;
     }
     cp_async_wait<0>();
@@ -972,7 +999,7 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
 struct QuadPipe {
     int stage[64];
     int idx[2][32];
-    float4 buf[2][3][32];
+    float4 buf[2][kRecordFloat4][32];
     RayTable rays;
 };
 
@@ -1009,9 +1036,8 @@ __device__ void quadrant_stream(const unsigned long long* sk, int len, int q, in
         cnt -= n;
         if (lane < n) {
             const int64_t e = vbase + (uint32_t(sk[mine]) >> 4);
-            cp_async16(&Q.buf[slot][0][lane], rec + 3 * e);
-            cp_async16(&Q.buf[slot][1][lane], rec + 3 * e + 1);
-            cp_async16(&Q.buf[slot][2][lane], rec + 3 * e + 2);
+            cp_async16(&Q.buf[slot][0][lane], rec + kRecordFloat4 * e);
+            cp_async16(&Q.buf[slot][1][lane], rec + kRecordFloat4 * e + 1);
         }
         cp_async_commit();
         __syncwarp();
@@ -1026,10 +1052,9 @@ __device__ void quadrant_stream(const unsigned long long* sk, int len, int q, in
         __syncwarp();
         const float4* c0 = Q.buf[slot][0];
         const float4* c1 = Q.buf[slot][1];
-        const float4* c2 = Q.buf[slot][2];
         float u, v, A, B, C, L;
-        const bool hit = batch_conic(c0, c1, c2, n_cur, bx0, bx1, by0, by1, u, v, A, B, C, L);
-        eval32<true>(c0, c1, c2, n_cur, hit, u, v, A, B, C, L, a, done, evals, px, py, Q.rays, ox, oy);
+        const bool hit = batch_conic(c0, c1, n_cur, u, v, A, B, C, L);
+        eval32<true>(c0, c1, n_cur, hit, u, v, A, B, C, L, a, done, evals, px, py, Q.rays, ox, oy);
         slot ^= 1;
         n_cur = __all_sync(0xffffffffu, done) ? 0 : n_next;
     }
@@ -1167,8 +1192,7 @@ composite_rays_block_kernel(const FrameDesc* __restrict__ F, const int64_t* __re
             // quadrant q (x half + 2 * y half) of the tile
             for (int i = threadIdx.x; i < len; i += blockDim.x) {
                 const unsigned long long k = sk[i];
-                const uint2 box = *reinterpret_cast<const uint2*>(
-                    reinterpret_cast<const float*>(d.rec + 3 * (vbase + (uint32_t(k) >> 4)) + 2) + 2);
+                const uint4 box = d.cp.meta[vbase + (uint32_t(k) >> 4)];
                 const int c0 = int(box.x & 0xFFFFu), c1 = int(box.x >> 16);
                 const int rr0 = int(box.y & 0xFFFFu), rr1 = int(box.y >> 16);
                 const uint32_t lo_x = c0 < xm, hi_x = c1 >= xm, lo_y = rr0 < ym, hi_y = rr1 >= ym;

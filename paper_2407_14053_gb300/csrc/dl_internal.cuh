@@ -63,22 +63,45 @@ struct ProjectParams {
     int32_t tile_sx, tile_sy;  // log2 of tile_w, tile_h (powers of two)
 };
 
-// Per (view, Gaussian) record written by the projection, 3 x float4:
+// Per (view, Gaussian) record written by the projection, 2 x float4 = 32 B
+// (one DRAM sector; records start at 32-byte boundaries):
 //  q0 = (u - w/2, v - h/2, A, B)
-//  q1 = (C, log2(opacity), r, g)
-//  q2 = (b, depth, rect_c, rect_r)   pixel bounding box of alpha >= 1/255,
-//       rect_c = c0 | c1 << 16, rect_r = r0 | r1 << 16 (bit patterns)
+//  q1 = (C, log2(opacity), colour bits lo, colour bits hi)
 // with log2 alpha = A dx^2 + B dx dy + C dy^2 + log2(opacity) at pixel offset
-// (dx, dy) from the mean (A, B, C are -log2(e)/2 times the conic's xx, 2xy, yy).
+// (dx, dy) from the mean (A, B, C are -log2(e)/2 times the conic's xx, 2xy,
+// yy).  The colour (r, g, b >= 0) keeps, per channel, the 8 exponent bits and
+// the top 13 mantissa bits of its FP32 value, rounded to nearest (relative
+// error <= 2^-14): lo = r21 << 11 | b21 >> 10, hi = g21 << 11 | (b21 & 0x3FF),
+// x21 being bits 30..10 of the rounded FP32 pattern (the sign bit is 0).
+constexpr int kRecordFloat4 = 2;
+
+__device__ __forceinline__ void pack_rgb(float r, float g, float b, float& lo, float& hi) {
+    // + 0x200 rounds the dropped 10 bits to nearest; a carry into the
+    // exponent is the correct rounding; colours are finite and >= 0
+    const uint32_t kr = (__float_as_uint(r) + 0x200u) >> 10;
+    const uint32_t kg = (__float_as_uint(g) + 0x200u) >> 10;
+    const uint32_t kb = (__float_as_uint(b) + 0x200u) >> 10;
+    lo = __uint_as_float((kr << 11) | (kb >> 10));
+    hi = __uint_as_float((kg << 11) | (kb & 0x3FFu));
+}
+
+__device__ __forceinline__ void unpack_rgb(float lo_f, float hi_f, float& r, float& g, float& b) {
+    const uint32_t lo = __float_as_uint(lo_f), hi = __float_as_uint(hi_f);
+    r = __uint_as_float((lo & 0xFFFFF800u) >> 1);
+    g = __uint_as_float((hi & 0xFFFFF800u) >> 1);
+    b = __uint_as_float(((lo & 0x7FFu) << 20) | ((hi & 0x3FFu) << 10));
+}
 // Per (view, Gaussian) tile metadata written beside the record, all that key
-// emission reads: {rect_c, rect_r (as in q2), depth key, tiles touched}; the
+// emission reads (the compositing loaders that test records against pixel
+// boxes read the box from here too): {rect_c, rect_r (as in q2), depth key, tiles touched}; the
 // depth key is the FP32 bits of z minus those of 0.2 (z > 0.2), clamped to
 // 28 bits; tiles touched = 0 marks a culled Gaussian (the rest is then 0).
 struct ProjectOut {
-    float4* rec;       // nv * n * 3
+    float4* rec;       // nv * n * kRecordFloat4
     uint4* meta;       // nv * n
     unsigned long long* total;  // sum of tiles touched (atomic)
     uint32_t* gcount;  // optional: keys per (view, tile) group (atomic; zeroed by caller)
+    unsigned long long* visible = nullptr;  // optional: records written (atomic)
 };
 
 template <typename T>
@@ -194,6 +217,7 @@ struct CompositeParams {
     int32_t width, height;
     float half_w, half_h;
     int32_t tile_w, tile_h, ntx, ntiles;
+    const uint4* meta;  // per (view, Gaussian) tile metadata of the projection (pixel box)
 };
 // DirectL: work items {group, begin, end, -} over grouped rays.
 // pairs (optional, 2 x u64): evaluated and composited (ray, Gaussian) pairs.

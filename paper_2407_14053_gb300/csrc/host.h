@@ -2,6 +2,7 @@
 // the helpers that api.cu and batch.cu share.  Host code only.
 #pragma once
 
+#include <array>
 #include <map>
 #include <memory>
 #include <string>
@@ -91,12 +92,48 @@ struct PendingFrame {
     int64_t n_keys, n_rays;
     int32_t launches;
     int64_t lists_small, lists_large, max_list;
+    int64_t n_visible;
+    int64_t frame = -1;  // frame number; its device counters arrive by a readback
+    int32_t status = 0;
+};
+
+// Capacities a frame signature (scene, display, mode, tile, view size) runs
+// with once one of its frames has been sized on the host: the tile-key
+// buffer's capacity at that time and the long-list capacity.  Later frames
+// of the signature size their launches from device counters and these
+// capacities, with no host synchronisation; a frame that exceeds them is
+// dropped on the device (its output left untouched, its status word set),
+// and the next frame of the signature is sized on the host again, as is one
+// after a frame that used more than 85 % of either capacity.
+struct FrameHint {
+    bool sized = false;
+    int32_t block_cap = 2048;
+    int64_t key_cap = 0;
+};
+using FrameSig = std::array<int32_t, 7>;
+
+// Pinned copies of the 256-byte counter block of frames rendered without a
+// host synchronisation (keys, visible records, list classes, status), in a
+// ring; a slot is read ("harvested") once its copy has completed, at the
+// latest before the slot is reused.
+constexpr int kReadbacks = 8;
+struct Readback {
+    unsigned long long* h = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    int64_t frame = -1;
+    FrameHint* hint = nullptr;
 };
 
 struct Workspace {
     DevBuf cams, rec, meta, count, offset, scan_tmp, keys[2], vals[2], ranges, radix_tmp, Mm, out, small,
         pairs, gcount, gstart, gfill, lists, gscan_tmp, raycol, fdesc;
     unsigned long long* h_total = nullptr;  // pinned, 256 bytes (copy of `small`)
+    Readback rb[kReadbacks];
+    int rb_next = 0;
+    int64_t frame_no = 0;      // frames enqueued by render_frame
+    int64_t last_async = -1;   // frame number of the last frame read back asynchronously
+    int64_t dropped = 0;       // frames dropped on the device (capacity exceeded)
     size_t last_bytes = 0;
     std::vector<StageEvents*> ev_free;
     std::vector<PendingFrame> pending;
@@ -109,6 +146,10 @@ struct Workspace {
     int aslot = 0;
     ~Workspace() {
         if (h_total) cudaFreeHost(h_total);
+        for (Readback& r : rb) {
+            if (r.h) cudaFreeHost(r.h);
+            if (r.done) cudaEventDestroy(r.done);
+        }
         for (int i = 0; i < 2; ++i) {
             if (ev_frame[i]) cudaEventDestroy(ev_frame[i]);
             if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
@@ -149,6 +190,7 @@ struct dl_ctx {
     bool count_pairs = false;  // with timing: the compositing pair counters
     dl_frame_stats stats{};
     int32_t n_batches = 0;  // live dl_batch objects on this context
+    std::map<dl::FrameSig, dl::FrameHint> hints;
 };
 
 namespace dl {
@@ -158,6 +200,10 @@ dl_status cuda_fail(dl_ctx* c, cudaError_t e, const char* what);
 dl_status check_ctx(dl_ctx* ctx);
 int bits_for(int64_t n);
 size_t max_smem_optin(int device);
+// Reads back every frame counter block whose copy has completed (wait: all
+// of them, waiting for the copies), updating the frames' statistics and the
+// capacities of their signatures.
+dl_status harvest_readbacks(dl_ctx* ctx, bool wait);
 // Rays of a ray set grouped by (view, tile) for one tile shape (cached per shape).
 dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th, cudaStream_t s,
                      TileGroups** out);

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
     constexpr int NC = (DEG + 1) * (DEG + 1);
     const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     unsigned long long my_total = 0;
+    uint32_t my_visible = 0;
     if (g < p.n) {
         const float mx = G.mean[3 * g], my = G.mean[3 * g + 1], mz = G.mean[3 * g + 2];
         // Sigma = R S S^T R^T (Eq. (8)), R from the normalised quaternion
@@ -156,10 +157,11 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
                             for (int i = 0; i < NC; ++i) acc = fmaf(Y[i], sh[i][c], acc);
                             col[c] = fmaxf(acc + 0.5f, 0.f);
                         }
-                        float4* rec = out.rec + 3 * e;
+                        float4* rec = out.rec + kRecordFloat4 * e;
+                        float clo, chi;
+                        pack_rgb(col[0], col[1], col[2], clo, chi);
                         rec[0] = make_float4(uc, vc, -0.5f * kLog2e * cyy * id, kLog2e * cxy * id);
-                        rec[1] = make_float4(-0.5f * kLog2e * cxx * id, log2o, col[0], col[1]);
-                        rec[2] = make_float4(col[2], tz, __uint_as_float(rect_c), __uint_as_float(rect_r));
+                        rec[1] = make_float4(-0.5f * kLog2e * cxx * id, log2o, clo, chi);
                         uint32_t dk = __float_as_uint(tz) - __float_as_uint(0.2f);
                         if (dk > 0x0FFFFFFFu) dk = 0x0FFFFFFFu;
                         meta = make_uint4(rect_c, rect_r, dk, cnt);
@@ -168,12 +170,17 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
             }
             out.meta[e] = meta;
             my_total += cnt;
+            my_visible += cnt ? 1u : 0u;
         }
     }
     // warp sum of the tile counts -> one 64-bit atomic per warp (no block
     // barrier: warps finish at different times)
     my_total = warp_sum(my_total);
     if ((threadIdx.x & 31) == 0 && my_total) atomicAdd(out.total, my_total);
+    if (out.visible) {
+        const unsigned long long vis = warp_sum((unsigned long long)my_visible);
+        if ((threadIdx.x & 31) == 0 && vis) atomicAdd(out.visible, vis);
+    }
 }
 
 // Key of a (view, tile, Gaussian) overlap: (view*ntiles + tile) << 28 | depth

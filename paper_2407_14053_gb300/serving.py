@@ -123,7 +123,16 @@ def summarize(reqs: List[Request], launches: int, slots_used: int) -> dict:
     t_first = min((r.arrival for r in reqs), default=0.0)
     t_last = max((r.done for r in done), default=0.0)
     span = max(t_last - t_first, 1e-9)
+    classes = {}
+    for key in sorted({r.display for r in done}, key=str):
+        cl = [r for r in done if r.display == key]
+        classes[str(key)] = {
+            "frames": len(cl), "p50_ms": 1e3 * percentile([r.latency for r in cl], 50),
+            "p99_ms": 1e3 * percentile([r.latency for r in cl], 99),
+            "service_ms_mean": 1e3 * float(np.mean([r.done - r.launched for r in cl])),
+            "fallbacks": sum(1 for r in cl if r.fallback)}
     return {"requests": len(reqs), "completed": len(done), "rejected": rejected,
+            "per_display": classes,
             "failed": sum(1 for r in done if r.status != 0 and not r.fallback),
             "fallbacks": sum(1 for r in done if r.fallback),
             "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
@@ -142,11 +151,13 @@ class Server:
     (the same in every lane; rendered at plan_pose, a 4x4 light-field centre),
     so slots of different sizes serve different request classes.  A request takes the first free slot that holds it;
     requests no slot can hold, or whose scene or display alone exceed the
-    budget, are rejected (status REJECTED_SLOT / REJECTED_BUDGET)."""
+    budget, are rejected (status REJECTED_SLOT / REJECTED_BUDGET).
+    keep_outputs: True keeps every request's device frame in ``Request.out``;
+    a set of request ids keeps those only."""
 
     def __init__(self, renderer, scenes: Dict, displays: Dict, slot_plans, plan_pose,
                  lanes: int = 2, hbm_budget: float = 150e9, margin: float = 1.3, tile=None,
-                 keep_outputs: bool = False):
+                 keep_outputs=False):
         self.r = renderer
         self.scene_src, self.display_src = scenes, displays
         self.tile = tile
@@ -231,7 +242,8 @@ class Server:
             b.clear(s)
             self.cache.release(("scene", req.scene))
             self.cache.release(("display", req.display))
-            if not self.keep_outputs:
+            if not (self.keep_outputs is True or
+                    (isinstance(self.keep_outputs, (set, frozenset)) and req.rid in self.keep_outputs)):
                 req.out = None
             lane["slot_req"][s] = None
         lane["busy"] = False

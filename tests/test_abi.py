@@ -57,7 +57,8 @@ int main(void) {
   P(dl_gaussians_desc, sh) P(dl_gaussians_desc, on_device) P(dl_display_params, pitch_lx)
   P(dl_display_params, repurpose) P(dl_display_params, reverse_views) P(dl_display_params, rig)
   P(dl_frame_stats, ms_total)
-  P(dl_frame_stats, max_list) P(dl_frame_stats, lists_small)
+  P(dl_frame_stats, max_list) P(dl_frame_stats, lists_small) P(dl_frame_stats, n_visible)
+  P(dl_frame_stats, status)
   return 0;
 }
 '''
@@ -86,6 +87,15 @@ def test_status_strings(lib):
     from paper_2407_14053_gb300 import _binding as B
     assert B.dl_status_string(0) == "DL_OK"
     assert B.dl_status_string(-7) == "DL_ERR_CAPACITY"
+
+
+def test_peaks_without_gpu_fail_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2407_14053_gb300 import _binding as B
+    with pytest.raises(B.DirectLError):
+        B.dl_measure_peaks(0)
 
 
 def test_create_without_gpu_fails_cleanly(lib):

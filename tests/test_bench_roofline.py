@@ -16,8 +16,9 @@ def test_hbm_binds_on_the_4k_frame():
     r = bench.compositing_roofline(2.71, 92.6e6, 11.1e6, 2.58e9, 0.34e9, 6782.8, "measured")
     b = r["bounds_ms"]
     assert r["bound"] == "hbm" and b["hbm"] > b["mufu"] > b["alu"]
-    # bytes: 44 B a key + 12 B a ray; the bound time over the stage time
-    assert abs(r["bytes_per_launch"] - (92.6e6 * 44 + 11.1e6 * 12)) < 1.0
+    # bytes: 40 B a key (8 B key, 32 B record) + 12 B a ray; the bound time
+    # over the stage time
+    assert abs(r["bytes_per_launch"] - (92.6e6 * 40 + 11.1e6 * 12)) < 1.0
     assert abs(r["frac"] - b["hbm"] / 2.71) < 1e-12
     assert abs(r["achieved"] - r["bytes_per_launch"] / 2.71e-3 / 1e9) < 1e-6
     assert r["unit"] == "GB/s" and r["peak"] == 6782.8

@@ -49,6 +49,10 @@ def _label(tol):
 def _frame(renderer, sid, did, L0, mode):
     out = renderer.render(sid, did, L0, mode)
     torch.cuda.synchronize()
+    if renderer.stats()["status"]:  # dropped on the device: render it again, sized
+        out = renderer.render(sid, did, L0, mode)
+        torch.cuda.synchronize()
+        assert renderer.stats()["status"] == 0
     return out.cpu().numpy()
 
 
@@ -219,6 +223,71 @@ def test_edge_cases(renderer, case):
             assert img.max() > 0.1
     renderer.free_display(did)
     renderer.free_scene(sid)
+
+
+def _away(distance=4.0):
+    """A light-field centre on the -z axis looking away from the origin (and
+    from the scene): every view sees nothing."""
+    L0 = np.eye(4)
+    L0[0, 0] = L0[2, 2] = -1.0
+    L0[2, 3] = -distance
+    return L0
+
+
+def test_frames_after_sizing_run_on_device_counters():
+    """After a frame of a (scene, display, mode, tile) has been sized on the
+    host, later frames run without a host synchronisation.  Frames that fit
+    the capacities equal freshly sized ones bit for bit and report their
+    counts; a frame that needs far more tile keys than the sizing frame is
+    dropped on the device (output untouched, status bit 0) and the next one
+    is sized again; with a host output the dropped frame is rendered again."""
+    from paper_2407_14053_gb300 import Renderer
+    wl = W.WORKLOADS["tiny"]
+    scene = W.make_scene(wl.scene)
+    toward = W.light_field_centre(4.0, 2.0)
+    ref_r = Renderer(0)
+    try:
+        sid = ref_r.load_gaussians(scene, "f32")
+        did = ref_r.set_display(wl.display)
+        ref = _frame(ref_r, sid, did, toward, "directl")
+        ref_keys = ref_r.stats()["n_keys"]
+    finally:
+        ref_r.close()
+    assert ref_keys > 65536 * 2
+    r = Renderer(0)
+    try:
+        sid = r.load_gaussians(scene, "f32")
+        did = r.set_display(wl.display)
+        out = torch.full((wl.display.height, wl.display.width, 3), -7.0, device="cuda")
+        r.render(sid, did, _away(), "directl", out)          # sized: no keys at all
+        torch.cuda.synchronize()
+        st = r.stats()
+        assert st["n_keys"] == 0 and st["status"] == 0 and not out.any()
+        out.fill_(-7.0)
+        r.render(sid, did, toward, "directl", out)            # far past the capacity
+        torch.cuda.synchronize()
+        st = r.stats()
+        assert st["status"] & 1 and bool((out == -7.0).all())
+        for i in range(4):                                    # sized again, then on device
+            r.render(sid, did, toward, "directl", out)
+            torch.cuda.synchronize()
+            st = r.stats()
+            assert st["status"] == 0 and st["n_keys"] == ref_keys
+            assert np.array_equal(out.cpu().numpy(), ref), f"frame {i}"
+    finally:
+        r.close()
+    # host output (a fresh context, so the key buffer is small): the dropped
+    # frame is rendered again within the call
+    r = Renderer(0)
+    try:
+        sid = r.load_gaussians(scene, "f32")
+        did = r.set_display(wl.display)
+        host = torch.empty((wl.display.height, wl.display.width, 3)).pin_memory()
+        r.render_to_host(sid, did, _away(), host, "directl")
+        r.render_to_host(sid, did, toward, host, "directl")
+        assert r.stats()["status"] == 0 and np.array_equal(host.numpy(), ref)
+    finally:
+        r.close()
 
 
 def test_host_output_matches_device_output(renderer):
