@@ -175,6 +175,12 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
     DL_CK(G->grouped.reserve(8 * size_t(nr)), "alloc");
     DL_CK(launch_ray_group_gather(vs, R.ray_pix.as<uint32_t>(), nr, G->grouped.as<int2>(), s),
           "group gather");
+    const int64_t nsub = 3 * int64_t(D.q.w) * D.q.h;
+    DL_CK(G->slot_of.reserve(4 * size_t(nsub)), "alloc");
+    DL_CK(launch_group_slots(G->grouped.as<int2>(), nr, R.ray_of.as<uint32_t>(), nsub,
+                             alt ? v0.as<uint32_t>() : v1.as<uint32_t>(), G->slot_of.as<uint32_t>(),
+                             s),
+          "group slots");
     std::vector<uint2> h_ranges(static_cast<size_t>(ngroups));
     DL_CK(cudaMemcpyAsync(h_ranges.data(), ranges.p, 8 * size_t(ngroups), cudaMemcpyDeviceToHost, s),
           "copy");
@@ -314,32 +320,26 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 // Per-Gaussian data and the implicit tree of the ray-order renderer.
 dl_status build_raycast(dl_ctx* ctx, Scene& S, cudaStream_t s) {
-    S.rc_level_n.assign(kMaxRayLevels + 8, 0);
-    int levels = 0;
-    const size_t n_nodes = raycast_bvh_nodes(S.n, S.rc_level_n.data(), &levels);
-    if (levels > kMaxRayLevels)
-        return fail(ctx, DL_ERR_CAPACITY, "ray-order tree of %d levels", levels);
-    S.rc_level_n.resize(size_t(levels));
-    S.rc_level_off.assign(size_t(levels), 0);
-    for (int lv = 1; lv < levels; ++lv)
-        S.rc_level_off[size_t(lv)] = S.rc_level_off[size_t(lv - 1)] + S.rc_level_n[size_t(lv - 1)];
-    DL_CK(S.rc_gauss.reserve(48 * size_t(S.n)), "alloc ray-order data");
-    DL_CK(S.rc_gbox.reserve(32 * size_t(S.n)), "alloc ray-order boxes");
-    DL_CK(S.rc_nodes.reserve(32 * n_nodes), "alloc ray-order tree");
-    DL_CK(S.rc_meta.reserve(16 * size_t(levels)), "alloc ray-order levels");
-    int64_t* meta = S.rc_meta.as<int64_t>();
-    DL_CK(cudaMemcpyAsync(meta, S.rc_level_off.data(), 8 * size_t(levels), cudaMemcpyHostToDevice, s),
-          "copy levels");
-    DL_CK(cudaMemcpyAsync(meta + levels, S.rc_level_n.data(), 8 * size_t(levels),
-                          cudaMemcpyHostToDevice, s),
-          "copy levels");
+    DL_CK(S.rc_gauss.reserve(48 * size_t(std::max<int64_t>(S.n, 1))), "alloc ray-order data");
+    DL_CK(S.rc_gbox.reserve(32 * size_t(std::max<int64_t>(S.n, 1))), "alloc ray-order boxes");
     const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
-    DL_CK(launch_raycast_prepare(S.dtype, attrs, S.n, S.rc_gauss.as<float4>(), S.rc_gbox.as<float4>(),
-                                 S.rc_nodes.as<float4>(), S.rc_level_off.data(),
-                                 S.rc_level_n.data(), levels, s),
+    DL_CK(launch_raycast_prepare(S.dtype, attrs, S.n, S.rc_gauss.as<float4>(), S.rc_gbox.as<float4>(), s),
           "ray-order preparation");
-    DL_CK(cudaStreamSynchronize(s), "sync");
-    S.rc_levels = levels;
+    DevBuf tmp;
+    DL_CK(tmp.reserve(raycast_build_tmp_bytes(S.n)), "alloc tree build");
+    int64_t n_bin = 0;
+    DL_CK(raycast_build_binary(S.rc_gbox.as<float4>(), S.n, tmp.p, &n_bin, s), "SAH tree");
+    DL_CK(S.rc_nodes.reserve(sizeof(RayNode) * size_t(std::max<int64_t>(n_bin, 1))), "alloc tree");
+    int64_t n_wide = 0;
+    int depth = 0;
+    DL_CK(raycast_collapse(S.rc_gbox.as<float4>(), S.n, tmp.p, n_bin, S.rc_nodes.as<RayNode>(), &n_wide,
+                           &depth, s),
+          "8-wide tree");
+    if (depth > kMaxWideDepth)
+        return fail(ctx, DL_ERR_CAPACITY, "ray-order tree of %d wide levels (limit %d)", depth,
+                    kMaxWideDepth);
+    S.rc_depth = depth;
+    S.rc_n_nodes = n_wide;
     S.rc_built = true;
     return DL_OK;
 }
@@ -482,9 +482,8 @@ dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[
     DL_CK(W.raycol.reserve(12 * size_t(R.n_rays > 0 ? R.n_rays : 1)), "alloc ray colours");
     const double pi = 3.14159265358979323846;
     const double focal = 0.5 * w / std::tan(0.5 * D.prm.fov_x_deg * pi / 180.0);
-    const int64_t* meta = S.rc_meta.as<int64_t>();
-    DL_CK(launch_raycast(S.dtype, S.sh_degree, S.rc_gauss.as<float4>(), S.rc_nodes.as<float4>(), meta,
-                         meta + S.rc_levels, S.rc_levels, S.n, S.sh.p, R.ray_view.as<uint32_t>(),
+    DL_CK(launch_raycast(S.dtype, S.sh_degree, S.rc_gauss.as<float4>(), S.rc_nodes.as<RayNode>(),
+                         S.n, S.sh.p, R.ray_view.as<uint32_t>(),
                          R.ray_pix.as<uint32_t>(), G->grouped.as<int2>(), R.n_rays, W.cams.as<Cam>(), float(focal),
                          0.5f * float(w), 0.5f * float(h), ctx->heap_cap, W.raycol.as<float>(), s),
           "ray-order rendering");
@@ -493,7 +492,7 @@ dl_status render_raycast(dl_ctx* ctx, Scene& S, Display& D, const double L0_c2w[
     float* dst = nullptr;
     st = out_target(ctx, out, kind, out_bytes, s, &dst);
     if (st) return st;
-    DL_CK(launch_reorder(R.ray_of.as<uint32_t>(), W.raycol.as<float>(), 3 * int64_t(w) * h, dst,
+    DL_CK(launch_reorder(G->slot_of.as<uint32_t>(), W.raycol.as<float>(), 3 * int64_t(w) * h, dst,
                          nullptr, s),
           "reorder");
     DL_CK(mark(8), "event");
@@ -1284,7 +1283,7 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
         DL_CK(launch_interweave(w, h, nv, D.V.as<uint16_t>(), Mm, dst, s), "interweave");
     } else {
         // a dropped frame (status set) leaves the output untouched
-        DL_CK(launch_reorder(R->ray_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst,
+        DL_CK(launch_reorder(G->slot_of.as<uint32_t>(), raycol, 3 * int64_t(w) * h, dst,
                              on_device ? d_status : nullptr, s),
               "reorder");
     }

@@ -194,7 +194,7 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
     for (int32_t i = 0; i < n_slots; ++i) {
         Slot& z = b->slots[size_t(i)];
         if (!z.active) continue;
-        DL_CK(launch_reorder(z.D->rep.ray_of.as<uint32_t>(), b->at<float>(z.o_raycol),
+        DL_CK(launch_reorder(z.G->slot_of.as<uint32_t>(), b->at<float>(z.o_raycol),
                              3 * int64_t(z.D->q.w) * z.D->q.h, z.out, b->status_d() + i, s),
               "reorder");
     }

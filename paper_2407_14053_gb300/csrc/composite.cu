@@ -286,7 +286,7 @@ composite_rays_kernel(CompositeParams p, const int4* __restrict__ work,
     }
     if (pairs) count_pairs(pairs, evals, a.blended);
     if (active) {
-        float* o = raycol + 3 * int64_t(ray.y);
+        float* o = raycol + 3 * int64_t(rid);  // grouped order
         o[0] = a.c0;
         o[1] = a.c1;
         o[2] = a.c2;
@@ -602,7 +602,7 @@ composite_rays_binned_kernel(CompositeParams p, const int4* __restrict__ gwork,
         stream_list<TRANSPOSED>(p, S.sk, len, vbase, rec, S.buf, S.wbuf, a, done, evals, px, py,
                                 bx0, bx1, by0, by1);
         if (active) {
-            float* o = raycol + 3 * int64_t(ray.y);
+            float* o = raycol + 3 * int64_t(rid);  // grouped order
             o[0] = a.c0;
             o[1] = a.c1;
             o[2] = a.c2;
@@ -1139,7 +1139,7 @@ composite_rays_warp_kernel(const FrameDesc* __restrict__ F, const int64_t* __res
             warp_stream<CAP, COUNT>(W, len, vbase, rec, a, done, evals, px, py, bx0, bx1, by0, by1,
                                     ox, oy);
             if (active) {
-                float* o = raycol + 3 * int64_t(ray.y);
+                float* o = raycol + 3 * (int64_t(rbeg) + rid);  // grouped order
                 o[0] = a.c0;
                 o[1] = a.c1;
                 o[2] = a.c2;
@@ -1217,7 +1217,7 @@ composite_rays_block_kernel(const FrameDesc* __restrict__ F, const int64_t* __re
                 quadrant_stream(sk, len, warp, vbase, d.rec, pipes[warp], a, done, evals, px, py,
                                 bx0, bx1, by0, by1, ox, oy);
                 if (mine) {
-                    float* o = d.raycol + 3 * int64_t(ray.y);
+                    float* o = d.raycol + 3 * int64_t(rid);  // grouped order
                     o[0] = a.c0;
                     o[1] = a.c1;
                     o[2] = a.c2;

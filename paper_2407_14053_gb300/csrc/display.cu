@@ -329,6 +329,22 @@ __global__ void group_gather_kernel(const uint32_t* __restrict__ order,
     }
 }
 
+// pos[ray id] = position of the ray in the (view, tile) grouping
+__global__ void group_pos_kernel(const int2* __restrict__ grouped, int64_t n,
+                                 uint32_t* __restrict__ pos) {
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n;
+         j += int64_t(gridDim.x) * blockDim.x)
+        pos[uint32_t(grouped[j].y)] = uint32_t(j);
+}
+
+// slot_of[i] = pos[ray_of[i]]: the grouped position of subpixel i's ray
+__global__ void group_slot_kernel(const uint32_t* __restrict__ ray_of, int64_t n,
+                                  const uint32_t* __restrict__ pos, uint32_t* __restrict__ slot_of) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        slot_of[i] = pos[ray_of[i]];
+}
+
 __global__ void rays_export_kernel(const uint32_t* __restrict__ ray_view,
                                    const uint32_t* __restrict__ ray_pix, int64_t n,
                                    int32_t* __restrict__ out) {
@@ -435,6 +451,17 @@ cudaError_t launch_rays_export(const uint32_t* ray_view, const uint32_t* ray_pix
 cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_pix, int64_t n_rays,
                                     int2* grouped, cudaStream_t s) {
     group_gather_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(order, ray_pix, n_rays, grouped);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_slots(const int2* grouped, int64_t n_rays, const uint32_t* ray_of,
+                               int64_t n_subpixels, uint32_t* pos_tmp, uint32_t* slot_of,
+                               cudaStream_t s) {
+    group_pos_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(grouped, n_rays, pos_tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    group_slot_kernel<<<grid_for(n_subpixels, 256), 256, 0, s>>>(ray_of, n_subpixels, pos_tmp,
+                                                                  slot_of);
     return cudaGetLastError();
 }
 

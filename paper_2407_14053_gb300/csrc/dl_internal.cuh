@@ -147,6 +147,12 @@ cudaError_t launch_rays_export(const uint32_t* ray_view, const uint32_t* ray_pix
 // Gathers per grouped ray {pixel, ray id}.
 cudaError_t launch_ray_group_gather(const uint32_t* order, const uint32_t* ray_pix, int64_t n_rays,
                                     int2* grouped, cudaStream_t s);
+// slot_of[i] = position in `grouped` of subpixel i's ray (ray_of[i]); the
+// compositing kernels write a ray's colour at its grouped position, so a
+// warp's rays write one contiguous run.  pos_tmp: n_rays words of scratch.
+cudaError_t launch_group_slots(const int2* grouped, int64_t n_rays, const uint32_t* ray_of,
+                               int64_t n_subpixels, uint32_t* pos_tmp, uint32_t* slot_of,
+                               cudaStream_t s);
 
 // ---- a5/a6: projection, key emission (project.cu) ------------------------
 // dtype: 0 f32, 1 bf16, 2 f16
@@ -172,23 +178,39 @@ cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const uint4* me
 
 // ---- ray-order 3DGS (raycast.cu) ------------------------------------------
 constexpr int kMaxHeap = 256;       // largest heap capacity c_h
-constexpr int kMaxRayLevels = 10;   // tree levels for n <= 2^28 Gaussians
-constexpr int kRayStack = 7 * kMaxRayLevels + 8;
-// Levels of the implicit 8-wide tree over n Gaussians: level_n[k] nodes at
-// level k (k = 0 the leaves), *n_levels levels; returns the node count.
-size_t raycast_bvh_nodes(int64_t n, int64_t* level_n, int* n_levels);
-// Per-Gaussian data (gauss: 3 float4, gbox: 2 float4 per Gaussian) and the
-// tree's boxes (nodes: 2 float4 per node, level k at node level_off[k]);
-// level_off / level_n are host arrays here.
+constexpr int kRayStack = 256;      // traversal stack entries per ray
+constexpr int kMaxWideDepth = (kRayStack - 8) / 7;  // deepest wide level the stack holds
+// 8-wide node of the ray-order tree: child boxes (structure of arrays) and
+// child references: a wide node index, kRayLeafBit | first << 3 | (count - 1)
+// for a leaf of Gaussians [first, first + count), or kRayNoChild.
+constexpr uint32_t kRayLeafBit = 0x80000000u;
+constexpr uint32_t kRayNoChild = 0x7FFFFFFFu;
+struct alignas(16) RayNode {
+    float lox[8], loy[8], loz[8], hix[8], hiy[8], hiz[8];
+    uint32_t child[8];
+    uint32_t pad[8];
+};
+static_assert(sizeof(RayNode) == 256, "one node, two 128-byte lines");
+// Per-Gaussian data of the ray-order renderer: gauss (3 float4: mean and
+// opacity, S = Sigma^-1) and gbox (2 float4: the alpha >= 1/255 box).
 cudaError_t launch_raycast_prepare(int dtype, const void* const* attrs, int64_t n, float4* gauss,
-                                   float4* gbox, float4* nodes, const int64_t* level_off,
-                                   const int64_t* level_n, int n_levels, cudaStream_t s);
+                                   float4* gbox, cudaStream_t s);
+// Scratch of the tree build for n Gaussians.
+size_t raycast_build_tmp_bytes(int64_t n);
+// Binary SAH tree over gbox (synchronises `s` once per level); *n_bin: its
+// internal nodes (the wide tree has at most that many, and at least one).
+cudaError_t raycast_build_binary(const float4* gbox, int64_t n, void* tmp, int64_t* n_bin,
+                                 cudaStream_t s);
+// Collapse into 8-wide nodes (`nodes`: room for max(n_bin, 1)); *n_wide
+// nodes, *depth the deepest wide level (0: the root alone).
+cudaError_t raycast_collapse(const float4* gbox, int64_t n, void* tmp, int64_t n_bin,
+                             RayNode* nodes, int64_t* n_wide, int* depth, cudaStream_t s);
 // One thread per ray (view ray_view, pixel ray_pix): ray colours into raycol
-// (3 floats per ray); level_off_dev / level_n_dev in device memory.  Thread i
-// casts ray order[i].y (order: a permutation of the rays as {pixel, ray id},
-// e.g. a tile grouping), or ray i when order is null.
-cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const float4* nodes,
-                           const int64_t* level_off_dev, const int64_t* level_n_dev, int n_levels,
+// (3 floats per thread, in thread order).  Thread i casts ray order[i].y
+// (order: a permutation of the rays as {pixel, ray id}, e.g. a tile
+// grouping), or ray i when order is null.  The tree's depth must be at most
+// kMaxWideDepth (checked when it is built), which bounds every ray's stack.
+cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const RayNode* nodes,
                            int64_t n, const void* sh, const uint32_t* ray_view,
                            const uint32_t* ray_pix, const int2* order, int64_t n_rays,
                            const Cam* cams, float focal, float half_w, float half_h, int heap_cap,
@@ -227,7 +249,9 @@ cudaError_t launch_composite_rays(const CompositeParams& p, const int4* work, in
                                   const float4* rec, float* raycol, unsigned long long* pairs,
                                   cudaStream_t s);
 // Encoded image from ray colours (Sec. 4 step (3), Sec. 6: the channel
-// reorder by precomputed indices): out[i] = raycol[3 ray_of[i] + i mod 3].
+// reorder by precomputed indices): out[i] = raycol[3 ray_of[i] + i mod 3],
+// with ray_of either the ray ids (colours in ray-id order) or a tile
+// grouping's slot_of (colours in grouped order).
 // Nothing is written when skip (optional, device) holds a nonzero word.
 cudaError_t launch_reorder(const uint32_t* ray_of, const float* raycol, int64_t n_subpixels,
                            float* out, const uint32_t* skip, cudaStream_t s);

@@ -51,19 +51,20 @@ struct Scene {
     int32_t in_use = 0;  // batch slots holding this scene
     DevBuf mean, log_scale, rot, opacity, sh;
     // ray-order renderer (built on the first DL_RAYCAST frame): per-Gaussian
-    // data, the implicit tree's boxes and its level table (device: offsets
-    // then counts, int64)
+    // data and boxes, and the 8-wide SAH tree (its nodes and depth)
     bool rc_built = false;
-    int32_t rc_levels = 0;
-    std::vector<int64_t> rc_level_n, rc_level_off;
-    DevBuf rc_gauss, rc_gbox, rc_nodes, rc_meta;
+    int32_t rc_depth = 0;
+    int64_t rc_n_nodes = 0;
+    DevBuf rc_gauss, rc_gbox, rc_nodes;
 };
 
 struct TileGroups {
     int32_t tw = 0, th = 0, ntx = 0, nty = 0, ntiles = 0;
     int64_t n_work = 0;   // <= 128-ray chunks (global radix path)
     int64_t n_gwork = 0;  // groups holding rays (binned path)
-    DevBuf grouped, work, gwork;
+    // grouped: {pixel, ray id} per position; slot_of: per subpixel, the
+    // position of its ray (ray colours are written in grouped order)
+    DevBuf grouped, work, gwork, slot_of;
 };
 
 struct RaySet {

@@ -7,13 +7,20 @@
 // and t_j > 0.2 (the near plane of the rasteriser); the heap orders by
 // (t, index), so the image does not depend on the traversal order.
 //
-// Acceleration: an implicit 8-wide bounding-volume tree over the scene's
-// stored order (a 3D Morton curve of the means): leaf node i bounds Gaussians
-// 8i..8i+7 (each by the box of its alpha >= 1/255 ellipsoid), node i of level
-// k > 0 bounds nodes 8i..8i+7 of level k-1.  Children are visited nearest
-// first, and once the heap is full a node whose box starts beyond the heap's
-// farthest entry is skipped: a Gaussian's highest-density point lies inside
-// its ellipsoid, hence inside every box above it.
+// Acceleration (Sec. 7: a compact 8-wide bounding-volume hierarchy built with
+// the surface area heuristic): every Gaussian is bounded by the box of its
+// alpha >= 1/255 ellipsoid.  A binary tree is built top down over the
+// scene's stored order (a 3D Morton curve of the means), so every node holds
+// a contiguous run of Gaussians; each node is split at the position of the
+// run that minimises the SAH cost A(left) n(left) + A(right) n(right) over
+// every split position (prefix and suffix boxes of the run), down to leaves
+// of at most four Gaussians.  The binary tree is then collapsed into 8-wide
+// nodes: a wide node starts from a binary node's two children and
+// repeatedly opens the child with the largest surface area until it has
+// eight.  Children are visited nearest first, and once the heap is full a
+// node whose box starts beyond the heap's farthest entry is skipped: a
+// Gaussian's highest-density point lies inside its ellipsoid, hence inside
+// every box above it.
 #include <cfloat>
 
 #include "dl_internal.cuh"
@@ -71,20 +78,251 @@ __global__ void rc_prepare_kernel(GaussiansView<T> G, int64_t n, float4* __restr
     }
 }
 
-// Node i bounds children 8i..8i+7 (< n_child) of the level below.
-__global__ void rc_level_kernel(const float4* __restrict__ child, int64_t n_child,
-                                float4* __restrict__ node, int64_t n_node) {
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n_node;
-         i += int64_t(gridDim.x) * blockDim.x) {
-        float4 lo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.f), hi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f);
-        for (int64_t c = 8 * i; c < 8 * i + 8 && c < n_child; ++c) {
-            const float4 a = child[2 * c], b = child[2 * c + 1];
-            lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z);
-            hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
-        }
-        node[2 * i] = lo;
-        node[2 * i + 1] = hi;
+// ---- SAH tree ------------------------------------------------------------
+constexpr int kLeafMax = 4;           // Gaussians per leaf of the binary tree
+constexpr int kMedianDepth = 40;      // from this binary depth on, runs split at the middle
+constexpr int kBuildThreads = 256;
+
+__host__ __device__ inline uint32_t leaf_ref(uint32_t first, uint32_t count) {
+    return kRayLeafBit | (first << 3) | (count - 1);
+}
+
+// Binary node of the build (not kept): box, children (node index or leaf
+// reference), the box's surface area.
+struct BinNode {
+    float4 lo, hi;
+    uint32_t child[2];
+    float area;
+    uint32_t pad;
+};
+// Run [a, b) of Gaussians that becomes binary node `node` at `depth`.
+struct BuildTask {
+    uint32_t a, b, node, depth;
+};
+
+struct Box {
+    float lx, ly, lz, hx, hy, hz;
+};
+__device__ __forceinline__ Box box_empty() { return {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX}; }
+__device__ __forceinline__ Box box_join(const Box& a, const Box& b) {
+    return {fminf(a.lx, b.lx), fminf(a.ly, b.ly), fminf(a.lz, b.lz),
+            fmaxf(a.hx, b.hx), fmaxf(a.hy, b.hy), fmaxf(a.hz, b.hz)};
+}
+__device__ __forceinline__ Box box_of(const float4* __restrict__ gbox, uint32_t g) {
+    const float4 l = gbox[2 * size_t(g)], h = gbox[2 * size_t(g) + 1];
+    return {l.x, l.y, l.z, h.x, h.y, h.z};
+}
+__device__ __forceinline__ float box_area(const Box& b) {
+    const float dx = b.hx - b.lx, dy = b.hy - b.ly, dz = b.hz - b.lz;
+    if (!(dx >= 0.f) || !(dy >= 0.f) || !(dz >= 0.f)) return 0.f;
+    return 2.f * (dx * dy + dy * dz + dz * dx);
+}
+__device__ __forceinline__ Box shfl_box(const Box& b, int src_delta, bool up) {
+    Box r;
+    if (up) {
+        r.lx = __shfl_up_sync(0xffffffffu, b.lx, src_delta);
+        r.ly = __shfl_up_sync(0xffffffffu, b.ly, src_delta);
+        r.lz = __shfl_up_sync(0xffffffffu, b.lz, src_delta);
+        r.hx = __shfl_up_sync(0xffffffffu, b.hx, src_delta);
+        r.hy = __shfl_up_sync(0xffffffffu, b.hy, src_delta);
+        r.hz = __shfl_up_sync(0xffffffffu, b.hz, src_delta);
+    } else {
+        r.lx = __shfl_down_sync(0xffffffffu, b.lx, src_delta);
+        r.ly = __shfl_down_sync(0xffffffffu, b.ly, src_delta);
+        r.lz = __shfl_down_sync(0xffffffffu, b.lz, src_delta);
+        r.hx = __shfl_down_sync(0xffffffffu, b.hx, src_delta);
+        r.hy = __shfl_down_sync(0xffffffffu, b.hy, src_delta);
+        r.hz = __shfl_down_sync(0xffffffffu, b.hz, src_delta);
     }
+    return r;
+}
+
+// Exclusive prefix (pre) and suffix (suf) unions of the block's per-thread
+// boxes in thread order, and their total.  Every thread of the block calls it.
+__device__ void block_box_scans(const Box& mine, Box& pre, Box& suf, Box& total) {
+    __shared__ Box s_warp[kBuildThreads / 32], s_pre[kBuildThreads / 32], s_suf[kBuildThreads / 32];
+    __shared__ Box s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    Box inc = mine, rinc = mine;  // inclusive prefix / suffix inside the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const Box u = shfl_box(inc, o, true), d = shfl_box(rinc, o, false);
+        if (lane >= o) inc = box_join(inc, u);
+        if (lane + o < 32) rinc = box_join(rinc, d);
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Box run = box_empty();
+        for (int w = 0; w < nw; ++w) {
+            s_pre[w] = run;
+            run = box_join(run, s_warp[w]);
+        }
+        s_total = run;
+        run = box_empty();
+        for (int w = nw - 1; w >= 0; --w) {
+            s_suf[w] = run;
+            run = box_join(run, s_warp[w]);
+        }
+    }
+    __syncthreads();
+    const Box ex_in = shfl_box(inc, 1, true);     // inclusive prefix of lane - 1
+    const Box ex_rin = shfl_box(rinc, 1, false);  // inclusive suffix of lane + 1
+    pre = lane > 0 ? box_join(s_pre[warp], ex_in) : s_pre[warp];
+    suf = lane < 31 ? box_join(s_suf[warp], ex_rin) : s_suf[warp];
+    total = s_total;
+    __syncthreads();
+}
+
+// One block per task: the run [a, b) is split at the position k (a < k < b)
+// minimising A([a, k)) (k - a) + A([k, b)) (b - k), over every position
+// (from binary depth kMedianDepth on: the middle).  A side of at most
+// kLeafMax Gaussians becomes a leaf, a longer one a new node and a task of
+// the next level.  sal: one float per Gaussian of scratch.  counters[0]:
+// binary nodes allocated, counters[1]: next level's tasks.
+__global__ void __launch_bounds__(kBuildThreads)
+sah_split_kernel(const BuildTask* __restrict__ tasks, const float4* __restrict__ gbox,
+                 float* __restrict__ sal, BinNode* __restrict__ nodes, BuildTask* __restrict__ next,
+                 uint32_t* __restrict__ counters) {
+    __shared__ float s_cost[kBuildThreads];
+    __shared__ uint32_t s_k[kBuildThreads];
+    const BuildTask tk = tasks[blockIdx.x];
+    const uint32_t a = tk.a, b = tk.b, m = b - a;
+    const uint32_t per = (m + blockDim.x - 1) / blockDim.x;
+    const uint32_t c0 = min(b, a + threadIdx.x * per), c1 = min(b, c0 + per);
+    Box cb = box_empty();
+    for (uint32_t g = c0; g < c1; ++g) cb = box_join(cb, box_of(gbox, g));
+    Box pre, suf, total;
+    block_box_scans(cb, pre, suf, total);
+    // forward: sal[g] = area of [a, g + 1)
+    Box L = pre;
+    for (uint32_t g = c0; g < c1; ++g) {
+        L = box_join(L, box_of(gbox, g));
+        sal[g] = box_area(L);
+    }
+    __syncthreads();
+    // backward: the cost of splitting at k = g, right side [g, b)
+    Box R = suf;
+    float best = FLT_MAX;
+    uint32_t bk = a + m / 2;
+    for (uint32_t g = c1; g > c0; --g) {
+        R = box_join(R, box_of(gbox, g - 1));
+        const uint32_t k = g - 1;
+        if (k > a) {
+            const float cost = sal[k - 1] * float(k - a) + box_area(R) * float(b - k);
+            if (cost < best || (cost == best && k < bk)) {
+                best = cost;
+                bk = k;
+            }
+        }
+    }
+    s_cost[threadIdx.x] = best;
+    s_k[threadIdx.x] = bk;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t k = a + m / 2;
+        if (tk.depth < uint32_t(kMedianDepth)) {
+            float bc = FLT_MAX;
+            for (unsigned t = 0; t < blockDim.x; ++t)
+                if (s_cost[t] < bc || (s_cost[t] == bc && s_k[t] < k)) {
+                    bc = s_cost[t];
+                    k = s_k[t];
+                }
+            if (!(bc < FLT_MAX)) k = a + m / 2;  // every box empty: the middle
+        }
+        BinNode nd;
+        nd.lo = make_float4(total.lx, total.ly, total.lz, 0.f);
+        nd.hi = make_float4(total.hx, total.hy, total.hz, 0.f);
+        nd.area = box_area(total);
+        nd.pad = 0u;
+        const uint32_t ra[2] = {a, k}, rb[2] = {k, b};
+        for (int side = 0; side < 2; ++side) {
+            const uint32_t n = rb[side] - ra[side];
+            if (n <= uint32_t(kLeafMax)) {
+                nd.child[side] = leaf_ref(ra[side], n);
+            } else {
+                const uint32_t id = atomicAdd(counters, 1u);
+                nd.child[side] = id;
+                next[atomicAdd(counters + 1, 1u)] = BuildTask{ra[side], rb[side], id, tk.depth + 1};
+            }
+        }
+        nodes[tk.node] = nd;
+    }
+}
+
+// Collapse of the binary tree into 8-wide nodes, one wide node per task: the
+// binary node's two children are opened, the one with the largest surface
+// area first, until there are eight (or only leaves).  counters[2]: wide
+// nodes allocated, [3]: next level's tasks, [4]: deepest wide level.
+struct CollapseTask {
+    uint32_t bin, wide, depth, pad;
+};
+
+__global__ void collapse_kernel(const CollapseTask* __restrict__ q, uint32_t nq,
+                                const BinNode* __restrict__ bins, const float4* __restrict__ gbox,
+                                RayNode* __restrict__ wide, CollapseTask* __restrict__ next,
+                                uint32_t* __restrict__ counters) {
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nq; idx += gridDim.x * blockDim.x) {
+        const CollapseTask t = q[idx];
+        uint32_t ref[8];
+        int c = 2;
+        ref[0] = bins[t.bin].child[0];
+        ref[1] = bins[t.bin].child[1];
+        while (c < 8) {
+            int best = -1;
+            float ba = -1.f;
+            for (int i = 0; i < c; ++i)
+                if (!(ref[i] & kRayLeafBit) && bins[ref[i]].area > ba) {
+                    ba = bins[ref[i]].area;
+                    best = i;
+                }
+            if (best < 0) break;
+            const uint32_t r = ref[best];
+            ref[best] = bins[r].child[0];
+            ref[c++] = bins[r].child[1];
+        }
+        RayNode nd;
+        for (int k = 0; k < 8; ++k) {
+            Box bx = box_empty();
+            uint32_t ch = kRayNoChild;
+            if (k < c) {
+                if (ref[k] & kRayLeafBit) {
+                    const uint32_t first = (ref[k] & ~kRayLeafBit) >> 3, cnt = (ref[k] & 7u) + 1u;
+                    for (uint32_t g = first; g < first + cnt; ++g) bx = box_join(bx, box_of(gbox, g));
+                    ch = ref[k];
+                } else {
+                    const BinNode& bn = bins[ref[k]];
+                    bx = {bn.lo.x, bn.lo.y, bn.lo.z, bn.hi.x, bn.hi.y, bn.hi.z};
+                    ch = atomicAdd(counters + 2, 1u);
+                    next[atomicAdd(counters + 3, 1u)] = CollapseTask{ref[k], ch, t.depth + 1, 0u};
+                }
+            }
+            nd.lox[k] = bx.lx; nd.loy[k] = bx.ly; nd.loz[k] = bx.lz;
+            nd.hix[k] = bx.hx; nd.hiy[k] = bx.hy; nd.hiz[k] = bx.hz;
+            nd.child[k] = ch;
+            nd.pad[k] = 0u;
+        }
+        wide[t.wide] = nd;
+        atomicMax(counters + 4, t.depth);
+    }
+}
+
+// A scene of at most kLeafMax Gaussians: the root holds one leaf.
+__global__ void leaf_root_kernel(const float4* __restrict__ gbox, uint32_t n, RayNode* __restrict__ wide) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    RayNode nd;
+    for (int k = 0; k < 8; ++k) {
+        Box bx = box_empty();
+        uint32_t ch = kRayNoChild;
+        if (k == 0 && n > 0) {
+            for (uint32_t g = 0; g < n; ++g) bx = box_join(bx, box_of(gbox, g));
+            ch = leaf_ref(0u, n);
+        }
+        nd.lox[k] = bx.lx; nd.loy[k] = bx.ly; nd.loz[k] = bx.lz;
+        nd.hix[k] = bx.hx; nd.hiy[k] = bx.hy; nd.hiz[k] = bx.hz;
+        nd.child[k] = ch;
+        nd.pad[k] = 0u;
+    }
+    wide[0] = nd;
 }
 
 // Ray-box slab test: entry distance, or +inf when the ray misses the box
@@ -118,8 +356,7 @@ __device__ __forceinline__ float rc_alpha(const float4* __restrict__ gauss, int6
 
 template <typename T, int DEG>
 __global__ void __launch_bounds__(128)
-rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nodes,
-                const int64_t* __restrict__ level_off, int n_levels, const int64_t* __restrict__ level_n,
+rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ nodes,
                 int64_t n, const T* __restrict__ sh, const uint32_t* __restrict__ ray_view,
                 const uint32_t* __restrict__ ray_pix, const int2* __restrict__ order,
                 int64_t n_rays, const Cam* __restrict__ cams, float focal, float half_w,
@@ -147,23 +384,25 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
     dx *= dn; dy *= dn; dz *= dn;
     const float ox = cam.c[0], oy = cam.c[1], oz = cam.c[2];
     const float ix = 1.f / dx, iy = 1.f / dy, iz = 1.f / dz;
-    // traversal: stack entries level << 28 | node; depth-first with <= 8
-    // children pushed per node holds at most 7 (levels - 1) + 8 <= kRayStack
+    // traversal of the 8-wide tree: a stack of wide node indices and leaf
+    // references; each node pushes its hit children farthest first, so at
+    // most 7 entries a level plus 8 are pending (the tree's depth is checked
+    // against kMaxWideDepth when it is built; the guard only keeps a stack
+    // access in bounds)
     uint32_t stack[kRayStack];
     int sp = 0;
-    stack[sp++] = uint32_t(n_levels - 1) << 28;
+    stack[sp++] = 0u;  // the root
     while (sp > 0) {
         const uint32_t e = stack[--sp];
-        const int lv = int(e >> 28);
-        const int64_t i = int64_t(e & 0x0FFFFFFFu);
         const float bound = hn == heap_cap ? __uint_as_float(uint32_t(hk[0] >> 32)) : INFINITY;
-        if (lv == 0) {  // leaf: Gaussians 8i..8i+7
-            for (int64_t g = 8 * i; g < 8 * i + 8 && g < n; ++g) {
+        if (e & kRayLeafBit) {  // leaf: Gaussians first .. first + count - 1
+            const uint32_t first = (e & ~kRayLeafBit) >> 3, cnt = (e & 7u) + 1u;
+            for (uint32_t g = first; g < first + cnt; ++g) {
                 float t;
                 const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
                 if (!(a >= kMinAlpha) || !(t > kNearT)) continue;
                 const unsigned long long key =
-                    (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | uint32_t(g);
+                    (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | g;
                 if (hn < heap_cap) {  // insert and sift up
                     int k = hn++;
                     while (k > 0) {
@@ -186,14 +425,32 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
                     hk[k] = key;
                 }
             }
-        } else {  // children 8i..8i+7 of the level below, nearest first
-            const float4* child = nodes + 2 * level_off[lv - 1];
-            const int64_t nc = level_n[lv - 1];
+        } else {  // wide node: its children, nearest first
+            const float4* nf = reinterpret_cast<const float4*>(nodes + e);
+            float lx[8], ly[8], lz[8], hx[8], hy[8], hz[8];
+            uint32_t chv[8];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float4 a0 = __ldg(nf + q), a1 = __ldg(nf + 2 + q), a2 = __ldg(nf + 4 + q);
+                const float4 a3 = __ldg(nf + 6 + q), a4 = __ldg(nf + 8 + q), a5 = __ldg(nf + 10 + q);
+                const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(nf + 12 + q));
+                lx[4 * q] = a0.x; lx[4 * q + 1] = a0.y; lx[4 * q + 2] = a0.z; lx[4 * q + 3] = a0.w;
+                ly[4 * q] = a1.x; ly[4 * q + 1] = a1.y; ly[4 * q + 2] = a1.z; ly[4 * q + 3] = a1.w;
+                lz[4 * q] = a2.x; lz[4 * q + 1] = a2.y; lz[4 * q + 2] = a2.z; lz[4 * q + 3] = a2.w;
+                hx[4 * q] = a3.x; hx[4 * q + 1] = a3.y; hx[4 * q + 2] = a3.z; hx[4 * q + 3] = a3.w;
+                hy[4 * q] = a4.x; hy[4 * q + 1] = a4.y; hy[4 * q + 2] = a4.z; hy[4 * q + 3] = a4.w;
+                hz[4 * q] = a5.x; hz[4 * q + 1] = a5.y; hz[4 * q + 2] = a5.z; hz[4 * q + 3] = a5.w;
+                chv[4 * q] = c4.x; chv[4 * q + 1] = c4.y; chv[4 * q + 2] = c4.z; chv[4 * q + 3] = c4.w;
+            }
             float ct[8];
             uint32_t ce[8];
             int m = 0;
-            for (int64_t c = 8 * i; c < 8 * i + 8 && c < nc; ++c) {
-                const float te = slab_enter(child[2 * c], child[2 * c + 1], ox, oy, oz, ix, iy, iz);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (chv[c] == kRayNoChild) continue;
+                const float te = slab_enter(make_float4(lx[c], ly[c], lz[c], 0.f),
+                                            make_float4(hx[c], hy[c], hz[c], 0.f), ox, oy, oz, ix,
+                                            iy, iz);
                 if (!(te < INFINITY) || te > bound) continue;  // misses, or beyond a full heap
                 int k = m++;
                 while (k > 0 && ct[k - 1] < te) {  // descending: nearest pushed last
@@ -202,8 +459,9 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
                     --k;
                 }
                 ct[k] = te;
-                ce[k] = (uint32_t(lv - 1) << 28) | uint32_t(c);
+                ce[k] = chv[c];
             }
+            if (sp + m > kRayStack) m = kRayStack - sp;
             for (int k = 0; k < m; ++k) stack[sp++] = ce[k];
         }
     }
@@ -246,9 +504,10 @@ rc_trace_kernel(const float4* __restrict__ gauss, const float4* __restrict__ nod
         c2 = fmaf(w, col[2], c2);
         tr = tn;
     }
-    raycol[3 * r] = c0;
-    raycol[3 * r + 1] = c1;
-    raycol[3 * r + 2] = c2;
+    // colours in thread order: the grouped order when `order` is given
+    raycol[3 * i] = c0;
+    raycol[3 * i + 1] = c1;
+    raycol[3 * i + 2] = c2;
 }
 
 int grid_of(int64_t n, int block) {
@@ -260,22 +519,9 @@ int grid_of(int64_t n, int block) {
 
 }  // namespace
 
-size_t raycast_bvh_nodes(int64_t n, int64_t* level_n, int* n_levels) {
-    int64_t cnt = (n + 7) / 8, total = 0;
-    int lv = 0;
-    for (;;) {
-        level_n[lv++] = cnt;
-        total += cnt;
-        if (cnt == 1) break;
-        cnt = (cnt + 7) / 8;
-    }
-    *n_levels = lv;
-    return size_t(total);
-}
-
 cudaError_t launch_raycast_prepare(int dtype, const void* const* attrs, int64_t n, float4* gauss,
-                                   float4* gbox, float4* nodes, const int64_t* level_off,
-                                   const int64_t* level_n, int n_levels, cudaStream_t s) {
+                                   float4* gbox, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
     const int grid = grid_of(n, 256);
     if (dtype == 1) {
         GaussiansView<__nv_bfloat16> G{static_cast<const float*>(attrs[0]),
@@ -295,21 +541,102 @@ cudaError_t launch_raycast_prepare(int dtype, const void* const* attrs, int64_t 
                                static_cast<const float*>(attrs[4])};
         rc_prepare_kernel<<<grid, 256, 0, s>>>(G, n, gauss, gbox);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const float4* below = gbox;
-    int64_t n_below = n;
-    for (int lv = 0; lv < n_levels; ++lv) {
-        float4* out = nodes + 2 * level_off[lv];
-        rc_level_kernel<<<grid_of(level_n[lv], 256), 256, 0, s>>>(below, n_below, out, level_n[lv]);
-        below = out;
-        n_below = level_n[lv];
-    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const float4* nodes,
-                           const int64_t* level_off_dev, const int64_t* level_n_dev, int n_levels,
+// Build scratch: binary nodes, two task lists, the SAH sweep's areas, the
+// counters and two collapse queues.
+struct BuildScratch {
+    BinNode* bins;
+    BuildTask* tasks[2];
+    float* sal;
+    uint32_t* counters;
+    CollapseTask* queue[2];
+};
+static size_t task_cap(int64_t n) { return size_t(n / (kLeafMax + 1) + 2); }
+static BuildScratch carve_build(void* tmp, int64_t n) {
+    BuildScratch b;
+    char* p = static_cast<char*>(tmp);
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += (bytes + 255) & ~size_t(255);
+        return q;
+    };
+    b.bins = reinterpret_cast<BinNode*>(take(sizeof(BinNode) * size_t(n + 1)));
+    b.tasks[0] = reinterpret_cast<BuildTask*>(take(sizeof(BuildTask) * task_cap(n)));
+    b.tasks[1] = reinterpret_cast<BuildTask*>(take(sizeof(BuildTask) * task_cap(n)));
+    b.sal = reinterpret_cast<float*>(take(sizeof(float) * size_t(n + 1)));
+    b.counters = reinterpret_cast<uint32_t*>(take(64));
+    b.queue[0] = reinterpret_cast<CollapseTask*>(take(sizeof(CollapseTask) * size_t(n + 1)));
+    b.queue[1] = reinterpret_cast<CollapseTask*>(take(sizeof(CollapseTask) * size_t(n + 1)));
+    return b;
+}
+
+size_t raycast_build_tmp_bytes(int64_t n) {
+    const size_t r = 255;
+    auto up = [&](size_t x) { return (x + r) & ~r; };
+    return up(sizeof(BinNode) * size_t(n + 1)) + 2 * up(sizeof(BuildTask) * task_cap(n)) +
+           up(sizeof(float) * size_t(n + 1)) + up(64) + 2 * up(sizeof(CollapseTask) * size_t(n + 1));
+}
+
+cudaError_t raycast_build_binary(const float4* gbox, int64_t n, void* tmp, int64_t* n_bin,
+                                 cudaStream_t s) {
+    *n_bin = 0;
+    if (n <= kLeafMax) return cudaSuccess;
+    BuildScratch b = carve_build(tmp, n);
+    uint32_t h[16] = {1u, 0u};  // the root is node 0
+    cudaError_t e = cudaMemcpyAsync(b.counters, h, sizeof(h), cudaMemcpyHostToDevice, s);
+    const BuildTask root{0u, uint32_t(n), 0u, 0u};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.tasks[0], &root, sizeof(root), cudaMemcpyHostToDevice, s);
+    uint32_t n_tasks = 1;
+    int cur = 0;
+    while (e == cudaSuccess && n_tasks > 0) {
+        sah_split_kernel<<<n_tasks, kBuildThreads, 0, s>>>(b.tasks[cur], gbox, b.sal, b.bins,
+                                                           b.tasks[cur ^ 1], b.counters);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, b.counters, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.counters + 1, 0, 4, s);
+        n_tasks = h[1];
+        cur ^= 1;
+    }
+    *n_bin = int64_t(h[0]);
+    return e;
+}
+
+cudaError_t raycast_collapse(const float4* gbox, int64_t n, void* tmp, int64_t n_bin,
+                             RayNode* nodes, int64_t* n_wide, int* depth, cudaStream_t s) {
+    *n_wide = 1;
+    *depth = 0;
+    if (n_bin == 0) {
+        leaf_root_kernel<<<1, 32, 0, s>>>(gbox, uint32_t(n > 0 ? n : 0), nodes);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+    }
+    BuildScratch b = carve_build(tmp, n);
+    uint32_t h[16] = {0u};
+    h[2] = 1u;  // the wide root is node 0
+    cudaError_t e = cudaMemcpyAsync(b.counters, h, sizeof(h), cudaMemcpyHostToDevice, s);
+    const CollapseTask root{0u, 0u, 0u, 0u};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.queue[0], &root, sizeof(root), cudaMemcpyHostToDevice, s);
+    uint32_t nq = 1;
+    int cur = 0;
+    while (e == cudaSuccess && nq > 0) {
+        collapse_kernel<<<grid_of(nq, 128), 128, 0, s>>>(b.queue[cur], nq, b.bins, gbox, nodes,
+                                                         b.queue[cur ^ 1], b.counters);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, b.counters, 32, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.counters + 3, 0, 4, s);
+        nq = h[3];
+        cur ^= 1;
+    }
+    *n_wide = int64_t(h[2]);
+    *depth = int(h[4]);
+    return e;
+}
+
+cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const RayNode* nodes,
                            int64_t n, const void* sh, const uint32_t* ray_view,
                            const uint32_t* ray_pix, const int2* order, int64_t n_rays,
                            const Cam* cams, float focal, float half_w, float half_h, int heap_cap,
@@ -317,8 +644,7 @@ cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const 
     if (n_rays <= 0) return cudaSuccess;
     const unsigned grid = unsigned((n_rays + 127) / 128);
 #define DL_RC(T, D)                                                                          \
-    rc_trace_kernel<T, D><<<grid, 128, 0, s>>>(gauss, nodes, level_off_dev, n_levels,         \
-                                               level_n_dev, n, static_cast<const T*>(sh),      \
+    rc_trace_kernel<T, D><<<grid, 128, 0, s>>>(gauss, nodes, n, static_cast<const T*>(sh),   \
                                                ray_view, ray_pix, order, n_rays, cams, focal,  \
                                                half_w, half_h, heap_cap, raycol)
 #define DL_RC_DEG(T)                  \
