@@ -770,8 +770,8 @@ def main():
         fps_rc = reduce_sum(k_rc, world, dev) / (ms_rc / 1e3)
         raycast = {"frames_per_s": fps_rc, "ms_per_frame": ms_rc / k_rc, "heap_capacity": 128,
                    "steps": k_rc, "speedup_directl_over": fps / fps_rc,
-                   "note": "one thread per ray (rays grouped by view and tile), implicit 8-wide "
-                           "tree over the Morton-ordered scene"}
+                   "note": "one thread per ray (rays grouped by view and tile), 8-wide SAH tree "
+                           "over the Morton-ordered scene"}
 
     # ---- end to end through the C ABI with host (pinned) frames ----
     # value: frames delivered to host memory by dl_render_frame_async_host,
