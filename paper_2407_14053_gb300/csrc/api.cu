@@ -1166,10 +1166,10 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     if (binned) {
         // ---- binned keys, sorted per tile in shared memory while compositing ----
         DL_CK(W.gfill.reserve(4 * size_t(ngroups)), "alloc");
-        DL_CK(cudaMemsetAsync(W.gfill.p, 0, 4 * size_t(ngroups), s), "memset");
+        DL_CK(cudaMemcpyAsync(W.gfill.p, W.gstart.p, 4 * size_t(ngroups), cudaMemcpyDeviceToDevice, s),
+              "cursors");
         DL_CK(mark(3), "event");
-        DL_CK(launch_emit_binned(pp, nv, W.meta.as<uint4>(),
-                                 W.gstart.as<uint32_t>(), W.gfill.as<uint32_t>(),
+        DL_CK(launch_emit_binned(pp, nv, W.meta.as<uint4>(), W.gfill.as<uint32_t>(),
                                  W.keys[0].as<unsigned long long>(), on_device ? d_nkeys : nullptr,
                                  key_cap, on_device ? d_status : nullptr, s),
               "emit binned");

@@ -167,7 +167,9 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
         uint32_t* gstart = b->at<uint32_t>(z.o_gstart);
         DL_CK(launch_exclusive_scan(gcount, gstart, z.ngroups + 1, nullptr, b->scan_tmp.p, s),
               "group scan");
-        DL_CK(launch_emit_binned(z.pp, nv, po.meta, gstart, gfill,
+        DL_CK(cudaMemcpyAsync(gfill, gstart, 4 * size_t(z.ngroups), cudaMemcpyDeviceToDevice, s),
+              "cursors");
+        DL_CK(launch_emit_binned(z.pp, nv, po.meta, gfill,
                                  b->at<unsigned long long>(z.o_keys), gstart + z.ngroups,
                                  uint32_t(z.key_cap), fd.status, s),
               "emit binned");

@@ -162,14 +162,14 @@ cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectPar
                            const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s);
 // Keys depth << 32 | Gaussian << 4 (Gaussians < 2^28; the low nibble is left
 // for the block class's quadrant bits) into their group's slice
-// [gstart[g], gstart[g+1])
-// (gfill zeroed by the caller).
+// [gstart[g], gstart[g+1]): cursor[g] holds gstart[g] at the launch (a copy
+// made by the caller) and is advanced by atomics.
 // total_keys (optional) = gstart + n_groups: when it exceeds key_cap no key is
 // written and *status |= 1.
 cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const uint4* meta,
-                               const uint32_t* gstart, uint32_t* gfill,
-                               unsigned long long* keys, const uint32_t* total_keys,
-                               uint32_t key_cap, uint32_t* status, cudaStream_t s);
+                               uint32_t* cursor, unsigned long long* keys,
+                               const uint32_t* total_keys, uint32_t key_cap, uint32_t* status,
+                               cudaStream_t s);
 // tiles touched per (view, Gaussian) out of the metadata (for the radix path's scan)
 cudaError_t launch_meta_counts(const uint4* meta, int64_t n, uint32_t* count, cudaStream_t s);
 cudaError_t launch_emit_keys(const ProjectParams& p, int32_t nv, const uint4* meta,

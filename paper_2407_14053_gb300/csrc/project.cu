@@ -29,11 +29,21 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
+// SH coefficients of a thread's Gaussian, staged once in shared memory (its
+// own column of float4, so a warp's loads are conflict-free) and read per
+// visible view: this keeps them out of registers, and the kernel at 64
+// registers and four blocks per SM.
+template <int DEG>
+constexpr int sh_float4() { return (3 * (DEG + 1) * (DEG + 1) + 3) / 4; }
+constexpr int kProjectThreads = 256;
+
 template <typename T, int DEG>
-__global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, ProjectParams p,
+__global__ void __launch_bounds__(kProjectThreads, 4) project_kernel(GaussiansView<T> G, ProjectParams p,
                                                       const Cam* __restrict__ cams, int32_t nv,
                                                       ProjectOut out) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
+    constexpr int NF = 3 * NC, NF4 = sh_float4<DEG>();
+    extern __shared__ float4 s_sh[];  // [NF4][kProjectThreads]
     const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     unsigned long long my_total = 0;
     uint32_t my_visible = 0;
@@ -64,11 +74,13 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
         const float log2o = log2f(opac);
         const bool visible_alpha = opac * 255.f > 1.f;
         const float K = visible_alpha ? 2.f * logf(255.f * opac) : 0.f;
-        float sh[NC][3];
 #pragma unroll
-        for (int i = 0; i < NC; ++i)
+        for (int q = 0; q < NF4; ++q) {
+            float v[4];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sh[i][c] = to_f(G.sh[(g * NC + i) * 3 + c]);
+            for (int k = 0; k < 4; ++k) v[k] = 4 * q + k < NF ? to_f(G.sh[g * NF + 4 * q + k]) : 0.f;
+            s_sh[q * kProjectThreads + threadIdx.x] = make_float4(v[0], v[1], v[2], v[3]);
+        }
 
         // warps start at different views (and wrap around), so warps in
         // flight add to the counters of different views' tiles
@@ -149,14 +161,22 @@ __global__ void __launch_bounds__(256, 3) project_kernel(GaussiansView<T> G, Pro
                         dx *= dn; dy *= dn; dz *= dn;
                         float Y[16];
                         sh_basis<DEG>(dx, dy, dz, Y);
+                        // coefficient f = 3 i + c, in order of f: every
+                        // channel sums its terms in order of i
+                        float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int q = 0; q < NF4; ++q) {
+                            const float4 w4 = s_sh[q * kProjectThreads + threadIdx.x];
+                            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const int f = 4 * q + k;
+                                if (f < NF) acc[f % 3] = fmaf(Y[f / 3], w[k], acc[f % 3]);
+                            }
+                        }
                         float col[3];
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            float acc = 0.f;
-#pragma unroll
-                            for (int i = 0; i < NC; ++i) acc = fmaf(Y[i], sh[i][c], acc);
-                            col[c] = fmaxf(acc + 0.5f, 0.f);
-                        }
+                        for (int c = 0; c < 3; ++c) col[c] = fmaxf(acc[c] + 0.5f, 0.f);
                         float4* rec = out.rec + kRecordFloat4 * e;
                         float clo, chi;
                         pack_rgb(col[0], col[1], col[2], clo, chi);
@@ -231,8 +251,10 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const uint4* __res
 // they never decide the order.
 constexpr int kEmitRounds = 2;
 
+// cursor[g] starts at the group's first slot (a copy of gstart), so the
+// cursor atomic returns a key's absolute slot.
 __global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, int32_t nv, const uint4* __restrict__ meta,
-                                   const uint32_t* __restrict__ gstart, uint32_t* __restrict__ gfill,
+                                   uint32_t* __restrict__ cursor,
                                    unsigned long long* __restrict__ keys,
                                    const uint32_t* __restrict__ total_keys, uint32_t key_cap,
                                    uint32_t* __restrict__ status) {
@@ -313,7 +335,7 @@ __global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, in
         // kEmitRounds rounds of 32 pairs at once: their cursor atomics are in
         // flight together (the kernel waits on the atomics' round trips)
         for (uint32_t r0 = 0; r0 < n_pairs; r0 += 32 * kEmitRounds) {
-            uint32_t grp[kEmitRounds], start[kEmitRounds], base[kEmitRounds];
+            uint32_t grp[kEmitRounds], base[kEmitRounds];
             unsigned long long key[kEmitRounds];
             unsigned peers[kEmitRounds];
             bool ok[kEmitRounds];
@@ -324,20 +346,19 @@ __global__ void __launch_bounds__(256, 6) emit_binned_kernel(ProjectParams p, in
                 if (r0 + 32u * u < n_pairs) {  // warp-uniform
                     ok[u] = pair_of(r0 + 32u * u + uint32_t(lane), grp[u], key[u]);
                     peers[u] = __match_any_sync(0xffffffffu, ok[u] ? grp[u] : 0xFFFFFFFFu);
-                    start[u] = ok[u] ? gstart[grp[u]] : 0u;
                 }
             }
 #pragma unroll
             for (int u = 0; u < kEmitRounds; ++u) {
                 base[u] = 0u;
                 if (ok[u] && lane == __ffs(peers[u]) - 1)
-                    base[u] = atomicAdd(gfill + grp[u], uint32_t(__popc(peers[u])));
+                    base[u] = atomicAdd(cursor + grp[u], uint32_t(__popc(peers[u])));
             }
 #pragma unroll
             for (int u = 0; u < kEmitRounds; ++u) {
                 if (r0 + 32u * u < n_pairs) {
                     const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
-                    if (ok[u]) keys[start[u] + b + __popc(peers[u] & lt)] = key[u];
+                    if (ok[u]) keys[b + __popc(peers[u] & lt)] = key[u];
                 }
             }
         }
@@ -365,13 +386,14 @@ static cudaError_t launch_project_t(const void* const* attrs, const ProjectParam
     G.rot = static_cast<const T*>(attrs[2]);
     G.opacity_logit = static_cast<const T*>(attrs[3]);
     G.sh = static_cast<const T*>(attrs[4]);
-    const int block = 256;
+    const int block = kProjectThreads;
     const int64_t grid = (p.n + block - 1) / block;
+    auto smem = [](int deg) { return size_t(16) * kProjectThreads * size_t((3 * (deg + 1) * (deg + 1) + 3) / 4); };
     switch (p.sh_degree) {
-        case 0: project_kernel<T, 0><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
-        case 1: project_kernel<T, 1><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
-        case 2: project_kernel<T, 2><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
-        default: project_kernel<T, 3><<<unsigned(grid), block, 0, s>>>(G, p, cams, nv, out); break;
+        case 0: project_kernel<T, 0><<<unsigned(grid), block, smem(0), s>>>(G, p, cams, nv, out); break;
+        case 1: project_kernel<T, 1><<<unsigned(grid), block, smem(1), s>>>(G, p, cams, nv, out); break;
+        case 2: project_kernel<T, 2><<<unsigned(grid), block, smem(2), s>>>(G, p, cams, nv, out); break;
+        default: project_kernel<T, 3><<<unsigned(grid), block, smem(3), s>>>(G, p, cams, nv, out); break;
     }
     return cudaGetLastError();
 }
@@ -384,14 +406,14 @@ cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectPar
 }
 
 cudaError_t launch_emit_binned(const ProjectParams& p, int32_t nv, const uint4* meta,
-                               const uint32_t* gstart, uint32_t* gfill,
+                               uint32_t* cursor,
                                unsigned long long* keys, const uint32_t* total_keys,
                                uint32_t key_cap, uint32_t* status, cudaStream_t s) {
     const int64_t total = int64_t(nv) * p.n;
     int64_t grid = (total + 255) / 256;
     const int64_t cap = int64_t(num_sms()) * 32;
     if (grid > cap) grid = cap;
-    emit_binned_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, meta, gstart, gfill, keys,
+    emit_binned_kernel<<<unsigned(grid > 0 ? grid : 1), 256, 0, s>>>(p, nv, meta, cursor, keys,
                                                                      total_keys, key_cap, status);
     return cudaGetLastError();
 }

@@ -325,18 +325,6 @@ __global__ void leaf_root_kernel(const float4* __restrict__ gbox, uint32_t n, Ra
     wide[0] = nd;
 }
 
-// Ray-box slab test: entry distance, or +inf when the ray misses the box
-// (or the box lies behind the near plane).
-__device__ __forceinline__ float slab_enter(const float4& lo, const float4& hi, float ox, float oy,
-                                            float oz, float ix, float iy, float iz) {
-    const float tx0 = (lo.x - ox) * ix, tx1 = (hi.x - ox) * ix;
-    const float ty0 = (lo.y - oy) * iy, ty1 = (hi.y - oy) * iy;
-    const float tz0 = (lo.z - oz) * iz, tz1 = (hi.z - oz) * iz;
-    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
-    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
-    return (tn <= tf && tf > kNearT) ? tn : INFINITY;
-}
-
 // Highest-density point and alpha of Gaussian g along the ray.
 __device__ __forceinline__ float rc_alpha(const float4* __restrict__ gauss, int64_t g, float ox,
                                           float oy, float oz, float dx, float dy, float dz, float& t) {
@@ -354,24 +342,67 @@ __device__ __forceinline__ float rc_alpha(const float4* __restrict__ gauss, int6
     return fminf(0.99f, a.w * __expf(-0.5f * q));
 }
 
+constexpr int kTraceThreads = 128;
+constexpr int kTraceWarps = kTraceThreads / 32;
+constexpr int kHeapTop = 16;  // heap slots 0..15 (its top four levels) in shared memory
+
+// A ray's entry into a box (+inf when it misses the box or the box lies
+// behind the near plane).
+__device__ __forceinline__ float slab_enter(const float4& lo, const float4& hi, float ox, float oy,
+                                            float oz, float ix, float iy, float iz) {
+    const float tx0 = (lo.x - ox) * ix, tx1 = (hi.x - ox) * ix;
+    const float ty0 = (lo.y - oy) * iy, ty1 = (hi.y - oy) * iy;
+    const float tz0 = (lo.z - oz) * iz, tz1 = (hi.z - oz) * iz;
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+    return (tn <= tf && tf > kNearT) ? tn : INFINITY;
+}
+
+// A ray's max-heap of its c_h nearest intersections: slots below kHeapTop
+// (the levels every insertion and removal passes through) in shared memory,
+// the rest in the thread's local memory.
+struct RayHeap {
+    unsigned long long* top;  // slot k < kHeapTop at top[32 k]
+    unsigned long long* rest;  // slot k >= kHeapTop at rest[k - kHeapTop]
+    __device__ __forceinline__ unsigned long long get(int k) const {
+        return k < kHeapTop ? top[32 * k] : rest[k - kHeapTop];
+    }
+    __device__ __forceinline__ void set(int k, unsigned long long v) const {
+        if (k < kHeapTop) top[32 * k] = v;
+        else rest[k - kHeapTop] = v;
+    }
+};
+
+// Traversal of the 8-wide tree is by the whole warp: its rays share a camera
+// centre and nearly a direction, so they need nearly the same nodes.  A
+// warp-shared stack holds {node or leaf reference, the lanes whose ray hit
+// its box}; a popped node is loaded once for the warp, every lane tests its
+// ray against the eight child boxes (a child beyond the lane's full heap does
+// not count as hit), and the children hit by any lane are pushed farthest
+// first by their nearest entry over those lanes.  A leaf is tested by the
+// lanes that hit it.  At most 7 entries a level plus 8 are pending (the
+// tree's depth is checked against kMaxWideDepth when it is built; the guard
+// only keeps the stack in bounds).  Every lane reaches every warp-wide
+// synchronisation point: the loop's trip count and the branch between leaf
+// and node are the same for the whole warp.
 template <typename T, int DEG>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTraceThreads)
 rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ nodes,
                 int64_t n, const T* __restrict__ sh, const uint32_t* __restrict__ ray_view,
                 const uint32_t* __restrict__ ray_pix, const int2* __restrict__ order,
                 int64_t n_rays, const Cam* __restrict__ cams, float focal, float half_w,
                 float half_h, int heap_cap, float* __restrict__ raycol) {
     constexpr int NC = (DEG + 1) * (DEG + 1);
-    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= n_rays) return;
+    __shared__ uint32_t s_ref[kTraceWarps][kRayStack];
+    __shared__ uint32_t s_lanes[kTraceWarps][kRayStack];
+    __shared__ unsigned long long s_top[kTraceWarps][kHeapTop][32];  // [slot][lane]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const bool valid = i0 < n_rays;
+    const int64_t i = valid ? i0 : n_rays - 1;  // lanes past the end follow the last ray, unwritten
     // thread i casts ray order[i].y: the rays grouped by (view, tile) and
-    // Morton-ordered inside a tile, so a warp's rays share a camera centre and
-    // nearly share a direction, and traverse the tree alike
+    // Morton-ordered inside a tile
     const int64_t r = order ? int64_t(order[i].y) : i;
-    // heap entries packed as t's FP32 bits << 32 | Gaussian index: t > 0, so
-    // the integer order of the packed key is the (t, index) order
-    unsigned long long hk[kMaxHeap];
-    int hn = 0;
     const uint32_t px = ray_pix[r];
     const Cam& cam = cams[ray_view[r]];
     // direction: camera ray ((c - w/2 - shift)/f, (r - h/2)/f, 1) to world
@@ -384,130 +415,183 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
     dx *= dn; dy *= dn; dz *= dn;
     const float ox = cam.c[0], oy = cam.c[1], oz = cam.c[2];
     const float ix = 1.f / dx, iy = 1.f / dy, iz = 1.f / dz;
-    // traversal of the 8-wide tree: a stack of wide node indices and leaf
-    // references; each node pushes its hit children farthest first, so at
-    // most 7 entries a level plus 8 are pending (the tree's depth is checked
-    // against kMaxWideDepth when it is built; the guard only keeps a stack
-    // access in bounds)
-    uint32_t stack[kRayStack];
-    int sp = 0;
-    stack[sp++] = 0u;  // the root
+    // heap entries packed as t's FP32 bits << 32 | Gaussian index: t > 0, so
+    // the integer order of the packed key is the (t, index) order
+    unsigned long long rest[kMaxHeap - kHeapTop];
+    const RayHeap hp{&s_top[warp][0][lane], rest};
+    int hn = 0;
+    uint32_t* const st_ref = s_ref[warp];
+    uint32_t* const st_lanes = s_lanes[warp];
+    const unsigned all = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) {
+        st_ref[0] = 0u;  // the root
+        st_lanes[0] = all;
+    }
+    int sp = all ? 1 : 0;
+    __syncwarp();
     while (sp > 0) {
-        const uint32_t e = stack[--sp];
-        const float bound = hn == heap_cap ? __uint_as_float(uint32_t(hk[0] >> 32)) : INFINITY;
+        --sp;
+        const uint32_t e = st_ref[sp];
+        const bool mine = (st_lanes[sp] >> lane) & 1u;
+        __syncwarp();
+        const float bound = hn == heap_cap ? __uint_as_float(uint32_t(hp.get(0) >> 32)) : INFINITY;
         if (e & kRayLeafBit) {  // leaf: Gaussians first .. first + count - 1
-            const uint32_t first = (e & ~kRayLeafBit) >> 3, cnt = (e & 7u) + 1u;
-            for (uint32_t g = first; g < first + cnt; ++g) {
-                float t;
-                const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
-                if (!(a >= kMinAlpha) || !(t > kNearT)) continue;
-                const unsigned long long key =
-                    (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | g;
-                if (hn < heap_cap) {  // insert and sift up
-                    int k = hn++;
-                    while (k > 0) {
-                        const int p = (k - 1) >> 1;
-                        if (!(hk[p] < key)) break;
-                        hk[k] = hk[p];
-                        k = p;
+            if (mine) {
+                const uint32_t first = (e & ~kRayLeafBit) >> 3, cnt = (e & 7u) + 1u;
+                for (uint32_t g = first; g < first + cnt; ++g) {
+                    float t;
+                    const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
+                    if (!(a >= kMinAlpha) || !(t > kNearT)) continue;
+                    const unsigned long long key =
+                        (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | g;
+                    if (hn < heap_cap) {  // insert and sift up
+                        int k = hn++;
+                        while (k > 0) {
+                            const int p = (k - 1) >> 1;
+                            const unsigned long long vp = hp.get(p);
+                            if (!(vp < key)) break;
+                            hp.set(k, vp);
+                            k = p;
+                        }
+                        hp.set(k, key);
+                    } else if (key < hp.get(0)) {  // replace the farthest
+                        int k = 0;
+                        for (;;) {
+                            int c = 2 * k + 1;
+                            if (c >= hn) break;
+                            unsigned long long vc = hp.get(c);
+                            if (c + 1 < hn) {
+                                const unsigned long long v2 = hp.get(c + 1);
+                                if (vc < v2) {
+                                    ++c;
+                                    vc = v2;
+                                }
+                            }
+                            if (!(key < vc)) break;
+                            hp.set(k, vc);
+                            k = c;
+                        }
+                        hp.set(k, key);
                     }
-                    hk[k] = key;
-                } else if (key < hk[0]) {  // replace the farthest
-                    int k = 0;
-                    for (;;) {
-                        int c = 2 * k + 1;
-                        if (c >= hn) break;
-                        if (c + 1 < hn && hk[c] < hk[c + 1]) ++c;
-                        if (!(key < hk[c])) break;
-                        hk[k] = hk[c];
-                        k = c;
-                    }
-                    hk[k] = key;
                 }
             }
         } else {  // wide node: its children, nearest first
             const float4* nf = reinterpret_cast<const float4*>(nodes + e);
-            float lx[8], ly[8], lz[8], hx[8], hy[8], hz[8];
+            float te[8];
             uint32_t chv[8];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const float4 a0 = __ldg(nf + q), a1 = __ldg(nf + 2 + q), a2 = __ldg(nf + 4 + q);
                 const float4 a3 = __ldg(nf + 6 + q), a4 = __ldg(nf + 8 + q), a5 = __ldg(nf + 10 + q);
                 const uint4 c4 = __ldg(reinterpret_cast<const uint4*>(nf + 12 + q));
-                lx[4 * q] = a0.x; lx[4 * q + 1] = a0.y; lx[4 * q + 2] = a0.z; lx[4 * q + 3] = a0.w;
-                ly[4 * q] = a1.x; ly[4 * q + 1] = a1.y; ly[4 * q + 2] = a1.z; ly[4 * q + 3] = a1.w;
-                lz[4 * q] = a2.x; lz[4 * q + 1] = a2.y; lz[4 * q + 2] = a2.z; lz[4 * q + 3] = a2.w;
-                hx[4 * q] = a3.x; hx[4 * q + 1] = a3.y; hx[4 * q + 2] = a3.z; hx[4 * q + 3] = a3.w;
-                hy[4 * q] = a4.x; hy[4 * q + 1] = a4.y; hy[4 * q + 2] = a4.z; hy[4 * q + 3] = a4.w;
-                hz[4 * q] = a5.x; hz[4 * q + 1] = a5.y; hz[4 * q + 2] = a5.z; hz[4 * q + 3] = a5.w;
-                chv[4 * q] = c4.x; chv[4 * q + 1] = c4.y; chv[4 * q + 2] = c4.z; chv[4 * q + 3] = c4.w;
+                const float lxa[4] = {a0.x, a0.y, a0.z, a0.w}, lya[4] = {a1.x, a1.y, a1.z, a1.w};
+                const float lza[4] = {a2.x, a2.y, a2.z, a2.w}, hxa[4] = {a3.x, a3.y, a3.z, a3.w};
+                const float hya[4] = {a4.x, a4.y, a4.z, a4.w}, hza[4] = {a5.x, a5.y, a5.z, a5.w};
+                const uint32_t ca[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    chv[4 * q + k] = ca[k];
+                    float t = INFINITY;
+                    if (mine && ca[k] != kRayNoChild) {
+                        t = slab_enter(make_float4(lxa[k], lya[k], lza[k], 0.f),
+                                       make_float4(hxa[k], hya[k], hza[k], 0.f), ox, oy, oz, ix, iy,
+                                       iz);
+                        if (t > bound) t = INFINITY;  // beyond a full heap
+                    }
+                    te[4 * q + k] = t;
+                }
             }
-            float ct[8];
-            uint32_t ce[8];
+            // children hit by any lane, with their nearest entry (t >= 0:
+            // the bits order like the values)
+            uint32_t hit[8], near[8];
             int m = 0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                if (chv[c] == kRayNoChild) continue;
-                const float te = slab_enter(make_float4(lx[c], ly[c], lz[c], 0.f),
-                                            make_float4(hx[c], hy[c], hz[c], 0.f), ox, oy, oz, ix,
-                                            iy, iz);
-                if (!(te < INFINITY) || te > bound) continue;  // misses, or beyond a full heap
-                int k = m++;
-                while (k > 0 && ct[k - 1] < te) {  // descending: nearest pushed last
-                    ct[k] = ct[k - 1];
-                    ce[k] = ce[k - 1];
-                    --k;
-                }
-                ct[k] = te;
-                ce[k] = chv[c];
+                const bool h = te[c] < INFINITY;
+                hit[c] = __ballot_sync(0xffffffffu, h);
+                near[c] = __reduce_min_sync(0xffffffffu,
+                                            h ? __float_as_uint(fmaxf(te[c], 0.f)) : 0xFFFFFFFFu);
+                m += hit[c] ? 1 : 0;
             }
-            if (sp + m > kRayStack) m = kRayStack - sp;
-            for (int k = 0; k < m; ++k) stack[sp++] = ce[k];
+            if (sp + m > kRayStack) m = 0;  // cannot happen (depth checked); keeps the stack in bounds
+            if (lane == 0 && m > 0) {
+                // farthest first: sort the hit children by descending entry
+                uint32_t kk[8], rr[8], ll[8];
+                int k = 0;
+                for (int c = 0; c < 8; ++c) {
+                    if (!hit[c]) continue;
+                    int j = k++;
+                    while (j > 0 && kk[j - 1] < near[c]) {
+                        kk[j] = kk[j - 1];
+                        rr[j] = rr[j - 1];
+                        ll[j] = ll[j - 1];
+                        --j;
+                    }
+                    kk[j] = near[c];
+                    rr[j] = chv[c];
+                    ll[j] = hit[c];
+                }
+                for (int j = 0; j < k; ++j) {
+                    st_ref[sp + j] = rr[j];
+                    st_lanes[sp + j] = ll[j];
+                }
+            }
+            sp += m;
+            __syncwarp();
         }
     }
-    // pop the heap from its farthest entry: list in ascending (t, index)
-    for (int k = hn - 1; k > 0; --k) {
-        const unsigned long long top = hk[0], last = hk[k];
-        int j = 0;
-        for (;;) {
-            int c = 2 * j + 1;
-            if (c >= k) break;
-            if (c + 1 < k && hk[c] < hk[c + 1]) ++c;
-            if (!(last < hk[c])) break;
-            hk[j] = hk[c];
-            j = c;
+    if (valid) {
+        // pop the heap from its farthest entry: list in ascending (t, index)
+        for (int k = hn - 1; k > 0; --k) {
+            const unsigned long long top = hp.get(0), last = hp.get(k);
+            int j = 0;
+            for (;;) {
+                int c = 2 * j + 1;
+                if (c >= k) break;
+                unsigned long long vc = hp.get(c);
+                if (c + 1 < k) {
+                    const unsigned long long v2 = hp.get(c + 1);
+                    if (vc < v2) {
+                        ++c;
+                        vc = v2;
+                    }
+                }
+                if (!(last < vc)) break;
+                hp.set(j, vc);
+                j = c;
+            }
+            hp.set(j, last);
+            hp.set(k, top);
         }
-        hk[j] = last;
-        hk[k] = top;
-    }
-    // blend front to back, colour from the SH at the ray direction
-    float Y[16];
-    sh_basis<DEG>(dx, dy, dz, Y);
-    float tr = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;  // transmittance, colour
-    for (int k = 0; k < hn; ++k) {
-        float t;
-        const int64_t g = int64_t(uint32_t(hk[k]));
-        const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
-        const float tn = tr * (1.f - a);
-        if (tn < 1e-4f) break;
-        float col[3];
+        // blend front to back, colour from the SH at the ray direction
+        float Y[16];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float tr = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;  // transmittance, colour
+        for (int k = 0; k < hn; ++k) {
+            float t;
+            const int64_t g = int64_t(uint32_t(hp.get(k)));
+            const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
+            const float tn = tr * (1.f - a);
+            if (tn < 1e-4f) break;
+            float col[3];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.f;
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.f;
 #pragma unroll
-            for (int j = 0; j < NC; ++j) acc = fmaf(Y[j], to_f(sh[(g * NC + j) * 3 + ch]), acc);
-            col[ch] = fmaxf(acc + 0.5f, 0.f);
+                for (int j = 0; j < NC; ++j) acc = fmaf(Y[j], to_f(sh[(g * NC + j) * 3 + ch]), acc);
+                col[ch] = fmaxf(acc + 0.5f, 0.f);
+            }
+            const float w = a * tr;
+            c0 = fmaf(w, col[0], c0);
+            c1 = fmaf(w, col[1], c1);
+            c2 = fmaf(w, col[2], c2);
+            tr = tn;
         }
-        const float w = a * tr;
-        c0 = fmaf(w, col[0], c0);
-        c1 = fmaf(w, col[1], c1);
-        c2 = fmaf(w, col[2], c2);
-        tr = tn;
+        // colours in thread order: the grouped order when `order` is given
+        raycol[3 * i] = c0;
+        raycol[3 * i + 1] = c1;
+        raycol[3 * i + 2] = c2;
     }
-    // colours in thread order: the grouped order when `order` is given
-    raycol[3 * i] = c0;
-    raycol[3 * i + 1] = c1;
-    raycol[3 * i + 2] = c2;
 }
 
 int grid_of(int64_t n, int block) {
@@ -642,9 +726,9 @@ cudaError_t launch_raycast(int dtype, int sh_degree, const float4* gauss, const 
                            const Cam* cams, float focal, float half_w, float half_h, int heap_cap,
                            float* raycol, cudaStream_t s) {
     if (n_rays <= 0) return cudaSuccess;
-    const unsigned grid = unsigned((n_rays + 127) / 128);
+    const unsigned grid = unsigned((n_rays + kTraceThreads - 1) / kTraceThreads);
 #define DL_RC(T, D)                                                                          \
-    rc_trace_kernel<T, D><<<grid, 128, 0, s>>>(gauss, nodes, n, static_cast<const T*>(sh),   \
+    rc_trace_kernel<T, D><<<grid, kTraceThreads, 0, s>>>(gauss, nodes, n, static_cast<const T*>(sh),   \
                                                ray_view, ray_pix, order, n_rays, cams, focal,  \
                                                half_w, half_h, heap_cap, raycol)
 #define DL_RC_DEG(T)                  \
