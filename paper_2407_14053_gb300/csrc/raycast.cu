@@ -420,6 +420,12 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
     unsigned long long rest[kMaxHeap - kHeapTop];
     const RayHeap hp{&s_top[warp][0][lane], rest};
     int hn = 0;
+    // Transmittance bound: tb is set once the intersections found so far
+    // (every one at t <= tmax) multiply T below 5e-5.  Sorted, they alone
+    // take T below 1e-4 by t = tmax, so blending stops at or before tmax and
+    // nothing beyond tb can be blended; the walk skips it.  (5e-5, not
+    // 1e-4: the product is formed in another order than the blend's.)
+    float prodT = 1.f, tmax = 0.f, tb = INFINITY;
     uint32_t* const st_ref = s_ref[warp];
     uint32_t* const st_lanes = s_lanes[warp];
     const unsigned all = __ballot_sync(0xffffffffu, valid);
@@ -434,14 +440,20 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
         const uint32_t e = st_ref[sp];
         const bool mine = (st_lanes[sp] >> lane) & 1u;
         __syncwarp();
-        const float bound = hn == heap_cap ? __uint_as_float(uint32_t(hp.get(0) >> 32)) : INFINITY;
+        const float bound =
+            fminf(tb, hn == heap_cap ? __uint_as_float(uint32_t(hp.get(0) >> 32)) : INFINITY);
         if (e & kRayLeafBit) {  // leaf: Gaussians first .. first + count - 1
             if (mine) {
                 const uint32_t first = (e & ~kRayLeafBit) >> 3, cnt = (e & 7u) + 1u;
                 for (uint32_t g = first; g < first + cnt; ++g) {
                     float t;
                     const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
-                    if (!(a >= kMinAlpha) || !(t > kNearT)) continue;
+                    if (!(a >= kMinAlpha) || !(t > kNearT) || t > tb) continue;
+                    if (tb == INFINITY) {
+                        prodT *= 1.f - a;
+                        tmax = fmaxf(tmax, t);
+                        if (prodT < 5e-5f) tb = tmax;
+                    }
                     const unsigned long long key =
                         (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | g;
                     if (hn < heap_cap) {  // insert and sift up
