@@ -663,11 +663,13 @@ composite_full_binned_kernel(CompositeParams p, const int32_t* __restrict__ list
 constexpr int kWarpsPerBlock = 4;
 
 // Positions of the warp's rays about their box centre (x, y), written per
-// ray chunk, and the per-ray candidate masks of one batch.  Coordinates are
-// stored apart, so four rays' x (or y) are one 16-byte read.
+// ray chunk, the per-ray candidate masks of one batch and the third colour
+// channel of its records (the other two are decoded in place).  Coordinates
+// are stored apart, so four rays' x (or y) are one 16-byte read.
 struct RayTable {
     float4 x[8], y[8];
     uint4 mask[8];
+    float blue[32];
 };
 
 // A warp's shared memory holds its group's keys while it sorts them and,
@@ -676,12 +678,12 @@ struct RayTable {
 // space, which keeps the 1024-key class at six blocks per SM.
 template <int CAP>
 struct WarpSort {
-    // at least one bucket a key up to 352 (or 320) keys: the passes that
+    // at least one bucket a key up to 384 (or 320) keys: the passes that
     // order keys inside buckets grow with the most crowded bucket, and depths
-    // cluster; for CAP = 512 the buckets fit in the space the stream phase
+    // cluster; for CAP = 512 the buckets fill the space the stream phase
     // needs anyway, for CAP = 1024 the sort phase sets the size (six blocks
     // per SM)
-    static constexpr int kBuckets = CAP <= 512 ? 352 : 320;
+    static constexpr int kBuckets = CAP <= 512 ? 384 : 320;
     unsigned long long sk[CAP];
     uint32_t bstart[kBuckets];  // bucket sizes, starts, then (after the scatter) ends
 };
@@ -701,7 +703,7 @@ union WarpSmem {
     WarpSort<CAP> s;
     WarpStream<CAP> c;
 };
-static_assert(sizeof(WarpStream<512>) <= sizeof(WarpSort<512>), "stream phase fits the sort's space");
+static_assert(sizeof(WarpSort<512>) <= sizeof(WarpStream<512>), "sort phase fits the stream's space");
 static_assert(sizeof(WarpStream<1024>) <= sizeof(WarpSort<1024>), "stream phase fits the sort's space");
 // blocks of kWarpsPerBlock warps per SM: eight (512-key class, 64
 // registers a thread) and six (1024-key class, 80 registers); 228 KB of
@@ -875,20 +877,28 @@ constexpr float kTestMargin = 0.05f;
 
 // Transposed evaluation of a batch of n <= 32 records held in shared memory
 // (c0, c1: the two halves of each record) for the warp's rays: lane j holds
-// record j's conic (u, v, A, B, C, L) when `hit` (j < n).  The lane expands
-// the quadratic about the box centre (ox, oy) into
+// record j's conic (u, v, A, B, C, L) and packed colour (pc, pd) when `hit`
+// (j < n).  The lane decodes the colour once for every ray that will blend
+// the record (r, g over the packed words, b into T.blue), then expands the
+// quadratic about the box centre (ox, oy) into
 // l2(x, y) = x (A x + B y + D) + y (C y + E) + F and tests it against every
 // ray (5 FMAs per pair, ray positions from the table), four rays per step
 // with the FMAs paired over two rays (packed FP32x2 FMA: per component the
 // same rounding as fmaf); ray r's mask of candidate records goes to
 // T.mask[r].  Then every lane blends its candidates in list order.
 template <bool COUNT>
-__device__ __forceinline__ void eval32(const float4* c0, const float4* c1, int n, bool hit, float u,
-                                       float v, float A, float B, float C, float L, Acc& a,
-                                       bool& done, uint32_t& evals, float px, float py,
-                                       RayTable& T, float ox, float oy) {
+__device__ __forceinline__ void eval32(const float4* c0, float4* c1, int n, bool hit, float u,
+                                       float v, float A, float B, float C, float L, float pc,
+                                       float pd, Acc& a, bool& done, uint32_t& evals, float px,
+                                       float py, RayTable& T, float ox, float oy) {
     const int lane = threadIdx.x & 31;
     if (!__any_sync(0xffffffffu, hit)) return;
+    if (hit) {
+        float r, g, b;
+        unpack_rgb(pc, pd, r, g, b);
+        reinterpret_cast<float2*>(c1 + lane)[1] = make_float2(r, g);
+        T.blue[lane] = b;
+    }
     const unsigned act = __ballot_sync(0xffffffffu, !done);
     const float du = u - ox, dv = v - oy;
     const float D = -fmaf(2.f * A, du, B * dv);
@@ -918,7 +928,7 @@ __device__ __forceinline__ void eval32(const float4* c0, const float4* c1, int n
     while (mine && !done) {  // candidates passed the (widened) test: alpha decides
         const int sidx = __ffs(mine) - 1;
         mine &= mine - 1;
-        if (!blend_rec<false, COUNT>(a, px, py, c0[sidx], c1[sidx])) done = true;
+        if (!blend<false, COUNT>(a, px, py, c0[sidx], c1[sidx], T.blue[sidx])) done = true;
     }
     __syncwarp();
 }
@@ -935,19 +945,20 @@ __device__ __forceinline__ void ray_table(RayTable& T, bool active, float px, fl
     __syncwarp();
 }
 
-// Lane's record of a shared-memory batch: loads its conic into registers
-// (lanes past the batch hold one that no ray passes).  A tile list holds
-// only records whose pixel box meets the tile, and the warp's rays spread
-// over the tile, so no box pre-test is made: the widened test below sorts
-// the records out at a few FMAs per pair.
+// Lane's record of a shared-memory batch: loads its conic and packed colour
+// into registers (lanes past the batch hold a conic that no ray passes).  A
+// tile list holds only records whose pixel box meets the tile, and the
+// warp's rays spread over the tile, so no box pre-test is made: the widened
+// test below sorts the records out at a few FMAs per pair.
 __device__ __forceinline__ bool batch_conic(const float4* c0, const float4* c1, int n, float& u,
-                                            float& v, float& A, float& B, float& C, float& L) {
+                                            float& v, float& A, float& B, float& C, float& L,
+                                            float& pc, float& pd) {
     const int lane = threadIdx.x & 31;
-    u = 0.f; v = 0.f; A = 0.f; B = 0.f; C = 0.f; L = -1e30f;
+    u = 0.f; v = 0.f; A = 0.f; B = 0.f; C = 0.f; L = -1e30f; pc = 0.f; pd = 0.f;
     if (lane >= n) return false;
     const float4 q0 = c0[lane];
-    const float2 q1 = *reinterpret_cast<const float2*>(c1 + lane);
-    u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y;
+    const float4 q1 = c1[lane];
+    u = q0.x; v = q0.y; A = q0.z; B = q0.w; C = q1.x; L = q1.y; pc = q1.z; pd = q1.w;
     return true;
 }
 
@@ -981,12 +992,13 @@ __device__ __forceinline__ void warp_stream(WarpSmem<CAP>& W, int len, int64_t v
         cp_async_wait<S - 1>();
         __syncwarp();
         const float4* c0 = W.c.buf[slot][0];
-        const float4* c1 = W.c.buf[slot][1];
+        float4* c1 = W.c.buf[slot][1];
         slot = slot + 1 == S ? 0 : slot + 1;
         const int n = len - b * 32 < 32 ? len - b * 32 : 32;
-        float u, v, A, B, C, L;
-        const bool hit = batch_conic(c0, c1, n, u, v, A, B, C, L);
-        eval32<COUNT>(c0, c1, n, hit, u, v, A, B, C, L, a, done, evals, px, py, W.c.rays, ox, oy);
+        float u, v, A, B, C, L, pc, pd;
+        const bool hit = batch_conic(c0, c1, n, u, v, A, B, C, L, pc, pd);
+        eval32<COUNT>(c0, c1, n, hit, u, v, A, B, C, L, pc, pd, a, done, evals, px, py, W.c.rays,
+                      ox, oy);
         if (__all_sync(0xffffffffu, done)) break;
     }
     cp_async_wait<0>();
@@ -1051,10 +1063,11 @@ __device__ void quadrant_stream(const unsigned long long* sk, int len, int q, in
         else cp_async_wait<0>();
         __syncwarp();
         const float4* c0 = Q.buf[slot][0];
-        const float4* c1 = Q.buf[slot][1];
-        float u, v, A, B, C, L;
-        const bool hit = batch_conic(c0, c1, n_cur, u, v, A, B, C, L);
-        eval32<true>(c0, c1, n_cur, hit, u, v, A, B, C, L, a, done, evals, px, py, Q.rays, ox, oy);
+        float4* c1 = Q.buf[slot][1];
+        float u, v, A, B, C, L, pc, pd;
+        const bool hit = batch_conic(c0, c1, n_cur, u, v, A, B, C, L, pc, pd);
+        eval32<true>(c0, c1, n_cur, hit, u, v, A, B, C, L, pc, pd, a, done, evals, px, py, Q.rays,
+                     ox, oy);
         slot ^= 1;
         n_cur = __all_sync(0xffffffffu, done) ? 0 : n_next;
     }
