@@ -189,6 +189,9 @@ def parse():
                     help="skip the ray-order 3DGS timing")
     ap.add_argument("--no-graph", action="store_true",
                     help="skip the 8K/100-view captured-graph batch section")
+    ap.add_argument("--two-pass-emission", action="store_true",
+                    help="DirectL keys through tile metadata and an emission kernel instead of "
+                         "from the projection kernel")
     return ap.parse_args()
 
 
@@ -428,6 +431,8 @@ def per_frame(totals: dict, n: int) -> dict:
     out["visible"] = totals["n_visible"] / max(n, 1)
     out["pairs_evaluated"] = totals["pairs_evaluated"] / max(n, 1)
     out["pairs_blended"] = totals["pairs_blended"] / max(n, 1)
+    out["reemitted_frames"] = int(totals.get("reemitted", 0))  # keys emitted a second time
+    out["dropped_frames"] = int(totals.get("status", 0))
     return out
 
 
@@ -670,6 +675,8 @@ def main():
     d = wl.display
     scene = W.make_scene(wl.scene)
     r = Renderer(local)
+    if args.two_pass_emission:
+        r.set_key_emission(False)
     sid = r.load_gaussians(scene, wl.scene.dtype)
     t0 = time.perf_counter()
     did = r.set_display(d)
@@ -826,19 +833,33 @@ def main():
 
     # ---- rooflines of the other stages (HBM-bound; per frame) ----
     ne = d.num_views * wl.scene.n
-    stages_roof = {
-        "project": stage_roofline(
-            "project_kernel (with the camera upload and counter resets before it)",
-            dl_stages["project"],
-            wl.scene.n * attribute_bytes(wl.scene) + 16 * ne + RECORD_BYTES * dl_stages["visible"],
-            f"{attribute_bytes(wl.scene)} B of attributes read once per Gaussian, 16 B tile "
-            f"metadata written per (view, Gaussian), {RECORD_BYTES} B record written per "
-            "visible (view, Gaussian)", hbm_gbs, hbm_source),
-        "emit": stage_roofline(
-            "emit_binned_kernel", dl_stages["emit"], 16 * ne + 8 * dl_stages["keys"],
-            "16 B tile metadata read per (view, Gaussian), 8 B key written per key",
-            hbm_gbs, hbm_source),
-    }
+    if args.two_pass_emission:
+        stages_roof = {
+            "project": stage_roofline(
+                "project_kernel (with the camera upload and counter resets before it)",
+                dl_stages["project"],
+                wl.scene.n * attribute_bytes(wl.scene) + 16 * ne +
+                RECORD_BYTES * dl_stages["visible"],
+                f"{attribute_bytes(wl.scene)} B of attributes read once per Gaussian, 16 B tile "
+                f"metadata written per (view, Gaussian), {RECORD_BYTES} B record written per "
+                "visible (view, Gaussian)", hbm_gbs, hbm_source),
+            "emit": stage_roofline(
+                "emit_binned_kernel", dl_stages["emit"], 16 * ne + 8 * dl_stages["keys"],
+                "16 B tile metadata read per (view, Gaussian), 8 B key written per key",
+                hbm_gbs, hbm_source),
+        }
+    else:
+        stages_roof = {
+            "project": stage_roofline(
+                "project_direct_kernel (projection emitting the tile keys; with the camera "
+                "upload and the cursor copy before it)",
+                dl_stages["project"],
+                wl.scene.n * attribute_bytes(wl.scene) + RECORD_BYTES * dl_stages["visible"] +
+                KEY_BYTES * dl_stages["keys"],
+                f"{attribute_bytes(wl.scene)} B of attributes read once per Gaussian, "
+                f"{RECORD_BYTES} B record written per visible (view, Gaussian), {KEY_BYTES} B "
+                "key written per key", hbm_gbs, hbm_source),
+        }
     if std is not None:
         ss = std["stages_ms"]
         pix = d.num_views * d.width * d.height

@@ -274,7 +274,18 @@ dl_status dl_ray_table_static(int32_t width, int32_t height, const uint16_t* V,
  *   the global radix sort.  DL_SORT_BINNED: always binned; a frame with a
  *   longer list fails with DL_ERR_CAPACITY.  Both give the same image. */
 enum { DL_OPT_SORT_MODE = 1, DL_OPT_EVAL_DIRECTL = 2, DL_OPT_EVAL_STANDARD = 3,
-       DL_OPT_WARP_LIST_CAP = 4, DL_OPT_STANDARD_VIEW_SIZE = 5, DL_OPT_HEAP_CAPACITY = 6 };
+       DL_OPT_WARP_LIST_CAP = 4, DL_OPT_STANDARD_VIEW_SIZE = 5, DL_OPT_HEAP_CAPACITY = 6,
+       DL_OPT_KEY_EMISSION = 7 };
+/* DL_OPT_KEY_EMISSION: where the binned path of DL_DIRECTL / DL_REQUIRED_ONLY
+ * writes its tile keys, once a frame of the same signature has been sized.
+ * 1 (default): the projection kernel emits every (view, tile, Gaussian) key
+ * itself, into per-(view, tile) slices of the key buffer laid out from the
+ * signature's previous frame (its key count per group plus an eighth and
+ * 16); a frame whose counts outgrow a slice emits its keys a second time
+ * into slices sized from its own counts, on the device, before compositing.
+ * 0: the projection writes per-(view, Gaussian) tile metadata and a second
+ * kernel emits the keys into slices sized from this frame's counts (Sec. 4
+ * step (2) as two passes).  Both give the same keys, so the same image. */
 /* DL_OPT_HEAP_CAPACITY: c_h of DL_RAYCAST, the number of nearest
  * intersections each ray keeps and blends (1..256, default 128).
  *
@@ -332,6 +343,11 @@ typedef struct {
                                 keys exceeded the key capacity, bit 1 a tile
                                 list exceeded the long-list capacity.  In
                                 dl_stage_totals: the number of dropped frames */
+    int32_t reemitted;       /* last frame: 1 when its keys outgrew the slices
+                                its signature's previous frame laid out and the
+                                projection emitted them again (key emission in
+                                the projection, DL_OPT_KEY_EMISSION 1), else 0.
+                                In dl_stage_totals: the number of such frames */
 } dl_frame_stats;
 
 /* While enabled, every dl_render_frame records CUDA events around its

@@ -26,7 +26,7 @@ DL_ERR_CAPACITY = -7
 DL_F32, DL_BF16, DL_F16 = 0, 1, 2
 DL_DIRECTL, DL_STANDARD, DL_REQUIRED_ONLY, DL_RAYCAST, DL_STANDARD_SR = 0, 1, 2, 3, 4
 DL_OPT_SORT_MODE, DL_OPT_EVAL_DIRECTL, DL_OPT_EVAL_STANDARD, DL_OPT_WARP_LIST_CAP = 1, 2, 3, 4
-DL_OPT_STANDARD_VIEW_SIZE, DL_OPT_HEAP_CAPACITY = 5, 6
+DL_OPT_STANDARD_VIEW_SIZE, DL_OPT_HEAP_CAPACITY, DL_OPT_KEY_EMISSION = 5, 6, 7
 DL_SORT_AUTO, DL_SORT_RADIX, DL_SORT_BINNED = 0, 1, 2
 DL_EVAL_DIRECT, DL_EVAL_TRANSPOSED = 0, 1
 
@@ -53,7 +53,7 @@ class dl_frame_stats(ctypes.Structure):
                 ("lists_large", c_int64), ("max_list", c_int64), ("n_visible", c_int64)] + [
         (f, ctypes.c_float) for f in ("ms_project", "ms_scan", "ms_sync", "ms_emit", "ms_sort",
                                       "ms_ranges", "ms_composite", "ms_interweave", "ms_total")] + [
-        ("status", c_int32)]
+        ("status", c_int32), ("reemitted", c_int32)]
 
 
 class dl_slot_plan(ctypes.Structure):

@@ -346,18 +346,24 @@ dl_status build_raycast(dl_ctx* ctx, Scene& S, cudaStream_t s) {
 
 // The counter block of a frame run on device counters (copied from the
 // workspace's 256-byte block: keys and visible records as u64 at bytes 0 and
-// 8, the list-class words {warp items, block items, longest list, -, 1024-key
-// items, cursors, status} from byte 128): fills the frame's statistics and
-// resets its signature's sizing when the frame was dropped or used more than
-// 85 % of a capacity.
+// 8; at byte 64 the end of the key slices (the exact key total, or with the
+// keys emitted by the projection the end of the next frame's slices) and
+// the re-emission flag; the list-class words {warp items, block items,
+// longest list, -, 1024-key items, cursors, status} from byte 128): fills
+// the frame's statistics and resets its signature's sizing when the frame
+// was dropped or used more than 85 % of a capacity.
 static void apply_readback(dl_ctx* ctx, Readback& r) {
     Workspace& W = ctx->ws;
     const unsigned long long* h = r.h;
-    const uint32_t* m = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(h) + 128);
-    const int64_t nkeys = int64_t(h[0]), vis = int64_t(h[1]);
+    const char* hb = reinterpret_cast<const char*>(h);
+    const uint32_t* m = reinterpret_cast<const uint32_t*>(hb + 128);
+    const uint32_t* t32 = reinterpret_cast<const uint32_t*>(hb + 64);
+    const int64_t nkeys = int64_t(h[0]), vis = int64_t(h[1]), slice_end = int64_t(t32[0]);
+    const int32_t reemitted = t32[1] != 0u ? 1 : 0;
     const int64_t lists_small = int64_t(m[0]) + int64_t(m[4]), lists_large = m[1], longest = m[2];
     const int32_t status = int32_t(m[7]);
     if (r.hint && (status != 0 || nkeys * 100 > r.hint->key_cap * 85 ||
+                   slice_end * 100 > r.hint->key_cap * 85 ||
                    longest * 100 > int64_t(r.hint->block_cap) * 85))
         r.hint->sized = false;
     if (status != 0) ++W.dropped;
@@ -369,6 +375,7 @@ static void apply_readback(dl_ctx* ctx, Readback& r) {
             f.lists_large = lists_large;
             f.max_list = longest;
             f.status = status;
+            f.reemitted = reemitted;
         }
     if (W.last_async == r.frame) {
         dl_frame_stats& fs = ctx->stats;
@@ -378,6 +385,7 @@ static void apply_readback(dl_ctx* ctx, Readback& r) {
         fs.lists_large = lists_large;
         fs.max_list = longest;
         fs.status = status;
+        fs.reemitted = reemitted;
         W.last_async = -1;
     }
     r.busy = false;
@@ -639,6 +647,21 @@ dl_status dl_load_gaussians(dl_ctx* ctx, const dl_gaussians_desc* d, void* strea
     return DL_OK;
 }
 
+// Drops the capacities and key slices of the frame signatures that name a
+// freed scene (field 0) or display (field 1); pending counter readbacks stop
+// pointing at them.
+static void drop_hints(dl_ctx* ctx, int field, int32_t id) {
+    for (auto it = ctx->hints.begin(); it != ctx->hints.end();) {
+        if (it->first[size_t(field)] == id) {
+            for (Readback& r : ctx->ws.rb)
+                if (r.hint == &it->second) r.hint = nullptr;
+            it = ctx->hints.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 dl_status dl_free_scene(dl_ctx* ctx, int32_t scene_id) {
     dl_status st = check_ctx(ctx);
     if (st) return st;
@@ -649,6 +672,7 @@ dl_status dl_free_scene(dl_ctx* ctx, int32_t scene_id) {
                     it->second->in_use);
     cudaDeviceSynchronize();
     ctx->scenes.erase(it);
+    drop_hints(ctx, 0, scene_id);
     return DL_OK;
 }
 
@@ -686,6 +710,7 @@ dl_status dl_free_display(dl_ctx* ctx, int32_t display_id) {
                     display_id, it->second->in_use);
     cudaDeviceSynchronize();
     ctx->displays.erase(it);
+    drop_hints(ctx, 1, display_id);
     return DL_OK;
 }
 
@@ -806,6 +831,12 @@ dl_status dl_set_option(dl_ctx* ctx, int32_t option, int64_t value) {
         ctx->warp_cap = int32_t(value);
         return DL_OK;
     }
+    if (option == DL_OPT_KEY_EMISSION) {
+        if (value != 0 && value != 1)
+            return fail(ctx, DL_ERR_INVALID_ARG, "key emission %lld", (long long)value);
+        ctx->direct_emit = value == 1;
+        return DL_OK;
+    }
     if (option == DL_OPT_HEAP_CAPACITY) {
         if (value < 1 || value > kMaxHeap)
             return fail(ctx, DL_ERR_INVALID_ARG, "heap capacity %lld out of [1, %d]",
@@ -892,6 +923,7 @@ dl_status dl_stage_totals(dl_ctx* ctx, dl_frame_stats* sum, int32_t* n_frames) {
         t.lists_large += f.lists_large;
         t.max_list = std::max(t.max_list, f.max_list);
         t.status += f.status != 0 ? 1 : 0;
+        t.reemitted += f.reemitted;
         W.ev_free.push_back(f.ev);
     }
     *n_frames = int32_t(W.pending.size());
@@ -1032,34 +1064,6 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     if (ne >= (int64_t(1) << 31)) return fail(ctx, DL_ERR_CAPACITY, "views x Gaussians >= 2^31");
     const int64_t ngroups = int64_t(nv) * ntiles;
     if (ngroups >= (int64_t(1) << 31) - 1) return fail(ctx, DL_ERR_CAPACITY, "too many tiles");
-    DL_CK(W.rec.reserve(16 * kRecordFloat4 * size_t(ne)), "alloc records");
-    DL_CK(W.meta.reserve(16 * size_t(ne)), "alloc tile metadata");
-    DL_CK(W.gcount.reserve(4 * size_t(ngroups + 1)), "alloc group counts");
-    DL_CK(W.gstart.reserve(4 * size_t(ngroups + 1)), "alloc group starts");
-    DL_CK(W.gscan_tmp.reserve(scan_tmp_bytes(ngroups + 1)), "alloc scan");
-    DL_CK(W.small.reserve(256), "alloc");
-    unsigned long long* d_total64 = W.small.as<unsigned long long>();
-    uint32_t* d_total32 = reinterpret_cast<uint32_t*>(W.small.as<char>() + 64);
-    uint32_t* d_meta = reinterpret_cast<uint32_t*>(W.small.as<char>() + 128);
-    DL_CK(cudaMemsetAsync(W.small.p, 0, 256, s), "memset");
-    DL_CK(cudaMemsetAsync(W.gcount.p, 0, 4 * size_t(ngroups + 1), s), "memset");
-    const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
-    ProjectOut po{W.rec.as<float4>(), W.meta.as<uint4>(), d_total64, W.gcount.as<uint32_t>(),
-                  d_total64 + 1};
-    DL_CK(launch_project(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, s), "project");
-    DL_CK(mark(1), "event");
-    // group starts (one extra entry: gstart[ngroups] = number of keys) and the
-    // split of the compositing work by list length
-    DL_CK(launch_exclusive_scan(W.gcount.as<uint32_t>(), W.gstart.as<uint32_t>(), ngroups + 1,
-                                d_total32, W.gscan_tmp.p, s),
-          "group scan");
-    const int4* gwork = mode == DL_STANDARD ? nullptr : G->gwork.as<int4>();
-    const int64_t n_work = mode == DL_STANDARD ? ngroups : G->n_gwork;
-    const size_t nw1 = size_t(std::max<int64_t>(n_work, 1));
-    DL_CK(W.lists.reserve(24 * nw1 + 16), "alloc lists");
-    int32_t* small_list = W.lists.as<int32_t>();
-    int32_t* large_list = small_list + nw1;
-    int4* items = reinterpret_cast<int4*>(W.lists.as<char>() + 8 * nw1 + 15 - ((8 * nw1 + 15) % 16));
     // DirectL: lists of up to warp_cap keys become warp items, longer ones go
     // to the block kernel; standard: small / large block classes.
     const bool warp_path = mode != DL_STANDARD && ctx->warp_cap > 0;
@@ -1069,14 +1073,96 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     // device (status word, output untouched) when they exceed them.
     FrameHint& hint = ctx->hints[FrameSig{scene_id, display_id, mode, tw, th, rw, rh}];
     const bool on_device = warp_path && hint.sized && ctx->sort_mode != DL_SORT_RADIX;
+    // keys emitted by the projection, into the slices the signature's last
+    // frame laid out
+    const bool direct = on_device && ctx->direct_emit && hint.slices_ready;
+    DL_CK(W.rec.reserve(16 * kRecordFloat4 * size_t(ne)), "alloc records");
+    if (!direct) DL_CK(W.meta.reserve(16 * size_t(ne)), "alloc tile metadata");
+    DL_CK(W.gcount.reserve(4 * size_t(ngroups + 1)), "alloc group counts");
+    DL_CK(W.gstart.reserve(4 * size_t(ngroups + 1)), "alloc group starts");
+    DL_CK(W.gfill.reserve(4 * size_t(ngroups)), "alloc cursors");
+    DL_CK(W.gscan_tmp.reserve(scan_tmp_bytes(ngroups + 1)), "alloc scan");
+    DL_CK(W.small.reserve(256), "alloc");
+    unsigned long long* d_total64 = W.small.as<unsigned long long>();
+    uint32_t* d_total32 = reinterpret_cast<uint32_t*>(W.small.as<char>() + 64);
+    uint32_t* d_redo = d_total32 + 1;  // a key found its slice full (direct emission)
+    uint32_t* d_meta = reinterpret_cast<uint32_t*>(W.small.as<char>() + 128);
     uint32_t* d_status = d_meta + 7;
-    const uint32_t* d_nkeys = W.gstart.as<uint32_t>() + ngroups;
+    DL_CK(cudaMemsetAsync(W.small.p, 0, 256, s), "memset");
     // the key buffer only grows, so its capacity covers every earlier sizing
     const uint32_t key_cap =
         on_device ? uint32_t(std::min<size_t>(W.keys[0].bytes / 8, size_t((1u << 31) - 2))) : 0u;
-    if (warp_path) {
-        DL_CK(launch_partition_warp(gwork, n_work, W.gstart.as<uint32_t>(), uint32_t(ctx->warp_cap),
-                                    ctx->warp_cap < 1024 ? 1024u : 0u, items, large_list, d_meta,
+    const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
+    const int4* gwork = mode == DL_STANDARD ? nullptr : G->gwork.as<int4>();
+    const int64_t n_work = mode == DL_STANDARD ? ngroups : G->n_gwork;
+    const size_t nw1 = size_t(std::max<int64_t>(n_work, 1));
+    DL_CK(W.lists.reserve(32 * nw1 + 16), "alloc lists");
+    // warp path: items, then block items; otherwise the two class lists
+    int4* items = W.lists.as<int4>();
+    int4* block_items = items + nw1;
+    int32_t* small_list = W.lists.as<int32_t>();
+    int32_t* large_list = small_list + nw1;
+    uint32_t* cursor = W.gfill.as<uint32_t>();
+    if (direct) {
+        DL_CK(hint.slices[hint.cur ^ 1].reserve(4 * size_t(ngroups + 1)), "alloc slices");
+        const uint32_t* slice = hint.slices[hint.cur].as<uint32_t>();
+        uint32_t* next = hint.slices[hint.cur ^ 1].as<uint32_t>();
+        DL_CK(cudaMemcpyAsync(cursor, slice, 4 * size_t(ngroups), cudaMemcpyDeviceToDevice, s),
+              "cursors");
+        ProjectOut po{W.rec.as<float4>(), nullptr, d_total64, nullptr, d_total64 + 1};
+        po.keys = W.keys[0].as<unsigned long long>();
+        po.cursor = cursor;
+        po.slice = slice;
+        po.key_cap = key_cap;
+        po.overflow = d_redo;
+        DL_CK(launch_project_direct(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, false, s),
+              "project");
+        DL_CK(mark(1), "event");
+        // the next frame's slices, from this frame's counts (the scan's
+        // total, at d_total32, is read back with the frame's counters)
+        DL_CK(launch_pad_counts(cursor, slice, ngroups, W.gcount.as<uint32_t>(), s), "pad counts");
+        DL_CK(launch_exclusive_scan(W.gcount.as<uint32_t>(), next, ngroups + 1, d_total32,
+                                    W.gscan_tmp.p, s),
+              "slice scan");
+        // a frame that outgrew a slice emits its keys again, into those
+        // slices (no key past key_cap: the frame is dropped, status bit 0)
+        DL_CK(launch_reset_cursor(d_redo, next, ngroups, cursor, s), "cursors");
+        ProjectOut po2 = po;
+        po2.slice = next;
+        po2.gate = d_redo;
+        po2.overflow = d_status;
+        DL_CK(launch_project_direct(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po2, true, s),
+              "re-emit keys");
+        GroupSlices sl;
+        sl.start = slice;
+        sl.start_alt = next;
+        sl.use_alt = d_redo;
+        sl.cursor = cursor;
+        DL_CK(launch_partition_warp(gwork, n_work, sl, uint32_t(ctx->warp_cap),
+                                    ctx->warp_cap < 1024 ? 1024u : 0u, items, block_items, d_meta,
+                                    nullptr, key_cap, d_status, s),
+              "partition");
+        hint.cur ^= 1;
+    } else {
+        DL_CK(cudaMemsetAsync(W.gcount.p, 0, 4 * size_t(ngroups + 1), s), "memset");
+        ProjectOut po{W.rec.as<float4>(), W.meta.as<uint4>(), d_total64, W.gcount.as<uint32_t>(),
+                      d_total64 + 1};
+        DL_CK(launch_project(S.dtype, attrs, pp, W.cams.as<Cam>(), nv, po, s), "project");
+        DL_CK(mark(1), "event");
+        // group starts (one extra entry: gstart[ngroups] = number of keys) and
+        // the split of the compositing work by list length
+        DL_CK(launch_exclusive_scan(W.gcount.as<uint32_t>(), W.gstart.as<uint32_t>(), ngroups + 1,
+                                    d_total32, W.gscan_tmp.p, s),
+              "group scan");
+    }
+    const uint32_t* d_nkeys = W.gstart.as<uint32_t>() + ngroups;
+    if (direct) {
+        // partitioned above
+    } else if (warp_path) {
+        GroupSlices sl;
+        sl.start = W.gstart.as<uint32_t>();
+        DL_CK(launch_partition_warp(gwork, n_work, sl, uint32_t(ctx->warp_cap),
+                                    ctx->warp_cap < 1024 ? 1024u : 0u, items, block_items, d_meta,
                                     on_device ? d_nkeys : nullptr, key_cap,
                                     on_device ? d_status : nullptr, s),
               "partition");
@@ -1119,10 +1205,12 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
             return fail(ctx, DL_ERR_CAPACITY, "a tile list holds %lld keys (binned limit %d)",
                         (long long)max_len, kLargeCap);
         // capacities for the signature's later frames: a quarter more keys
-        // (and 65,536) than this frame, lists up to 1.25 times its longest
+        // (and 16 a group, the slack of the emission slices, and 65,536)
+        // than this frame, lists up to 1.25 times its longest
         hint.sized = false;
+        hint.slices_ready = false;
         if (warp_path && binned) {
-            const int64_t want = nk + nk / 4 + 65536;
+            const int64_t want = nk + nk / 4 + 16 * ngroups + 65536;
             int bc = 2048;
             while (bc < kLargeCap && bc < max_len + max_len / 4) bc <<= 1;
             if (want < (int64_t(1) << 31) - 2 && block_smem_bytes(bc) <= max_smem_optin(ctx->device)) {
@@ -1161,18 +1249,39 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
         raycol = W.raycol.as<float>();
     }
     int sort_bits = 0;
-    int launches = int32_t((nv + kCamBatch - 1) / kCamBatch) + 1 + 3 + (n_work > 0 ? 1 : 0);
+    // cameras, projection, scan, partition (direct emission: and the counts'
+    // padding, the cursor reset and the gated re-emission)
+    int launches = int32_t((nv + kCamBatch - 1) / kCamBatch) + 1 + 3 + (n_work > 0 ? 1 : 0) +
+                   (direct ? 3 : 0);
     DL_CK(W.keys[0].reserve(8 * size_t(nk > 0 ? nk : 1)), "alloc keys");
     if (binned) {
         // ---- binned keys, sorted per tile in shared memory while compositing ----
-        DL_CK(W.gfill.reserve(4 * size_t(ngroups)), "alloc");
-        DL_CK(cudaMemcpyAsync(W.gfill.p, W.gstart.p, 4 * size_t(ngroups), cudaMemcpyDeviceToDevice, s),
-              "cursors");
         DL_CK(mark(3), "event");
-        DL_CK(launch_emit_binned(pp, nv, W.meta.as<uint4>(), W.gfill.as<uint32_t>(),
-                                 W.keys[0].as<unsigned long long>(), on_device ? d_nkeys : nullptr,
-                                 key_cap, on_device ? d_status : nullptr, s),
-              "emit binned");
+        if (!direct) {
+            DL_CK(cudaMemcpyAsync(cursor, W.gstart.p, 4 * size_t(ngroups), cudaMemcpyDeviceToDevice,
+                                  s),
+                  "cursors");
+            DL_CK(launch_emit_binned(pp, nv, W.meta.as<uint4>(), cursor,
+                                     W.keys[0].as<unsigned long long>(),
+                                     on_device ? d_nkeys : nullptr, key_cap,
+                                     on_device ? d_status : nullptr, s),
+                  "emit binned");
+            if (warp_path && hint.sized && ctx->direct_emit) {
+                // the signature's first slices for keys emitted by the
+                // projection, from this frame's counts
+                for (DevBuf& b : hint.slices)
+                    DL_CK(b.reserve(4 * size_t(ngroups + 1)), "alloc slices");
+                DL_CK(launch_pad_counts(W.gcount.as<uint32_t>(), nullptr, ngroups,
+                                        hint.slices[hint.cur ^ 1].as<uint32_t>(), s),
+                      "pad counts");
+                DL_CK(launch_exclusive_scan(hint.slices[hint.cur ^ 1].as<uint32_t>(),
+                                            hint.slices[hint.cur].as<uint32_t>(), ngroups + 1,
+                                            d_total32, W.gscan_tmp.p, s),
+                      "slice scan");
+                hint.slices_ready = true;
+                launches += 4;
+            }
+        }
         DL_CK(mark(4), "event");
         DL_CK(mark(5), "event");
         DL_CK(mark(6), "event");
@@ -1196,8 +1305,7 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
             fd.raycol = raycol;
             fd.items = items;
             fd.gwork = G->gwork.as<int4>();
-            fd.block_list = large_list;
-            fd.gstart = W.gstart.as<uint32_t>();
+            fd.block_items = block_items;
             fd.meta = d_meta;
             fd.status = d_meta + 7;
             fd.n_work = n_work;
@@ -1228,7 +1336,8 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
                                                ctx->eval_transposed[mode], s),
                   "composite rays (large lists)");
         }
-        launches += 1 + (n_small > 0 ? 1 : 0) + (n_mid > 0 ? 1 : 0) + (n_large > 0 ? 1 : 0);
+        launches += (direct ? 0 : 1) + (n_small > 0 ? 1 : 0) + (n_mid > 0 ? 1 : 0) +
+                    (n_large > 0 ? 1 : 0);
     } else {
         // ---- global tile keys and a stable LSD radix sort ----
         DL_CK(W.count.reserve(4 * size_t(ne)), "alloc counts");

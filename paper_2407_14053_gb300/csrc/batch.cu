@@ -137,10 +137,9 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
         fd.keys = b->at<unsigned long long>(z.o_keys);
         fd.rec = b->at<float4>(z.o_rec);
         fd.raycol = b->at<float>(z.o_raycol);
-        fd.block_list = b->at<int32_t>(z.o_lists);
-        fd.items = b->at<int4>(z.o_lists + align_up(4 * size_t(z.nwork_cap), 16));
+        fd.items = b->at<int4>(z.o_lists);
+        fd.block_items = b->at<int4>(z.o_lists + 16 * size_t(z.nwork_cap));
         fd.gwork = z.G->gwork.as<int4>();
-        fd.gstart = b->at<uint32_t>(z.o_gstart);
         fd.meta = b->at<uint32_t>(z.o_zero + align_up(8 * size_t(z.ng_cap) + 4, 16));
         fd.status = b->status_d() + i;
         fd.n_work = z.G->n_gwork;
@@ -173,8 +172,10 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
                                  b->at<unsigned long long>(z.o_keys), gstart + z.ngroups,
                                  uint32_t(z.key_cap), fd.status, s),
               "emit binned");
-        DL_CK(launch_partition_warp(z.G->gwork.as<int4>(), z.G->n_gwork, gstart, kWarpCap1, kWarpCap2,
-                                    const_cast<int4*>(fd.items), const_cast<int32_t*>(fd.block_list),
+        GroupSlices sl;
+        sl.start = gstart;
+        DL_CK(launch_partition_warp(z.G->gwork.as<int4>(), z.G->n_gwork, sl, kWarpCap1, kWarpCap2,
+                                    const_cast<int4*>(fd.items), const_cast<int4*>(fd.block_items),
                                     meta, gstart + z.ngroups, uint32_t(z.key_cap), fd.status, s),
               "partition");
     }
@@ -304,7 +305,7 @@ dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plan
         z.o_zero = take(z.zero_bytes);
         z.o_gstart = take(4 * size_t(z.ng_cap + 1));
         z.o_keys = take(8 * size_t(z.key_cap));
-        z.o_lists = take(align_up(4 * size_t(z.nwork_cap), 16) + 16 * size_t(z.nwork_cap) + 16);
+        z.o_lists = take(32 * size_t(z.nwork_cap) + 16);  // items, then block items
         z.o_raycol = take(12 * size_t(std::max<int64_t>(z.nrays_cap, 1)));
         z.cam_first = b->total_views;
         b->total_views += z.nv_cap;

@@ -751,11 +751,53 @@ __device__ void warp_sort(const unsigned long long* __restrict__ keys, uint32_t 
     int NB = 1;
     while (NB < len) NB <<= 1;
     if (NB > kWarpBuckets) NB = kWarpBuckets;
+    // Depths cluster (a dense core in front of a sparse background), so
+    // buckets spread evenly over [lo, hi] crowd where the keys are.  With 64
+    // buckets or more the mapping is equi-depth at a coarse grain: a first
+    // count over kCoarse even bins of [lo, hi] gives bin c a share of the
+    // buckets in proportion to its keys (at least one when it has any), and
+    // a key takes the bucket of its position within its bin.  The bucket is
+    // non-decreasing in the depth word (t is; so is the bin; within a bin so
+    // are t - c, exact, and its scaled integer part; the bins' bucket ranges
+    // are disjoint and in order), which is all the phases below need.  The
+    // bins' table takes the last kCoarse bucket words.
+    constexpr int kCoarse = 32;
+    const bool equi = NB >= 2 * kCoarse;
+    if (equi && NB > kWarpBuckets - kCoarse) NB = kWarpBuckets - kCoarse;
+    uint32_t* const table = W.bstart + (kWarpBuckets - kCoarse);
     for (int b = lane; b < NB; b += 32) W.bstart[b] = 0u;
+    const float scale = float(equi ? kCoarse : NB) / (float(hi - lo) + 1.0f);
+    if (equi) {
+        auto bin = [&](unsigned long long k) {
+            return min(kCoarse - 1, int(float(uint32_t(k >> 32) - lo) * scale));
+        };
+        table[lane] = 0u;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < KPL; ++j)
+            if (j * 32 + lane < len) atomicAdd(&table[bin(kr[j])], 1u);
+        if (!in_regs)
+            for (int i = KPL * 32 + lane; i < len; i += 32) atomicAdd(&table[bin(keys[start + i])], 1u);
+        __syncwarp();
+        const uint32_t nc = table[lane];  // keys in bin `lane`
+        const uint32_t nb = nc * uint32_t(NB - kCoarse) / uint32_t(len) + (nc ? 1u : 0u);
+        uint32_t inc = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        __syncwarp();
+        table[lane] = (inc - nb) | (nb << 16);  // first bucket | buckets << 16
+    }
     __syncwarp();
-    const float scale = float(NB) / (float(hi - lo) + 1.0f);
     auto bucket = [&](unsigned long long k) {
-        return min(NB - 1, int(float(uint32_t(k >> 32) - lo) * scale));
+        const float t = float(uint32_t(k >> 32) - lo) * scale;
+        if (!equi) return min(NB - 1, int(t));
+        const int c = min(kCoarse - 1, int(t));
+        const uint32_t q = table[c];
+        const int nb = int(q >> 16);
+        return int(q & 0xFFFFu) + min(nb - 1, int((t - float(c)) * float(nb)));
     };
     // the first KPL * 32 keys are in registers, the rest are re-read
 #pragma unroll
@@ -1188,9 +1230,10 @@ composite_rays_block_kernel(const FrameDesc* __restrict__ F, const int64_t* __re
     while (item < n_items) {
         const int f = frame_of(prefix, n_frames, item);
         const FrameDesc& d = F[f];
-        const int4 wi = d.gwork[d.block_list[item - __ldg(prefix + f)]];
-        const uint32_t start = d.gstart[wi.x];
-        const int len = int(d.gstart[wi.x + 1] - start);
+        const int4 bi = d.block_items[item - __ldg(prefix + f)];
+        const int4 wi = d.gwork[bi.z];
+        const uint32_t start = uint32_t(bi.y);
+        const int len = bi.w;
         if (len > cap) {
             if (threadIdx.x == 0) atomicOr(d.status, 2u);
         } else {
@@ -1199,20 +1242,11 @@ composite_rays_block_kernel(const FrameDesc* __restrict__ F, const int64_t* __re
             const int xm = (tile % d.cp.ntx) * d.cp.tile_w + (d.cp.tile_w >> 1);
             const int ym = (tile / d.cp.ntx) * d.cp.tile_h + (d.cp.tile_h >> 1);
             const int qx = warp & 1, qy = warp >> 1;
+            // the keys carry the quadrant bits (bit q: the record's pixel
+            // box overlaps quadrant q, x half + 2 * y half, of the tile)
             block_sort<0>(d.keys, start, len, cap, sk, cnt);
-            const int64_t vbase = int64_t(v) * d.cp.n;
-            // quadrant bits: bit q set when the record's pixel box overlaps
-            // quadrant q (x half + 2 * y half) of the tile
-            for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                const unsigned long long k = sk[i];
-                const uint4 box = d.cp.meta[vbase + (uint32_t(k) >> 4)];
-                const int c0 = int(box.x & 0xFFFFu), c1 = int(box.x >> 16);
-                const int rr0 = int(box.y & 0xFFFFu), rr1 = int(box.y >> 16);
-                const uint32_t lo_x = c0 < xm, hi_x = c1 >= xm, lo_y = rr0 < ym, hi_y = rr1 >= ym;
-                sk[i] = k | ((lo_x & lo_y) | ((hi_x & lo_y) << 1) | ((lo_x & hi_y) << 2) |
-                             ((hi_x & hi_y) << 3));
-            }
             __syncthreads();
+            const int64_t vbase = int64_t(v) * d.cp.n;
             for (int r0 = wi.y; r0 < wi.z; r0 += 32) {
                 const int rid = r0 + lane;
                 const int2 ray = rid < wi.z ? d.grouped[rid] : make_int2(0, -1);
@@ -1267,23 +1301,27 @@ __global__ void batch_prefix_kernel(const FrameDesc* __restrict__ F, int n_frame
 // Items of the warp classes: DirectL groups with fewer than 65536 rays and
 // at most cap1 keys become self-contained items at the front of `items`,
 // those with cap1 < keys <= cap2 at the back (cap2 = 0: no second class); the
-// rest go to the block list (as gwork indices).
-// meta = {n_items1, n_block, max keys, -, n_items2}.
+// rest become block items {group, first key, gwork index, keys}.
+// meta = {n_items1, n_block, max keys, -, n_items2}.  Nothing is written
+// when the frame's keys were not all emitted (*total_keys > key_cap, or
+// status bit 0 already set).
 __global__ void partition_warp_kernel(const int4* __restrict__ gwork, int64_t n_work,
-                                      const uint32_t* __restrict__ gstart, uint32_t cap1,
-                                      uint32_t cap2, int4* __restrict__ items,
-                                      int32_t* __restrict__ block_list, uint32_t* __restrict__ meta,
+                                      GroupSlices S, uint32_t cap1, uint32_t cap2,
+                                      int4* __restrict__ items, int4* __restrict__ block_items,
+                                      uint32_t* __restrict__ meta,
                                       const uint32_t* __restrict__ total_keys, uint32_t key_cap,
                                       uint32_t* __restrict__ status) {
     if (total_keys && *total_keys > key_cap) {  // keys were not emitted
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 1u);
         return;
     }
+    if (status && (*status & 1u)) return;
+    const uint32_t* __restrict__ first = S.use_alt && *S.use_alt ? S.start_alt : S.start;
     for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < n_work;
          w += int64_t(gridDim.x) * blockDim.x) {
         const int4 wi = gwork[w];
-        const uint32_t st = gstart[wi.x];
-        const uint32_t len = gstart[wi.x + 1] - st;
+        const uint32_t st = first[wi.x];
+        const uint32_t len = (S.cursor ? S.cursor[wi.x] : S.start[wi.x + 1]) - st;
         const uint32_t nr = uint32_t(wi.z - wi.y);
         const int4 it = make_int4(wi.x, int(st), wi.y, int((nr << 16) | len));
         if (nr < 65536u && len <= cap1)
@@ -1291,7 +1329,7 @@ __global__ void partition_warp_kernel(const int4* __restrict__ gwork, int64_t n_
         else if (nr < 65536u && len <= cap2)
             items[n_work - 1 - int64_t(atomicAdd(meta + 4, 1u))] = it;
         else
-            block_list[atomicAdd(meta + 1, 1u)] = int32_t(w);
+            block_items[atomicAdd(meta + 1, 1u)] = make_int4(wi.x, int(st), int(w), int(len));
         atomicMax(meta + 2, len);
     }
 }
@@ -1506,16 +1544,16 @@ cudaError_t launch_composite_rays_block(int block_cap, const FrameDesc* frames,
                              prefix + 2 * (n_frames + 1), n_frames, block_cap, cursor, pairs, s);
 }
 
-cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
-                                  uint32_t cap1, uint32_t cap2, int4* items, int32_t* block_list,
+cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const GroupSlices& slices,
+                                  uint32_t cap1, uint32_t cap2, int4* items, int4* block_items,
                                   uint32_t* meta, const uint32_t* total_keys, uint32_t key_cap,
                                   uint32_t* status, cudaStream_t s) {
     if (n_work <= 0) return cudaSuccess;
     int64_t grid = (n_work + 255) / 256;
     const int64_t lim = int64_t(num_sms()) * 16;
     if (grid > lim) grid = lim;
-    partition_warp_kernel<<<unsigned(grid), 256, 0, s>>>(gwork, n_work, gstart, cap1, cap2, items,
-                                                         block_list, meta, total_keys, key_cap,
+    partition_warp_kernel<<<unsigned(grid), 256, 0, s>>>(gwork, n_work, slices, cap1, cap2, items,
+                                                         block_items, meta, total_keys, key_cap,
                                                          status);
     return cudaGetLastError();
 }

@@ -102,6 +102,13 @@ struct ProjectOut {
     unsigned long long* total;  // sum of tiles touched (atomic)
     uint32_t* gcount;  // optional: keys per (view, tile) group (atomic; zeroed by caller)
     unsigned long long* visible = nullptr;  // optional: records written (atomic)
+    // launch_project_direct only (meta and gcount unused there)
+    unsigned long long* keys = nullptr;  // binned keys, written into their group's slice
+    uint32_t* cursor = nullptr;          // per group: next slot (starts at slice[g])
+    const uint32_t* slice = nullptr;     // group g's slots: [slice[g], slice[g + 1])
+    uint32_t key_cap = 0;                // slots past the key buffer are never written
+    uint32_t* overflow = nullptr;        // |= 1 when a key found its slice full
+    const uint32_t* gate = nullptr;      // keys-only pass: runs only when *gate != 0
 };
 
 template <typename T>
@@ -160,8 +167,24 @@ cudaError_t launch_group_slots(const int2* grouped, int64_t n_rays, const uint32
 cudaError_t launch_store_cams(const CamBatch& b, int32_t n, Cam* dst, cudaStream_t s);
 cudaError_t launch_project(int dtype, const void* const* attrs, const ProjectParams& p,
                            const Cam* cams, int32_t nv, ProjectOut out, cudaStream_t s);
-// Keys depth << 32 | Gaussian << 4 (Gaussians < 2^28; the low nibble is left
-// for the block class's quadrant bits) into their group's slice
+// Projection that emits the binned keys itself (no tile metadata, no
+// emission pass) into slices laid out before the launch (out.slice,
+// out.cursor, out.keys, out.key_cap, out.overflow); keys_only: the pass that
+// re-emits a frame whose slices overflowed, gated by *out.gate, writing
+// neither records nor totals.
+cudaError_t launch_project_direct(int dtype, const void* const* attrs, const ProjectParams& p,
+                                  const Cam* cams, int32_t nv, ProjectOut out, bool keys_only,
+                                  cudaStream_t s);
+// padded[g] = count + count / 8 + 16 with count = cursor[g] - slice[g]
+// (slice == nullptr: count = cursor[g]); padded[n_groups] = 0.
+cudaError_t launch_pad_counts(const uint32_t* cursor, const uint32_t* slice, int64_t n_groups,
+                              uint32_t* padded, cudaStream_t s);
+// cursor[g] = start[g] for every group when *flag != 0 (else nothing).
+cudaError_t launch_reset_cursor(const uint32_t* flag, const uint32_t* start, int64_t n_groups,
+                                uint32_t* cursor, cudaStream_t s);
+// Keys depth << 32 | Gaussian << 4 | quadrant bits (Gaussians < 2^28; bit q
+// of the nibble: the pixel box overlaps quadrant q, x half + 2 * y half, of
+// the tile) into their group's slice
 // [gstart[g], gstart[g+1]): cursor[g] holds gstart[g] at the launch (a copy
 // made by the caller) and is advanced by atomics.
 // total_keys (optional) = gstart + n_groups: when it exceeds key_cap no key is
@@ -284,11 +307,22 @@ cudaError_t launch_composite_full_binned(const CompositeParams& p, const int32_t
 // persistent over self-contained items {group, first key, first ray,
 // rays << 16 | keys} made by launch_partition_warp: groups of at most cap1
 // keys at the front of `items`, cap1 < keys <= cap2 at the back (from
-// items[n_work - 1] down), the other groups' gwork indices in block_list;
-// meta = {n_items1, n_block, max keys, -, n_items2}.  When *total_keys
-// (gstart[n_groups]) exceeds key_cap nothing is written and status |= 1.
-cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint32_t* gstart,
-                                  uint32_t cap1, uint32_t cap2, int4* items, int32_t* block_list,
+// items[n_work - 1] down), the other groups as block items {group, first
+// key, gwork index, keys}; meta = {n_items1, n_block, max keys, -,
+// n_items2}.  When *total_keys (optional: the slices' end) exceeds key_cap
+// nothing is written and status |= 1; nothing is written either when status
+// bit 0 is already set (keys were dropped).
+// Where each group's keys are: [start[g], start[g + 1]) when cursor is
+// null; else [s[g], cursor[g]) with s = start_alt when *use_alt != 0, else
+// start (the slices of a frame whose keys the projection emitted).
+struct GroupSlices {
+    const uint32_t* start = nullptr;
+    const uint32_t* start_alt = nullptr;
+    const uint32_t* use_alt = nullptr;
+    const uint32_t* cursor = nullptr;
+};
+cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const GroupSlices& slices,
+                                  uint32_t cap1, uint32_t cap2, int4* items, int4* block_items,
                                   uint32_t* meta, const uint32_t* total_keys, uint32_t key_cap,
                                   uint32_t* status, cudaStream_t s);
 
@@ -297,13 +331,12 @@ cudaError_t launch_partition_warp(const int4* gwork, int64_t n_work, const uint3
 struct FrameDesc {
     CompositeParams cp;
     const int2* grouped;              // {pixel, ray id} per grouped ray
-    const unsigned long long* keys;   // binned keys (slices by gstart)
+    const unsigned long long* keys;   // binned keys (the items give each group's slice)
     const float4* rec;                // records, view-major
     float* raycol;                    // 3 floats per ray id
     const int4* items;                // launch_partition_warp output
     const int4* gwork;                // {group, ray begin, ray end, -}
-    const int32_t* block_list;
-    const uint32_t* gstart;
+    const int4* block_items;          // {group, first key, gwork index, keys}
     const uint32_t* meta;             // {n_items1, n_block, max, -, n_items2}
     uint32_t* status;                 // bit 0 keys overflow, bit 1 list longer than the block cap
     int64_t n_work;

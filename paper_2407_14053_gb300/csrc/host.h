@@ -96,6 +96,7 @@ struct PendingFrame {
     int64_t n_visible;
     int64_t frame = -1;  // frame number; its device counters arrive by a readback
     int32_t status = 0;
+    int32_t reemitted = 0;
 };
 
 // Capacities a frame signature (scene, display, mode, tile, view size) runs
@@ -106,10 +107,17 @@ struct PendingFrame {
 // dropped on the device (its output left untouched, its status word set),
 // and the next frame of the signature is sized on the host again, as is one
 // after a frame that used more than 85 % of either capacity.
+// With the keys emitted by the projection, the signature also keeps the
+// slices of the key buffer its next frame emits into: every group gets its
+// key count in the last frame plus an eighth and 16 (slices[cur]); a frame
+// writes the next layout into slices[cur ^ 1] and flips cur.
 struct FrameHint {
     bool sized = false;
     int32_t block_cap = 2048;
     int64_t key_cap = 0;
+    bool slices_ready = false;
+    int cur = 0;
+    DevBuf slices[2];  // n_groups + 1 slot offsets each
 };
 using FrameSig = std::array<int32_t, 7>;
 
@@ -185,6 +193,7 @@ struct dl_ctx {
     int32_t sort_mode = DL_SORT_AUTO;
     int32_t eval_transposed[3] = {1, 0, 1};  // per mode
     int32_t warp_cap = 512;
+    bool direct_emit = true;  // DL_OPT_KEY_EMISSION
     int32_t std_view_w = 0, std_view_h = 0;  // DL_OPT_STANDARD_VIEW_SIZE (0: panel)
     int32_t heap_cap = 128;                  // DL_OPT_HEAP_CAPACITY
     bool timing = false;

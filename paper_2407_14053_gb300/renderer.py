@@ -172,6 +172,12 @@ class Renderer:
         intersections kept per ray (1..256)."""
         B.dl_set_option(self.ctx, B.DL_OPT_HEAP_CAPACITY, int(cap))
 
+    def set_key_emission(self, in_projection: bool = True) -> None:
+        """Binned DirectL frames: True (default) has the projection kernel
+        emit the tile keys into slices laid out from the previous frame;
+        False uses tile metadata and a separate emission kernel."""
+        B.dl_set_option(self.ctx, B.DL_OPT_KEY_EMISSION, 1 if in_projection else 0)
+
     def set_warp_cap(self, cap: int) -> None:
         """Longest tile list (512 or 1024 keys; 0 = none) one warp composites."""
         B.dl_set_option(self.ctx, B.DL_OPT_WARP_LIST_CAP, int(cap))

@@ -58,7 +58,7 @@ int main(void) {
   P(dl_display_params, repurpose) P(dl_display_params, reverse_views) P(dl_display_params, rig)
   P(dl_frame_stats, ms_total)
   P(dl_frame_stats, max_list) P(dl_frame_stats, lists_small) P(dl_frame_stats, n_visible)
-  P(dl_frame_stats, status)
+  P(dl_frame_stats, status) P(dl_frame_stats, reemitted)
   return 0;
 }
 '''
