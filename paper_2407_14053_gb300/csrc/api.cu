@@ -1205,12 +1205,13 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
             return fail(ctx, DL_ERR_CAPACITY, "a tile list holds %lld keys (binned limit %d)",
                         (long long)max_len, kLargeCap);
         // capacities for the signature's later frames: a quarter more keys
-        // (and 16 a group, the slack of the emission slices, and 65,536)
-        // than this frame, lists up to 1.25 times its longest
+        // (and 65,536) than the slices this frame's counts lay out (its keys,
+        // an eighth more and 16 a group), lists up to 1.25 times its longest
         hint.sized = false;
         hint.slices_ready = false;
         if (warp_path && binned) {
-            const int64_t want = nk + nk / 4 + 16 * ngroups + 65536;
+            const int64_t laid = nk + nk / 8 + 16 * ngroups;
+            const int64_t want = laid + laid / 4 + 65536;
             int bc = 2048;
             while (bc < kLargeCap && bc < max_len + max_len / 4) bc <<= 1;
             if (want < (int64_t(1) << 31) - 2 && block_smem_bytes(bc) <= max_smem_optin(ctx->device)) {
