@@ -161,7 +161,7 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
     DL_CK(rtmp.reserve(radix_tmp_bytes(nr)), "alloc");
     DL_CK(ranges.reserve(8 * size_t(ngroups)), "alloc");
     DL_CK(launch_ray_group_keys(R.ray_view.as<uint32_t>(), R.ray_pix.as<uint32_t>(), nr, tw, th,
-                                G->ntx, G->ntiles, k0.as<unsigned long long>(), v0.as<uint32_t>(), s),
+                                G->ntx, D.q.nv, k0.as<unsigned long long>(), v0.as<uint32_t>(), s),
           "group keys");
     int alt = 0;
     DL_CK(radix_sort_pairs(k0.as<unsigned long long>(), v0.as<uint32_t>(),
@@ -185,10 +185,15 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
     DL_CK(cudaMemcpyAsync(h_ranges.data(), ranges.p, 8 * size_t(ngroups), cudaMemcpyDeviceToHost, s),
           "copy");
     DL_CK(cudaStreamSynchronize(s), "sync");
+    // h_ranges[tile * nv + v]: the rays of group g = v * ntiles + tile, in
+    // the grouping's (tile-major) order
+    const int64_t nv = D.q.nv;
+    auto group_of = [&](int64_t k) { return (k % nv) * G->ntiles + k / nv; };
     std::vector<int4> work;
     work.reserve(size_t(nr / kRaysPerBlock + ngroups / 4 + 16));
-    for (int64_t g = 0; g < ngroups; ++g) {
-        const uint2 r = h_ranges[size_t(g)];
+    for (int64_t k = 0; k < ngroups; ++k) {
+        const uint2 r = h_ranges[size_t(k)];
+        const int64_t g = group_of(k);
         for (uint32_t b = r.x; b < r.y; b += kRaysPerBlock)
             work.push_back(make_int4(int(g), int(b), int(std::min<uint32_t>(b + kRaysPerBlock, r.y)), 0));
     }
@@ -198,9 +203,9 @@ dl_status get_groups(dl_ctx* ctx, Display& D, RaySet& R, int32_t tw, int32_t th,
         DL_CK(cudaMemcpyAsync(G->work.p, work.data(), 16 * work.size(), cudaMemcpyHostToDevice, s),
               "copy");
     std::vector<int4> gwork;
-    for (int64_t g = 0; g < ngroups; ++g) {
-        const uint2 r = h_ranges[size_t(g)];
-        if (r.y > r.x) gwork.push_back(make_int4(int(g), int(r.x), int(r.y), 0));
+    for (int64_t k = 0; k < ngroups; ++k) {
+        const uint2 r = h_ranges[size_t(k)];
+        if (r.y > r.x) gwork.push_back(make_int4(int(group_of(k)), int(r.x), int(r.y), 0));
     }
     G->n_gwork = int64_t(gwork.size());
     DL_CK(G->gwork.reserve(16 * std::max<size_t>(gwork.size(), 1)), "alloc");
@@ -1411,7 +1416,9 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
         rbk->hint = &hint;
         W.rb_next = (W.rb_next + 1) % kReadbacks;
     }
-    launches += 1;
+    launches += (mode == DL_STANDARD || lowres || sr)
+                    ? 1
+                    : reorder_launches(G->slot_of.as<uint32_t>(), 3 * int64_t(w) * h, dst);
     DL_CK(mark(8), "event");
     st = out_finish(ctx, out, kind, dst, out_bytes, s, cs);
     if (st) return st;

@@ -302,14 +302,15 @@ __global__ void ray_attr_kernel(int32_t w, int64_t n, const uint16_t* __restrict
 
 __global__ void group_keys_kernel(const uint32_t* __restrict__ ray_view,
                                   const uint32_t* __restrict__ ray_pix, int64_t n, int32_t tw,
-                                  int32_t th, int32_t ntx, int32_t ntiles,
+                                  int32_t th, int32_t ntx, int32_t nv,
                                   unsigned long long* __restrict__ keys,
                                   uint32_t* __restrict__ vals) {
     for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n;
          r += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t px = ray_pix[r];
         const uint32_t row = px >> 16, col = px & 0xFFFF;
-        const uint64_t g = uint64_t(ray_view[r]) * ntiles + (row / th) * ntx + (col / tw);
+        // tile-major: the views of a tile are neighbours in the grouping
+        const uint64_t g = uint64_t((row / th) * ntx + (col / tw)) * nv + ray_view[r];
         // inside the tile, order rays along a Morton curve so that each warp's
         // rays cover a compact patch
         uint32_t x = col % tw, y = row % th, m = 0;
@@ -434,10 +435,10 @@ cudaError_t launch_ray_attributes(const DisplayQ& q, const uint16_t* V, const vo
 }
 
 cudaError_t launch_ray_group_keys(const uint32_t* ray_view, const uint32_t* ray_pix, int64_t n_rays,
-                                  int32_t tile_w, int32_t tile_h, int32_t ntx, int32_t ntiles,
+                                  int32_t tile_w, int32_t tile_h, int32_t ntx, int32_t nv,
                                   unsigned long long* keys, uint32_t* vals, cudaStream_t s) {
     group_keys_kernel<<<grid_for(n_rays, 256), 256, 0, s>>>(ray_view, ray_pix, n_rays, tile_w,
-                                                             tile_h, ntx, ntiles, keys, vals);
+                                                             tile_h, ntx, nv, keys, vals);
     return cudaGetLastError();
 }
 

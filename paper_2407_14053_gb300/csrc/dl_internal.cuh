@@ -143,10 +143,13 @@ cudaError_t launch_ray_table(const DisplayQ& q, const uint16_t* V, const uint32_
                              uint32_t* ray_of, void* tmp, uint32_t* d_n_rays, cudaStream_t s);
 cudaError_t launch_ray_attributes(const DisplayQ& q, const uint16_t* V, const void* tmp,
                                   uint32_t* ray_view, uint32_t* ray_pix, cudaStream_t s);
-// Group keys of rays for a compositing tile shape: key = (v*ntiles + tile) << 16
-// | Morton code of the pixel inside the tile; value = ray id.
+// Group keys of rays for a compositing tile shape: key = (tile*nv + v) << 16
+// | Morton code of the pixel inside the tile; value = ray id.  Sorted, the
+// rays are grouped tile-major (every view of a tile, then the next tile), so
+// a tile's ray colours are one run and the reorder's gathers for a patch of
+// the panel stay in a few kilobytes.
 cudaError_t launch_ray_group_keys(const uint32_t* ray_view, const uint32_t* ray_pix, int64_t n_rays,
-                                  int32_t tile_w, int32_t tile_h, int32_t ntx, int32_t ntiles,
+                                  int32_t tile_w, int32_t tile_h, int32_t ntx, int32_t nv,
                                   unsigned long long* keys, uint32_t* vals, cudaStream_t s);
 // (view, row, col) int32 triplets of every ray.
 cudaError_t launch_rays_export(const uint32_t* ray_view, const uint32_t* ray_pix, int64_t n_rays,
@@ -278,6 +281,8 @@ cudaError_t launch_composite_rays(const CompositeParams& p, const int4* work, in
 // Nothing is written when skip (optional, device) holds a nonzero word.
 cudaError_t launch_reorder(const uint32_t* ray_of, const float* raycol, int64_t n_subpixels,
                            float* out, const uint32_t* skip, cudaStream_t s);
+// kernels launch_reorder launches for these arguments (1 or 2)
+int reorder_launches(const uint32_t* ray_of, int64_t n_subpixels, const float* out);
 // Standard paradigm: every pixel of every view into Mm (nv x h x w x 3).
 cudaError_t launch_composite_full(const CompositeParams& p, int32_t nv, const uint2* ranges,
                                   const uint32_t* vals, const float4* rec, float* Mm,
