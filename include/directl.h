@@ -294,9 +294,10 @@ enum { DL_OPT_SORT_MODE = 1, DL_OPT_EVAL_DIRECTL = 2, DL_OPT_EVAL_STANDARD = 3,
  * highest-density point t_j = (mu - o)^T S^-1 d / (d^T S^-1 d) > 0.2 (Eqs.
  * (16)-(17)) enters a max-heap that keeps the c_h smallest (t, index); they
  * are blended in t order (alpha clamped to 0.99, stop before T < 1e-4) with
- * the SH colour at d.  An implicit 8-wide tree of the Gaussians' alpha >=
- * 1/255 boxes over the scene's stored order is built on the first such frame
- * of a scene and kept with it. */
+ * the SH colour at d.  An 8-wide tree of the Gaussians' alpha >= 1/255
+ * boxes (binary SAH splits over the scene's stored Morton order, collapsed
+ * into 8-wide nodes; Sec. 7) is built on the GPU on the first such frame of
+ * a scene and kept with it. */
 /* DL_OPT_STANDARD_VIEW_SIZE: resolution at which DL_STANDARD renders each
  * view, value = (view_w << 16) | view_h, 0 = the panel's (HR).  Below panel
  * resolution (the LR / MR configurations of the paper's experiments) every

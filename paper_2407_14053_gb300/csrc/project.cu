@@ -299,7 +299,7 @@ __global__ void emit_keys_kernel(ProjectParams p, int32_t nv, const uint4* __res
 // that the Gaussian's pixel box overlaps quadrant q (x half + 2 * y half) of
 // the tile, which the block class uses to split a group among its warps;
 // the index is unique in a group, so the nibble never decides the order.
-constexpr int kEmitRounds = 2;
+constexpr int kEmitRounds = 3;
 
 // One warp's keys of one view: lane i holds a Gaussian touching cnt tiles
 // (tiles [tx0, tx0 + span) x [ty0, ...), group base vb = view * tiles,
