@@ -676,7 +676,7 @@ def main():
     scene = W.make_scene(wl.scene)
     r = Renderer(local)
     if args.two_pass_emission:
-        r.set_key_emission(False)
+        r.set_key_emission("two_pass")
     sid = r.load_gaussians(scene, wl.scene.dtype)
     t0 = time.perf_counter()
     did = r.set_display(d)
@@ -833,7 +833,9 @@ def main():
 
     # ---- rooflines of the other stages (HBM-bound; per frame) ----
     ne = d.num_views * wl.scene.n
-    if args.two_pass_emission:
+    # the library's default emits the keys from the projection for scenes of
+    # 131,072 Gaussians or more
+    if args.two_pass_emission or wl.scene.n < 131072:
         stages_roof = {
             "project": stage_roofline(
                 "project_kernel (with the camera upload and counter resets before it)",

@@ -278,14 +278,17 @@ enum { DL_OPT_SORT_MODE = 1, DL_OPT_EVAL_DIRECTL = 2, DL_OPT_EVAL_STANDARD = 3,
        DL_OPT_KEY_EMISSION = 7 };
 /* DL_OPT_KEY_EMISSION: where the binned path of DL_DIRECTL / DL_REQUIRED_ONLY
  * writes its tile keys, once a frame of the same signature has been sized.
- * 1 (default): the projection kernel emits every (view, tile, Gaussian) key
- * itself, into per-(view, tile) slices of the key buffer laid out from the
+ * 1: the projection kernel emits every (view, tile, Gaussian) key itself,
+ * into per-(view, tile) slices of the key buffer laid out from the
  * signature's previous frame (its key count per group plus an eighth and
  * 16); a frame whose counts outgrow a slice emits its keys a second time
  * into slices sized from its own counts, on the device, before compositing.
  * 0: the projection writes per-(view, Gaussian) tile metadata and a second
  * kernel emits the keys into slices sized from this frame's counts (Sec. 4
- * step (2) as two passes).  Both give the same keys, so the same image. */
+ * step (2) as two passes).  2 (default): 1 for scenes of at least 131,072
+ * Gaussians, else 0 (a small scene has too few warps in flight to hide the
+ * projection's waits on its cursor atomics).  All give the same keys, so
+ * the same image. */
 /* DL_OPT_HEAP_CAPACITY: c_h of DL_RAYCAST, the number of nearest
  * intersections each ray keeps and blends (1..256, default 128).
  *

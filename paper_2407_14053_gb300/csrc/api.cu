@@ -125,6 +125,9 @@ constexpr int kRaysPerBlock = 128;
 // memory) falls back to the global radix sort.
 constexpr int kSmallCap = 1024;
 constexpr int kLargeCap = 16384;
+// DL_OPT_KEY_EMISSION 2: the projection emits the keys for scenes of at
+// least this many Gaussians
+constexpr int64_t kEmitInProjectionMin = 131072;
 
 size_t max_smem_optin(int device) {
     int v = 0;
@@ -841,9 +844,9 @@ dl_status dl_set_option(dl_ctx* ctx, int32_t option, int64_t value) {
         return DL_OK;
     }
     if (option == DL_OPT_KEY_EMISSION) {
-        if (value != 0 && value != 1)
+        if (value < 0 || value > 2)
             return fail(ctx, DL_ERR_INVALID_ARG, "key emission %lld", (long long)value);
-        ctx->direct_emit = value == 1;
+        ctx->key_emission = int32_t(value);
         return DL_OK;
     }
     if (option == DL_OPT_HEAP_CAPACITY) {
@@ -1084,7 +1087,12 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     const bool on_device = warp_path && hint.sized && ctx->sort_mode != DL_SORT_RADIX;
     // keys emitted by the projection, into the slices the signature's last
     // frame laid out
-    const bool direct = on_device && ctx->direct_emit && hint.slices_ready;
+    // (by default only for scenes of 131,072 Gaussians or more: a warp's
+    // views run one after another, each waiting on its cursor atomics, which
+    // only enough warps in flight hide)
+    const bool emit_in_projection =
+        ctx->key_emission == 1 || (ctx->key_emission == 2 && S.n >= kEmitInProjectionMin);
+    const bool direct = on_device && emit_in_projection && hint.slices_ready;
     DL_CK(W.rec.reserve(16 * kRecordFloat4 * size_t(ne)), "alloc records");
     if (!direct) DL_CK(W.meta.reserve(16 * size_t(ne)), "alloc tile metadata");
     DL_CK(W.gcount.reserve(4 * size_t(ngroups + 1)), "alloc group counts");
@@ -1276,7 +1284,7 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
                                      on_device ? d_nkeys : nullptr, key_cap,
                                      on_device ? d_status : nullptr, s),
                   "emit binned");
-            if (warp_path && hint.sized && ctx->direct_emit) {
+            if (warp_path && hint.sized && emit_in_projection) {
                 // the signature's first slices for keys emitted by the
                 // projection, from this frame's counts
                 for (DevBuf& b : hint.slices)

@@ -193,7 +193,7 @@ struct dl_ctx {
     int32_t sort_mode = DL_SORT_AUTO;
     int32_t eval_transposed[3] = {1, 0, 1};  // per mode
     int32_t warp_cap = 512;
-    bool direct_emit = true;  // DL_OPT_KEY_EMISSION
+    int32_t key_emission = 2;  // DL_OPT_KEY_EMISSION (2: by scene size)
     int32_t std_view_w = 0, std_view_h = 0;  // DL_OPT_STANDARD_VIEW_SIZE (0: panel)
     int32_t heap_cap = 128;                  // DL_OPT_HEAP_CAPACITY
     bool timing = false;

@@ -172,11 +172,14 @@ class Renderer:
         intersections kept per ray (1..256)."""
         B.dl_set_option(self.ctx, B.DL_OPT_HEAP_CAPACITY, int(cap))
 
-    def set_key_emission(self, in_projection: bool = True) -> None:
-        """Binned DirectL frames: True (default) has the projection kernel
-        emit the tile keys into slices laid out from the previous frame;
-        False uses tile metadata and a separate emission kernel."""
-        B.dl_set_option(self.ctx, B.DL_OPT_KEY_EMISSION, 1 if in_projection else 0)
+    def set_key_emission(self, where="auto") -> None:
+        """Binned DirectL frames: "projection" (or True) has the projection
+        kernel emit the tile keys into slices laid out from the previous
+        frame; "two_pass" (or False) uses tile metadata and a separate
+        emission kernel; "auto" (default) picks the projection for scenes of
+        at least 131,072 Gaussians."""
+        value = {True: 1, False: 0, "projection": 1, "two_pass": 0, "auto": 2}[where]
+        B.dl_set_option(self.ctx, B.DL_OPT_KEY_EMISSION, value)
 
     def set_warp_cap(self, cap: int) -> None:
         """Longest tile list (512 or 1024 keys; 0 = none) one warp composites."""

@@ -305,7 +305,7 @@ def test_key_emission_in_projection_matches_two_pass():
              W.light_field_centre(3.7, -6.0), W.light_field_centre(4.0, 0.0)]
     two = Renderer(0)
     try:
-        two.set_key_emission(False)
+        two.set_key_emission("two_pass")
         sid = two.load_gaussians(scene, "f32")
         did = two.set_display(wl.display)
         refs = [_frame(two, sid, did, L, "directl") for L in poses]
@@ -313,6 +313,7 @@ def test_key_emission_in_projection_matches_two_pass():
         two.close()
     r = Renderer(0)
     try:
+        r.set_key_emission("projection")  # the scene is below the default's size threshold
         sid = r.load_gaussians(scene, "f32")
         did = r.set_display(wl.display)
         _frame(r, sid, did, W.light_field_centre(3.5, 0.0), "directl")  # sized, with headroom
