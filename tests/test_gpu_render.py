@@ -615,3 +615,35 @@ def test_hr_with_repurposing_equals_directl(renderer):
         ref = oracle.render_subpixels(oracle.Scene(scene), wl.display, L0, sub, V, src)
         ok, maxerr, nbad = _accept(a[sub], ref, TOL)
         assert nbad == 0, f"{name}: {nbad} subpixels outside tolerance; max |err| {maxerr:.3g}"
+
+
+def test_reorder_tail_and_unaligned_output(renderer):
+    """The reorder writes four subpixels a thread through 16-byte accesses
+    when the output is 16-byte aligned, and the rest (a subpixel count that
+    is not a multiple of four, or an unaligned output) one at a time: a
+    241x135 panel (97,605 subpixels) rendered into an aligned and into a
+    4-byte-offset buffer gives the same frame, which matches the oracle on a
+    sample of subpixels."""
+    d = W.WORKLOADS["tiny"].display.replace(width=241)
+    scene = W.make_scene(W.WORKLOADS["tiny"].scene)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 1.5)
+    n = 3 * d.width * d.height
+    assert n % 4 != 0
+    ref = _frame(renderer, sid, did, L0, "directl")
+    buf = torch.full((n + 1,), -3.0, device="cuda")
+    out = buf[1:].view(d.height, d.width, 3)
+    assert out.data_ptr() % 16 != 0
+    renderer.render(sid, did, L0, "directl", out)
+    torch.cuda.synchronize()
+    assert renderer.stats()["status"] == 0
+    assert np.array_equal(out.cpu().numpy(), ref) and float(buf[0]) == -3.0
+    V, src = _sources(renderer, did, d, "directl")
+    rng = np.random.default_rng(5)
+    sub = np.unique(np.r_[rng.integers(0, n, size=300), np.arange(n - 7, n)])  # and the tail
+    res = oracle.render_subpixels(oracle.Scene(scene), d, L0, sub, V, src)
+    ok, maxerr, nbad = _accept(ref.reshape(-1)[sub], res, TOL)
+    assert nbad == 0, f"{nbad} subpixels outside tolerance; max |err| {maxerr:.3g}"
+    renderer.free_display(did)
+    renderer.free_scene(sid)
