@@ -455,7 +455,7 @@ def load_traffic(kernel: str, workload: str, source_file: str):
     return rec.get("dram_bytes_per_launch")
 
 
-def run_graph_batched(device: int, steps: int) -> dict:
+def run_graph_batched(device: int, steps: int, two_pass: bool = False) -> dict:
     """8K panel, 100 views, 3M Gaussians (BF16): tile shape picked by the
     autotuner, then one frame per step from a captured CUDA graph of the
     frame batch (no host synchronisation inside a frame)."""
@@ -464,6 +464,8 @@ def run_graph_batched(device: int, steps: int) -> dict:
     from paper_2407_14053_gb300 import Renderer
     wl = W.WORKLOADS["8k"]
     r = Renderer(device)
+    if two_pass:
+        r.set_key_emission("two_pass")
     try:
         t0 = time.perf_counter()
         scene = W.make_scene(wl.scene)
@@ -893,7 +895,7 @@ def main():
 
     graph = None
     if not args.no_graph and world == 1:
-        graph = run_graph_batched(local, max(3, args.steps // 4))
+        graph = run_graph_batched(local, max(3, args.steps // 4), args.two_pass_emission)
         graph["uneven_multislot"] = run_multislot(local, max(3, args.steps // 2))
     serving = None
     if not args.no_serving and world == 1:

@@ -125,9 +125,6 @@ constexpr int kRaysPerBlock = 128;
 // memory) falls back to the global radix sort.
 constexpr int kSmallCap = 1024;
 constexpr int kLargeCap = 16384;
-// DL_OPT_KEY_EMISSION 2: the projection emits the keys for scenes of at
-// least this many Gaussians
-constexpr int64_t kEmitInProjectionMin = 131072;
 
 size_t max_smem_optin(int device) {
     int v = 0;
@@ -1090,9 +1087,8 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
     // (by default only for scenes of 131,072 Gaussians or more: a warp's
     // views run one after another, each waiting on its cursor atomics, which
     // only enough warps in flight hide)
-    const bool emit_in_projection =
-        ctx->key_emission == 1 || (ctx->key_emission == 2 && S.n >= kEmitInProjectionMin);
-    const bool direct = on_device && emit_in_projection && hint.slices_ready;
+    const bool in_projection = emit_in_projection(ctx->key_emission, S.n);
+    const bool direct = on_device && in_projection && hint.slices_ready;
     DL_CK(W.rec.reserve(16 * kRecordFloat4 * size_t(ne)), "alloc records");
     if (!direct) DL_CK(W.meta.reserve(16 * size_t(ne)), "alloc tile metadata");
     DL_CK(W.gcount.reserve(4 * size_t(ngroups + 1)), "alloc group counts");
@@ -1284,7 +1280,7 @@ dl_status render_frame(dl_ctx* ctx, int32_t scene_id, int32_t display_id, const 
                                      on_device ? d_nkeys : nullptr, key_cap,
                                      on_device ? d_status : nullptr, s),
                   "emit binned");
-            if (warp_path && hint.sized && emit_in_projection) {
+            if (warp_path && hint.sized && in_projection) {
                 // the signature's first slices for keys emitted by the
                 // projection, from this frame's counts
                 for (DevBuf& b : hint.slices)

@@ -29,6 +29,11 @@ struct Slot {
     int32_t nv_cap = 0;
     // offsets of the slot's device arrays in the arena
     size_t o_rec = 0, o_meta = 0, o_zero = 0, o_gstart = 0, o_keys = 0, o_lists = 0, o_raycol = 0;
+    // keys emitted by the projection: the slices this launch emits into
+    // (A) and the ones its counts lay out for the next launch (B, copied to
+    // A at the end), ng_cap + 1 words each
+    size_t o_slices = 0;
+    bool direct = false;
     size_t zero_bytes = 0;  // gcount | gfill | meta, zeroed by every launch
     int64_t cam_first = 0;  // first camera of the slot in the staging cameras
     // assignment
@@ -160,6 +165,51 @@ dl_status enqueue(dl_batch* b, cudaStream_t s) {
         const Scene& S = *z.S;
         const int32_t nv = z.D->q.nv;
         const void* attrs[5] = {S.mean.p, S.log_scale.p, S.rot.p, S.opacity.p, S.sh.p};
+        if (z.direct) {
+            // the projection emits the keys into slices A (laid out by the
+            // slot's previous launch); B from this launch's counts; a slot
+            // that outgrew A emits again into B (meta word 12: the flag)
+            uint32_t* sa = b->at<uint32_t>(z.o_slices);
+            uint32_t* sb = sa + (z.ng_cap + 1);
+            uint32_t* redo = meta + 12;
+            DL_CK(cudaMemcpyAsync(gfill, sa, 4 * size_t(z.ngroups), cudaMemcpyDeviceToDevice, s),
+                  "cursors");
+            ProjectOut po{b->at<float4>(z.o_rec), nullptr,
+                          reinterpret_cast<unsigned long long*>(meta + 8), nullptr};
+            po.keys = b->at<unsigned long long>(z.o_keys);
+            po.cursor = gfill;
+            po.slice = sa;
+            po.key_cap = uint32_t(z.key_cap);
+            po.overflow = redo;
+            DL_CK(launch_project_direct(S.dtype, attrs, z.pp, b->cams_d() + z.cam_first, nv, po,
+                                        false, s),
+                  "project");
+            DL_CK(launch_pad_counts(gfill, sa, z.ngroups, gcount, s), "pad counts");
+            DL_CK(launch_exclusive_scan(gcount, sb, z.ngroups + 1, nullptr, b->scan_tmp.p, s),
+                  "slice scan");
+            DL_CK(launch_reset_cursor(redo, sb, z.ngroups, gfill, s), "cursors");
+            ProjectOut po2 = po;
+            po2.slice = sb;
+            po2.gate = redo;
+            po2.overflow = fd.status;
+            DL_CK(launch_project_direct(S.dtype, attrs, z.pp, b->cams_d() + z.cam_first, nv, po2,
+                                        true, s),
+                  "re-emit keys");
+            GroupSlices sl;
+            sl.start = sa;
+            sl.start_alt = sb;
+            sl.use_alt = redo;
+            sl.cursor = gfill;
+            DL_CK(launch_partition_warp(z.G->gwork.as<int4>(), z.G->n_gwork, sl, kWarpCap1,
+                                        kWarpCap2, const_cast<int4*>(fd.items),
+                                        const_cast<int4*>(fd.block_items), meta, nullptr,
+                                        uint32_t(z.key_cap), fd.status, s),
+                  "partition");
+            // the next launch's slices (the items hold this launch's offsets)
+            DL_CK(cudaMemcpyAsync(sa, sb, 4 * size_t(z.ngroups + 1), cudaMemcpyDeviceToDevice, s),
+                  "next slices");
+            continue;
+        }
         ProjectOut po{b->at<float4>(z.o_rec), b->at<uint4>(z.o_meta),
                       reinterpret_cast<unsigned long long*>(meta + 8), gcount};
         DL_CK(launch_project(S.dtype, attrs, z.pp, b->cams_d() + z.cam_first, nv, po, s), "project");
@@ -278,7 +328,11 @@ dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plan
         z.ng_cap = int64_t(D->q.nv) * G->ntiles;
         z.nrays_cap = D->rep.n_rays;
         z.nwork_cap = G->n_gwork;
-        z.key_cap = std::min<int64_t>(int64_t(std::ceil(double(ctx->stats.n_keys) * margin)) + 4096,
+        // room for the slices the keys are emitted into (count + count/8 +
+        // 16 a group) when the projection emits them
+        const int64_t nk = ctx->stats.n_keys;
+        const int64_t laid = nk + nk / 8 + 16 * z.ng_cap;
+        z.key_cap = std::min<int64_t>(int64_t(std::ceil(double(laid) * margin)) + 4096,
                                       (int64_t(1) << 31) - 2);
         longest = std::max<int64_t>(longest, int64_t(std::ceil(double(ctx->stats.max_list) * margin)));
         scan_bytes = std::max(scan_bytes, scan_tmp_bytes(z.ng_cap + 1));
@@ -306,6 +360,7 @@ dl_status dl_batch_create(dl_ctx* ctx, int32_t n_slots, const dl_slot_plan* plan
         z.o_gstart = take(4 * size_t(z.ng_cap + 1));
         z.o_keys = take(8 * size_t(z.key_cap));
         z.o_lists = take(32 * size_t(z.nwork_cap) + 16);  // items, then block items
+        z.o_slices = take(8 * size_t(z.ng_cap + 1));
         z.o_raycol = take(12 * size_t(std::max<int64_t>(z.nrays_cap, 1)));
         z.cam_first = b->total_views;
         b->total_views += z.nv_cap;
@@ -382,6 +437,12 @@ dl_status dl_batch_assign(dl_batch* b, int32_t slot, int32_t scene_id, int32_t d
     z.out = out_dev;
     z.pp = make_project_params(*S, *D, tw, th);
     z.ngroups = ng;
+    z.direct = emit_in_projection(ctx->key_emission, S->n);
+    if (z.direct) {  // empty slices: the first launch emits into slices of its own counts
+        DL_CK(cudaMemsetAsync(b->at<uint32_t>(z.o_slices), 0, 4 * size_t(ng + 1), nullptr),
+              "memset");
+        DL_CK(cudaStreamSynchronize(nullptr), "sync");
+    }
     // identity pose until dl_batch_set_pose
     // a pose on the -z axis at distance 4 until dl_batch_set_pose
     const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, -4, 0, 0, 0, 1};

@@ -111,6 +111,14 @@ struct PendingFrame {
 // slices of the key buffer its next frame emits into: every group gets its
 // key count in the last frame plus an eighth and 16 (slices[cur]); a frame
 // writes the next layout into slices[cur ^ 1] and flips cur.
+// DL_OPT_KEY_EMISSION 2: the projection emits the keys for scenes of at
+// least this many Gaussians (with fewer, too few warps are in flight to hide
+// its waits on the cursor atomics)
+constexpr int64_t kEmitInProjectionMin = 131072;
+inline bool emit_in_projection(int32_t option, int64_t n_gaussians) {
+    return option == 1 || (option == 2 && n_gaussians >= kEmitInProjectionMin);
+}
+
 struct FrameHint {
     bool sized = false;
     int32_t block_cap = 2048;

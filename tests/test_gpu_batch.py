@@ -95,6 +95,42 @@ def test_mixed_batch_equals_single_frames(env):
         b.close()
 
 
+def test_keys_emitted_by_the_projection_in_batches(env):
+    """Slots whose projection emits the keys (forced here: the scenes are
+    below the default's size threshold) give the frames dl_render_frame
+    gives, bit for bit, over several launches and graph replays: the first
+    launch after an assignment emits into empty slices and re-emits on the
+    device, later ones reuse the slices the launch before laid out, and a
+    turn of the light field that outgrows them re-emits again."""
+    r, S, D = env
+    r.set_key_emission("projection")
+    plans = [(S[s], D[d], t, W.light_field_centre(4.0, y)) for s, d, t, y in FRAMES]
+    try:
+        b = r.batch(plans, margin=1.5)
+        try:
+            outs = []
+            for i, (s, d, t, y) in enumerate(FRAMES):
+                outs.append(_out(r, D[d], np.nan))
+                b.assign(i, S[s], D[d], outs[-1], tile=t)
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                for step, dyaw in enumerate((0.5, 0.5, 9.0, -4.0)):
+                    if step == 2:
+                        b.capture()  # the last two launches replay a graph
+                    for i, (s, d, t, y) in enumerate(FRAMES):
+                        b.set_pose(i, W.light_field_centre(4.0, y + dyaw))
+                    b.launch()
+                    assert b.wait() == [0] * len(FRAMES), step
+                    st.synchronize()
+                    for i, (s, d, t, y) in enumerate(FRAMES):
+                        ref = _single(r, S[s], D[d], W.light_field_centre(4.0, y + dyaw), t)
+                        assert np.array_equal(outs[i].cpu().numpy(), ref), (step, i)
+        finally:
+            b.close()
+    finally:
+        r.set_key_emission("auto")
+
+
 def test_batch_matches_oracle_on_a_sample(env):
     r, S, D = env
     tiny = W.WORKLOADS["tiny"]
