@@ -1317,20 +1317,39 @@ __global__ void partition_warp_kernel(const int4* __restrict__ gwork, int64_t n_
     }
     if (status && (*status & 1u)) return;
     const uint32_t* __restrict__ first = S.use_alt && *S.use_alt ? S.start_alt : S.start;
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    // one counter atomic a warp and class: the warp's items of a class stay
+    // together and in group order (consecutive items share records in L2)
+    auto slot = [&](unsigned am, bool mine, uint32_t* counter) -> uint32_t {
+        const unsigned m = __ballot_sync(am, mine);
+        uint32_t base = 0u;
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            if (int(threadIdx.x & 31) == leader) base = atomicAdd(counter, uint32_t(__popc(m)));
+            base = __shfl_sync(am, base, leader);
+        }
+        return base + uint32_t(__popc(m & lt));
+    };
     for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < n_work;
          w += int64_t(gridDim.x) * blockDim.x) {
+        const unsigned am = __activemask();
         const int4 wi = gwork[w];
         const uint32_t st = first[wi.x];
         const uint32_t len = (S.cursor ? S.cursor[wi.x] : S.start[wi.x + 1]) - st;
         const uint32_t nr = uint32_t(wi.z - wi.y);
         const int4 it = make_int4(wi.x, int(st), wi.y, int((nr << 16) | len));
-        if (nr < 65536u && len <= cap1)
-            items[atomicAdd(meta, 1u)] = it;
-        else if (nr < 65536u && len <= cap2)
-            items[n_work - 1 - int64_t(atomicAdd(meta + 4, 1u))] = it;
+        const int cls = nr < 65536u && len <= cap1 ? 0 : (nr < 65536u && len <= cap2 ? 1 : 2);
+        const uint32_t s0 = slot(am, cls == 0, meta);
+        const uint32_t s1 = slot(am, cls == 1, meta + 4);
+        const uint32_t s2 = slot(am, cls == 2, meta + 1);
+        if (cls == 0)
+            items[s0] = it;
+        else if (cls == 1)
+            items[n_work - 1 - int64_t(s1)] = it;
         else
-            block_items[atomicAdd(meta + 1, 1u)] = make_int4(wi.x, int(st), int(w), int(len));
-        atomicMax(meta + 2, len);
+            block_items[s2] = make_int4(wi.x, int(st), int(w), int(len));
+        const uint32_t longest = __reduce_max_sync(am, len);
+        if (int(threadIdx.x & 31) == __ffs(am) - 1) atomicMax(meta + 2, longest);
     }
 }
 
