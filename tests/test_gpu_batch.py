@@ -180,11 +180,18 @@ def test_graph_replay_follows_new_poses(env):
         b.close()
 
 
-def test_key_overflow_is_reported_and_output_kept(env):
+@pytest.mark.parametrize("emission", ["auto", "projection"])
+def test_key_overflow_is_reported_and_output_kept(env, emission):
+    """A slot whose frame needs more keys than its capacity is reported
+    (status bit 0) and its output is left as it was, whether the keys go
+    through the two-pass emission or are emitted by the projection (where
+    the first launch after the assignment re-emits into slices from its own
+    counts, which then exceed the capacity); the other slot is exact."""
     from paper_2407_14053_gb300 import DL_ERR_CAPACITY, DirectLError
     r, S, D = env
     far = W.light_field_centre(14.0, 0.0)
     near = W.light_field_centre(2.2, 0.0)
+    r.set_key_emission(emission)
     b = r.batch([(S[0], D[0], None, far), (S[0], D[0], None, far)], margin=1.0)
     try:
         outs = [_out(r, D[0], -7.0), _out(r, D[0], -7.0)]
@@ -202,6 +209,7 @@ def test_key_overflow_is_reported_and_output_kept(env):
         assert np.array_equal(outs[1].cpu().numpy(), _single(r, S[0], D[0], far, (32, 32)))
     finally:
         b.close()
+        r.set_key_emission("auto")
 
 
 def test_host_side_limits_and_lifetime(env):

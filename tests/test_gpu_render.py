@@ -234,13 +234,16 @@ def _away(distance=4.0):
     return L0
 
 
-def test_frames_after_sizing_run_on_device_counters():
+@pytest.mark.parametrize("emission", ["auto", "projection"])
+def test_frames_after_sizing_run_on_device_counters(emission):
     """After a frame of a (scene, display, mode, tile) has been sized on the
     host, later frames run without a host synchronisation.  Frames that fit
     the capacities equal freshly sized ones bit for bit and report their
     counts; a frame that needs far more tile keys than the sizing frame is
     dropped on the device (output untouched, status bit 0) and the next one
-    is sized again; with a host output the dropped frame is rendered again."""
+    is sized again; with a host output the dropped frame is rendered again.
+    The same with the keys emitted by the projection, where the frame past
+    the capacity outgrows its slices, re-emits, and is dropped there."""
     from paper_2407_14053_gb300 import Renderer
     wl = W.WORKLOADS["tiny"]
     scene = W.make_scene(wl.scene)
@@ -256,6 +259,7 @@ def test_frames_after_sizing_run_on_device_counters():
     assert ref_keys > 65536 * 2
     r = Renderer(0)
     try:
+        r.set_key_emission(emission)
         sid = r.load_gaussians(scene, "f32")
         did = r.set_display(wl.display)
         out = torch.full((wl.display.height, wl.display.width, 3), -7.0, device="cuda")
@@ -280,6 +284,7 @@ def test_frames_after_sizing_run_on_device_counters():
     # frame is rendered again within the call
     r = Renderer(0)
     try:
+        r.set_key_emission(emission)
         sid = r.load_gaussians(scene, "f32")
         did = r.set_display(wl.display)
         host = torch.empty((wl.display.height, wl.display.width, 3)).pin_memory()
