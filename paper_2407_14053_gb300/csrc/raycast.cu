@@ -1,11 +1,13 @@
 // Ray-order 3DGS (Sec. 7, Alg. 3): every required ray is cast through the
 // scene, one thread per ray.  Per ray, each Gaussian it meets gives its point
 // of highest density t_j = (mu - o)^T S^-1 d / (d^T S^-1 d) (Eq. (16)) and
-// alpha_j = o_j G(o + t_j d) (Eq. (17)); a max-heap of capacity c_h keeps the
-// c_h nearest; they are sorted by t and blended front to back with the SH
-// colour at the ray direction.  The ray meets a Gaussian when alpha_j >= 1/255
-// and t_j > 0.2 (the near plane of the rasteriser); the heap orders by
-// (t, index), so the image does not depend on the traversal order.
+// alpha_j = o_j G(o + t_j d) (Eq. (17)); the c_h nearest are kept (Alg. 3
+// keeps them in a max-heap of capacity c_h; here an ascending list of the
+// same capacity, which needs no sort at the end) and blended front to back
+// with the SH colour at the ray direction.  The ray meets a Gaussian when
+// alpha_j >= 1/255 and t_j > 0.2 (the near plane of the rasteriser); the
+// list orders by (t, index), so the image does not depend on the traversal
+// order.
 //
 // Acceleration (Sec. 7: a compact 8-wide bounding-volume hierarchy built with
 // the surface area heuristic): every Gaussian is bounded by the box of its
@@ -17,8 +19,8 @@
 // of at most four Gaussians.  The binary tree is then collapsed into 8-wide
 // nodes: a wide node starts from a binary node's two children and
 // repeatedly opens the child with the largest surface area until it has
-// eight.  Children are visited nearest first, and once the heap is full a
-// node whose box starts beyond the heap's farthest entry is skipped: a
+// eight.  Children are visited nearest first, and once the list is full a
+// node whose box starts beyond the list's farthest entry is skipped: a
 // Gaussian's highest-density point lies inside its ellipsoid, hence inside
 // every box above it.
 #include <cfloat>
@@ -344,7 +346,7 @@ __device__ __forceinline__ float rc_alpha(const float4* __restrict__ gauss, int6
 
 constexpr int kTraceThreads = 128;
 constexpr int kTraceWarps = kTraceThreads / 32;
-constexpr int kHeapTop = 16;  // heap slots 0..15 (its top four levels) in shared memory
+constexpr int kListHead = 16;  // list slots 0..15 (the 16 nearest) in shared memory
 
 // A ray's entry into a box (+inf when it misses the box or the box lies
 // behind the near plane).
@@ -358,18 +360,17 @@ __device__ __forceinline__ float slab_enter(const float4& lo, const float4& hi, 
     return (tn <= tf && tf > kNearT) ? tn : INFINITY;
 }
 
-// A ray's max-heap of its c_h nearest intersections: slots below kHeapTop
-// (the levels every insertion and removal passes through) in shared memory,
-// the rest in the thread's local memory.
-struct RayHeap {
-    unsigned long long* top;  // slot k < kHeapTop at top[32 k]
-    unsigned long long* rest;  // slot k >= kHeapTop at rest[k - kHeapTop]
+// A ray's ascending list of its c_h nearest intersections: slots below
+// kListHead in shared memory, the rest in the thread's local memory.
+struct RayList {
+    unsigned long long* head;  // slot k < kListHead at head[32 k]
+    unsigned long long* rest;  // slot k >= kListHead at rest[k - kListHead]
     __device__ __forceinline__ unsigned long long get(int k) const {
-        return k < kHeapTop ? top[32 * k] : rest[k - kHeapTop];
+        return k < kListHead ? head[32 * k] : rest[k - kListHead];
     }
     __device__ __forceinline__ void set(int k, unsigned long long v) const {
-        if (k < kHeapTop) top[32 * k] = v;
-        else rest[k - kHeapTop] = v;
+        if (k < kListHead) head[32 * k] = v;
+        else rest[k - kListHead] = v;
     }
 };
 
@@ -377,7 +378,7 @@ struct RayHeap {
 // centre and nearly a direction, so they need nearly the same nodes.  A
 // warp-shared stack holds {node or leaf reference, the lanes whose ray hit
 // its box}; a popped node is loaded once for the warp, every lane tests its
-// ray against the eight child boxes (a child beyond the lane's full heap does
+// ray against the eight child boxes (a child beyond the lane's full list does
 // not count as hit), and the children hit by any lane are pushed farthest
 // first by their nearest entry over those lanes.  A leaf is tested by the
 // lanes that hit it.  At most 7 entries a level plus 8 are pending (the
@@ -395,7 +396,7 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
     constexpr int NC = (DEG + 1) * (DEG + 1);
     __shared__ uint32_t s_ref[kTraceWarps][kRayStack];
     __shared__ uint32_t s_lanes[kTraceWarps][kRayStack];
-    __shared__ unsigned long long s_top[kTraceWarps][kHeapTop][32];  // [slot][lane]
+    __shared__ unsigned long long s_head[kTraceWarps][kListHead][32];  // [slot][lane]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const bool valid = i0 < n_rays;
@@ -415,10 +416,10 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
     dx *= dn; dy *= dn; dz *= dn;
     const float ox = cam.c[0], oy = cam.c[1], oz = cam.c[2];
     const float ix = 1.f / dx, iy = 1.f / dy, iz = 1.f / dz;
-    // heap entries packed as t's FP32 bits << 32 | Gaussian index: t > 0, so
+    // list entries packed as t's FP32 bits << 32 | Gaussian index: t > 0, so
     // the integer order of the packed key is the (t, index) order
-    unsigned long long rest[kMaxHeap - kHeapTop];
-    const RayHeap hp{&s_top[warp][0][lane], rest};
+    unsigned long long rest[kMaxHeap - kListHead];
+    const RayList hl{&s_head[warp][0][lane], rest};
     int hn = 0;
     // Transmittance bound: tb is set once the intersections found so far
     // (every one at t <= tmax) multiply T below 5e-5.  Sorted, they alone
@@ -440,8 +441,8 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
         const uint32_t e = st_ref[sp];
         const bool mine = (st_lanes[sp] >> lane) & 1u;
         __syncwarp();
-        const float bound =
-            fminf(tb, hn == heap_cap ? __uint_as_float(uint32_t(hp.get(0) >> 32)) : INFINITY);
+        const float bound = fminf(
+            tb, hn == heap_cap ? __uint_as_float(uint32_t(hl.get(hn - 1) >> 32)) : INFINITY);
         if (e & kRayLeafBit) {  // leaf: Gaussians first .. first + count - 1
             if (mine) {
                 const uint32_t first = (e & ~kRayLeafBit) >> 3, cnt = (e & 7u) + 1u;
@@ -456,35 +457,20 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
                     }
                     const unsigned long long key =
                         (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | g;
-                    if (hn < heap_cap) {  // insert and sift up
-                        int k = hn++;
-                        while (k > 0) {
-                            const int p = (k - 1) >> 1;
-                            const unsigned long long vp = hp.get(p);
-                            if (!(vp < key)) break;
-                            hp.set(k, vp);
-                            k = p;
-                        }
-                        hp.set(k, key);
-                    } else if (key < hp.get(0)) {  // replace the farthest
-                        int k = 0;
-                        for (;;) {
-                            int c = 2 * k + 1;
-                            if (c >= hn) break;
-                            unsigned long long vc = hp.get(c);
-                            if (c + 1 < hn) {
-                                const unsigned long long v2 = hp.get(c + 1);
-                                if (vc < v2) {
-                                    ++c;
-                                    vc = v2;
-                                }
-                            }
-                            if (!(key < vc)) break;
-                            hp.set(k, vc);
-                            k = c;
-                        }
-                        hp.set(k, key);
+                    if (hn == heap_cap) {  // full: drop the farthest if this one is nearer
+                        if (!(key < hl.get(hn - 1))) continue;
+                        --hn;
                     }
+                    // insert into the ascending list: rays find their
+                    // intersections nearly in order, so few entries move
+                    int k = hn++;
+                    while (k > 0) {
+                        const unsigned long long vp = hl.get(k - 1);
+                        if (!(key < vp)) break;
+                        hl.set(k, vp);
+                        --k;
+                    }
+                    hl.set(k, key);
                 }
             }
         } else {  // wide node: its children, nearest first
@@ -508,7 +494,7 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
                         t = slab_enter(make_float4(lxa[k], lya[k], lza[k], 0.f),
                                        make_float4(hxa[k], hya[k], hza[k], 0.f), ox, oy, oz, ix, iy,
                                        iz);
-                        if (t > bound) t = INFINITY;  // beyond a full heap
+                        if (t > bound) t = INFINITY;  // beyond a full list
                     }
                     te[4 * q + k] = t;
                 }
@@ -553,35 +539,13 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
         }
     }
     if (valid) {
-        // pop the heap from its farthest entry: list in ascending (t, index)
-        for (int k = hn - 1; k > 0; --k) {
-            const unsigned long long top = hp.get(0), last = hp.get(k);
-            int j = 0;
-            for (;;) {
-                int c = 2 * j + 1;
-                if (c >= k) break;
-                unsigned long long vc = hp.get(c);
-                if (c + 1 < k) {
-                    const unsigned long long v2 = hp.get(c + 1);
-                    if (vc < v2) {
-                        ++c;
-                        vc = v2;
-                    }
-                }
-                if (!(last < vc)) break;
-                hp.set(j, vc);
-                j = c;
-            }
-            hp.set(j, last);
-            hp.set(k, top);
-        }
         // blend front to back, colour from the SH at the ray direction
         float Y[16];
         sh_basis<DEG>(dx, dy, dz, Y);
         float tr = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;  // transmittance, colour
         for (int k = 0; k < hn; ++k) {
             float t;
-            const int64_t g = int64_t(uint32_t(hp.get(k)));
+            const int64_t g = int64_t(uint32_t(hl.get(k)));
             const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
             const float tn = tr * (1.f - a);
             if (tn < 1e-4f) break;
