@@ -446,31 +446,45 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
         if (e & kRayLeafBit) {  // leaf: Gaussians first .. first + count - 1
             if (mine) {
                 const uint32_t first = (e & ~kRayLeafBit) >> 3, cnt = (e & 7u) + 1u;
-                for (uint32_t g = first; g < first + cnt; ++g) {
-                    float t;
-                    const float a = rc_alpha(gauss, g, ox, oy, oz, dx, dy, dz, t);
-                    if (!(a >= kMinAlpha) || !(t > kNearT) || t > tb) continue;
-                    if (tb == INFINITY) {
-                        prodT *= 1.f - a;
-                        tmax = fmaxf(tmax, t);
-                        if (prodT < 5e-5f) tb = tmax;
+                // the leaf's Gaussians evaluated together (their loads in
+                // flight at once), then taken in order
+                for (uint32_t base = 0; base < cnt; base += kLeafMax) {
+                    float al[kLeafMax], tl[kLeafMax];
+#pragma unroll
+                    for (int q = 0; q < kLeafMax; ++q) {
+                        al[q] = 0.f;
+                        tl[q] = 0.f;
+                        if (base + q < cnt)
+                            al[q] = rc_alpha(gauss, first + base + q, ox, oy, oz, dx, dy, dz, tl[q]);
                     }
-                    const unsigned long long key =
-                        (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | g;
-                    if (hn == heap_cap) {  // full: drop the farthest if this one is nearer
-                        if (!(key < hl.get(hn - 1))) continue;
-                        --hn;
+#pragma unroll
+                    for (int q = 0; q < kLeafMax; ++q) {
+                        if (base + q >= cnt) break;
+                        const uint32_t g = first + base + q;
+                        const float a = al[q], t = tl[q];
+                        if (!(a >= kMinAlpha) || !(t > kNearT) || t > tb) continue;
+                        if (tb == INFINITY) {
+                            prodT *= 1.f - a;
+                            tmax = fmaxf(tmax, t);
+                            if (prodT < 5e-5f) tb = tmax;
+                        }
+                        const unsigned long long key =
+                            (static_cast<unsigned long long>(__float_as_uint(t)) << 32) | g;
+                        if (hn == heap_cap) {  // full: drop the farthest if this one is nearer
+                            if (!(key < hl.get(hn - 1))) continue;
+                            --hn;
+                        }
+                        // insert into the ascending list: rays find their
+                        // intersections nearly in order, so few entries move
+                        int k = hn++;
+                        while (k > 0) {
+                            const unsigned long long vp = hl.get(k - 1);
+                            if (!(key < vp)) break;
+                            hl.set(k, vp);
+                            --k;
+                        }
+                        hl.set(k, key);
                     }
-                    // insert into the ascending list: rays find their
-                    // intersections nearly in order, so few entries move
-                    int k = hn++;
-                    while (k > 0) {
-                        const unsigned long long vp = hl.get(k - 1);
-                        if (!(key < vp)) break;
-                        hl.set(k, vp);
-                        --k;
-                    }
-                    hl.set(k, key);
                 }
             }
         } else {  // wide node: its children, nearest first
@@ -512,26 +526,25 @@ rc_trace_kernel(const float4* __restrict__ gauss, const RayNode* __restrict__ no
                 m += hit[c] ? 1 : 0;
             }
             if (sp + m > kRayStack) m = 0;  // cannot happen (depth checked); keeps the stack in bounds
-            if (lane == 0 && m > 0) {
-                // farthest first: sort the hit children by descending entry
-                uint32_t kk[8], rr[8], ll[8];
-                int k = 0;
+            if (lane < 8 && m > 0) {
+                // farthest first: lane c places child c by its rank in
+                // descending entry (ties by child position)
+                uint32_t my_hit = 0u, my_near = 0u, my_ref = 0u;
+#pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    if (!hit[c]) continue;
-                    int j = k++;
-                    while (j > 0 && kk[j - 1] < near[c]) {
-                        kk[j] = kk[j - 1];
-                        rr[j] = rr[j - 1];
-                        ll[j] = ll[j - 1];
-                        --j;
+                    if (c == lane) {
+                        my_hit = hit[c];
+                        my_near = near[c];
+                        my_ref = chv[c];
                     }
-                    kk[j] = near[c];
-                    rr[j] = chv[c];
-                    ll[j] = hit[c];
                 }
-                for (int j = 0; j < k; ++j) {
-                    st_ref[sp + j] = rr[j];
-                    st_lanes[sp + j] = ll[j];
+                if (my_hit) {
+                    int rank = 0;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        rank += (hit[c] && (near[c] > my_near || (near[c] == my_near && c < lane)));
+                    st_ref[sp + rank] = my_ref;
+                    st_lanes[sp + rank] = my_hit;
                 }
             }
             sp += m;
