@@ -98,6 +98,39 @@ __device__ __forceinline__ bool blend_rec(Acc& a, float px, float py, const floa
     return blend<CHECK_L2, COUNT>(a, px, py, q0, make_float4(q1.x, q1.y, r, g), b);
 }
 
+// blend() of two candidates in list order, their alphas formed together
+// (`two` false: the second is none).  The arithmetic and its order are
+// blend()'s on each candidate in turn; false once the ray is finished.
+template <bool COUNT>
+__device__ __forceinline__ bool blend2(Acc& a, float px, float py, const float4& p0,
+                                       const float4& p1, float pb, const float4& q0,
+                                       const float4& q1, float qb, bool two) {
+    const float la = log2_alpha(px, py, p0.x, p0.y, p0.z, p0.w, p1.x, p1.y);
+    const float lb = log2_alpha(px, py, q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
+    float alpha_a = fminf(0.99f, ex2_approx(la));
+    float alpha_b = fminf(0.99f, ex2_approx(lb));
+    alpha_a = alpha_a < (1.0f / 255.0f) ? 0.f : alpha_a;
+    alpha_b = (alpha_b < (1.0f / 255.0f) || !two) ? 0.f : alpha_b;
+    const float wa0 = alpha_a * a.T;
+    const float Ta = a.T - wa0;
+    const bool goa = Ta >= 1e-4f;
+    const float wa = goa ? wa0 : 0.f;
+    a.c0 = fmaf(wa, p1.z, a.c0);
+    a.c1 = fmaf(wa, p1.w, a.c1);
+    a.c2 = fmaf(wa, pb, a.c2);
+    a.T = goa ? Ta : a.T;
+    const float wb0 = alpha_b * a.T;
+    const float Tb = a.T - wb0;
+    const bool gob = goa && Tb >= 1e-4f;
+    const float wb = gob ? wb0 : 0.f;
+    a.c0 = fmaf(wb, q1.z, a.c0);
+    a.c1 = fmaf(wb, q1.w, a.c1);
+    a.c2 = fmaf(wb, qb, a.c2);
+    a.T = gob ? Tb : a.T;
+    if (COUNT) a.blended += (goa && alpha_a > 0.f) + (gob && alpha_b > 0.f);
+    return gob;
+}
+
 // A record and its pixel box in the shared-memory layout of the batch
 // loaders: s0 = (u, v, A, B), s1 = (C, L, r, g), s2 = (b, -, rect_c, rect_r).
 __device__ __forceinline__ void store_decoded(const float4& q0, const float4& q1, uint2 rect,
@@ -968,9 +1001,13 @@ __device__ __forceinline__ void eval32(const float4* c0, float4* c1, int n, bool
     unsigned mine = (act >> lane) & 1u ? reinterpret_cast<const unsigned*>(T.mask)[lane] : 0u;
     if (COUNT && !done) evals += uint32_t(n);
     while (mine && !done) {  // candidates passed the (widened) test: alpha decides
-        const int sidx = __ffs(mine) - 1;
+        const int s1 = __ffs(mine) - 1;
         mine &= mine - 1;
-        if (!blend<false, COUNT>(a, px, py, c0[sidx], c1[sidx], T.blue[sidx])) done = true;
+        const bool two = mine != 0u;
+        const int s2 = two ? __ffs(mine) - 1 : s1;
+        mine &= mine - 1u;
+        if (!blend2<COUNT>(a, px, py, c0[s1], c1[s1], T.blue[s1], c0[s2], c1[s2], T.blue[s2], two))
+            done = true;
     }
     __syncwarp();
 }
