@@ -253,11 +253,11 @@ dl_status dl_set_tile(dl_ctx* ctx, int32_t mode, int32_t tile_w, int32_t tile_h)
  * exit, so panels are limited to width*height <= 65536 pixels (e.g. 256x256);
  * larger panels, NULL pointers or non-positive sizes return
  * DL_ERR_INVALID_ARG.  The first call on a device, with that device
- * current, looks the array's device address up (make it before any stream
- * capture) and keeps it for the process: a cudaDeviceReset on that device
- * invalidates it, so the call must not be used after one.  Enqueued on
- * `stream`, then synchronises it once to read the ray
- * count.  All calls share the array, which keeps the last call's contents:
+ * current, looks the array's device address up and keeps it for the
+ * process: a cudaDeviceReset on that device invalidates it, so the call must
+ * not be used after one.  Enqueued on `stream`, then synchronises it once to
+ * read the ray count.  All calls share the array, which keeps the last
+ * call's contents:
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and must be serialised by the caller.
  */
