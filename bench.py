@@ -520,74 +520,97 @@ def run_graph_batched(device: int, steps: int, two_pass: bool = False) -> dict:
         torch.cuda.empty_cache()
 
 
+def _time_batch(r, specs, steps: int, device: int):
+    """Loads each (scene spec, display) of `specs`, then times one frame of
+    each per step: the frames rendered together by one launch sequence (one
+    persistent launch per compositing class over all their tile lists)
+    replayed from a captured CUDA graph, against the same frames through one
+    dl_render_frame call each."""
+    import torch
+    S, D, outs = [], [], []
+    for spec, disp in specs:
+        S.append(r.load_gaussians(W.make_scene(spec), spec.dtype))
+        D.append(r.set_display(disp))
+        outs.append(torch.empty((disp.height, disp.width, 3), dtype=torch.float32,
+                                device=f"cuda:{device}"))
+    n = len(specs)
+    poses = W.camera_path(200, 4.0, 10.0)
+    b = r.batch([(S[k], D[k], None, poses[0]) for k in range(n)], margin=1.25)
+    st = torch.cuda.Stream()
+    for k in range(n):
+        b.assign(k, S[k], D[k], outs[k])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        b.capture()
+        for i in range(3):
+            for k in range(n):
+                b.set_pose(k, poses[(i + 40 * k) % 200])
+            b.launch()
+        b.wait()
+        e0.record()
+        for i in range(steps):
+            for k in range(n):
+                b.set_pose(k, poses[(7 * i + 40 * k) % 200])
+            b.launch()
+        e1.record()
+        status = b.wait(raise_on_capacity=False)
+    st.synchronize()
+    graph_ms = e0.elapsed_time(e1) / steps
+    torch.cuda.synchronize()
+    for i in range(2):
+        for k in range(n):
+            r.render(S[k], D[k], poses[(i + 40 * k) % 200], "directl", outs[k])
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(steps):
+        for k in range(n):
+            r.render(S[k], D[k], poses[(7 * i + 40 * k) % 200], "directl", outs[k])
+    e1.record()
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1) / steps
+    bytes_, _ = b.info()
+    b.close()
+    return {"ms_per_launch": graph_ms, "frames_per_s": n * 1e3 / graph_ms,
+            "render_frame_ms_for_all": single_ms, "speedup_over_render_frame": single_ms / graph_ms,
+            "steps": steps, "status": status, "batch_bytes": bytes_}
+
+
 def run_multislot(device: int, steps: int) -> dict:
     """Uneven frames in one batch: a 4K/45-view frame of 1M Gaussians (BF16),
     a 1080p/45-view frame of 200k (FP32) and a 4K/60-view frame of 300k
-    (FP16), rendered together by one launch sequence (one persistent launch
-    per compositing class over all three frames' tile lists) replayed from a
-    captured CUDA graph, against the same three frames through three
-    dl_render_frame calls."""
+    (FP16); and sixteen small frames (240x135 and 480x270 panels, 45 views,
+    four scenes of 5k-40k Gaussians), where one launch per class in place of
+    sixteen frames' launches is what batching saves."""
     import torch
 
     from paper_2407_14053_gb300 import Renderer
     p4k, p1080 = W.WORKLOADS["4k"].display, W.WORKLOADS["1080p"].display
-    specs = [(W.WORKLOADS["4k"].scene, p4k),
+    large = [(W.WORKLOADS["4k"].scene, p4k),
              (W.WORKLOADS["1080p"].scene, p1080),
              (W.SceneSpec(300_000, 3, "clustered", "f16", seed=5), p4k.replace(num_views=60))]
-    r = Renderer(device)
-    try:
-        S, D, outs = [], [], []
-        for spec, disp in specs:
-            S.append(r.load_gaussians(W.make_scene(spec), spec.dtype))
-            D.append(r.set_display(disp))
-            outs.append(torch.empty((disp.height, disp.width, 3), dtype=torch.float32,
-                                    device=f"cuda:{device}"))
-        poses = W.camera_path(200, 4.0, 10.0)
-        b = r.batch([(S[k], D[k], None, poses[0]) for k in range(3)], margin=1.25)
-        st = torch.cuda.Stream()
-        for k in range(3):
-            b.assign(k, S[k], D[k], outs[k])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(st):
-            b.capture()
-            for i in range(3):
-                for k in range(3):
-                    b.set_pose(k, poses[(i + 40 * k) % 200])
-                b.launch()
-            b.wait()
-            e0.record()
-            for i in range(steps):
-                for k in range(3):
-                    b.set_pose(k, poses[(7 * i + 40 * k) % 200])
-                b.launch()
-            e1.record()
-            status = b.wait(raise_on_capacity=False)
-        st.synchronize()
-        graph_ms = e0.elapsed_time(e1) / steps
-        torch.cuda.synchronize()
-        for i in range(2):
-            for k in range(3):
-                r.render(S[k], D[k], poses[(i + 40 * k) % 200], "directl", outs[k])
-        torch.cuda.synchronize()
-        e0.record()
-        for i in range(steps):
-            for k in range(3):
-                r.render(S[k], D[k], poses[(7 * i + 40 * k) % 200], "directl", outs[k])
-        e1.record()
-        torch.cuda.synchronize()
-        single_ms = e0.elapsed_time(e1) / steps
-        bytes_, _ = b.info()
-        b.close()
-        return {"frames": ["4k/45 views, 1M Gaussians bf16", "1080p/45 views, 200k f32",
+    tiny = W.WORKLOADS["tiny"].display
+    small_disp = [tiny, tiny.replace(width=480, height=270)]
+    small = [(W.SceneSpec(n, 3, "clustered", "f16", seed=60 + k), small_disp[k % 2])
+             for k, n in enumerate([5_000, 10_000, 20_000, 40_000] * 4)]
+    out = {}
+    for name, specs in (("large", large), ("small", small)):
+        r = Renderer(device)
+        try:
+            out[name] = _time_batch(r, specs, steps, device)
+        finally:
+            r.close()
+            torch.cuda.empty_cache()
+    res = out["large"]
+    res.update({"frames": ["4k/45 views, 1M Gaussians bf16", "1080p/45 views, 200k f32",
                            "4k/60 views, 300k f16"],
-                "ms_per_launch": graph_ms, "frames_per_s": 3e3 / graph_ms,
-                "render_frame_ms_for_the_three": single_ms,
-                "speedup_over_render_frame": single_ms / graph_ms, "steps": steps,
-                "status": status, "batch_bytes": bytes_,
-                "note": "three uneven frames per launch, captured graph replayed with new poses"}
-    finally:
-        r.close()
-        torch.cuda.empty_cache()
+                "render_frame_ms_for_the_three": res.pop("render_frame_ms_for_all"),
+                "note": "three uneven frames per launch, captured graph replayed with new poses"})
+    sm = out["small"]
+    sm.update({"frames": "16: 240x135 and 480x270 panels, 45 views, scenes of 5k, 10k, 20k, 40k "
+                         "Gaussians (SH3, f16)",
+               "note": "sixteen small frames per launch, captured graph replayed with new poses"})
+    res["small_frames"] = sm
+    return res
 
 
 def run_serving(device: int, n_requests: int = 256, n_scenes: int = 8, util: float = 0.7,
