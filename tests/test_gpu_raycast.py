@@ -1,10 +1,10 @@
 """Ray-order 3DGS (Sec. 7, Alg. 3) on the GPU against the FP64 oracle: the
-DirectL rays of a frame cast through the scene with a heap of c_h nearest
-intersections, full tiny frames, with a small heap (the heap overflows on
-most rays), the default one, and a dense scene with c_h = 40 (the kernel
-collects intersections in passes of 32, so rays there need two passes and
-the second stops part-way); the BF16 case against the oracle on the stored
-values."""
+DirectL rays of a frame cast through the scene keeping the c_h nearest
+intersections, full tiny frames: a small c_h (the kernel's list fills on
+most rays and then drops its farthest entry), the default 128, the
+degenerate c_h = 1 and the largest, 256, and a dense scene with c_h = 40
+(many rays meet more intersections than that); the BF16 case against the
+oracle on the stored values."""
 import os
 
 import numpy as np
@@ -32,9 +32,11 @@ CASES = [
     ("uniform f32, c_h 4", W.SceneSpec(2000, 0, "uniform", "f32", seed=0), 4, 0),
     ("clustered bf16 SH3", W.SceneSpec(3000, 3, "clustered", "bf16", seed=7), 128, 0),
     ("clustered bf16 SH3, off-axis", W.SceneSpec(3000, 3, "clustered", "bf16", seed=7), 16, 1),
-    # four times the density: many rays meet more than one pass's 32
-    # intersections, and c_h = 40 ends the last pass part-way
+    # four times the density: many rays meet more than 40 intersections
     ("uniform f32 dense, c_h 40", W.SceneSpec(8000, 0, "uniform", "f32", seed=3), 40, 0),
+    # the smallest and the largest capacity
+    ("uniform f32 dense, c_h 1", W.SceneSpec(8000, 0, "uniform", "f32", seed=3), 1, 0),
+    ("uniform f32 dense, c_h 256", W.SceneSpec(8000, 0, "uniform", "f32", seed=3), 256, 0),
 ]
 
 
