@@ -73,3 +73,46 @@ def test_heap_capacity_option(renderer):
     for bad in (0, 257):
         with pytest.raises(DirectLError):
             renderer.set_heap_capacity(bad)
+
+
+@pytest.mark.parametrize("case", ["ragged", "neg_slant", "one_gaussian", "three_gaussians",
+                                  "behind"])
+def test_raycast_edge_cases(renderer, case):
+    """Panels not a multiple of the tile, a negative slant, scenes small
+    enough for the tree's root to be one leaf, and every Gaussian behind the
+    cameras (an empty frame)."""
+    d = W.WORKLOADS["tiny"].display
+    n = 400
+    if case == "ragged":
+        d = d.replace(width=37, height=23)
+    elif case == "neg_slant":
+        d = d.replace(tan_slant=-0.21, offset_k=3.3)
+    elif case == "one_gaussian":
+        n = 1
+    elif case == "three_gaussians":
+        n = 3
+    scene = W.make_scene(W.SceneSpec(n, 0, "uniform", "f32", seed=11))
+    if n <= 3:
+        scene["mean"][:] = np.array([[0.0, 0.0, 0.0], [0.3, 0.0, 0.2], [-0.2, 0.1, -0.3]])[:n]
+        scene["log_scale"][:] = -2.0
+        scene["opacity_logit"][:] = 2.0
+    if case == "behind":
+        scene["mean"][:, 2] = -4.5  # every mean behind the cameras (z < -4)
+    sid = renderer.load_gaussians(scene, "f32")
+    did = renderer.set_display(d)
+    L0 = W.light_field_centre(4.0, 0.0)
+    img = renderer.render(sid, did, L0, "raycast")
+    torch.cuda.synchronize()
+    img = img.cpu().numpy().reshape(-1)
+    if case == "behind":
+        assert not img.any()
+    else:
+        V = oracle.view_map(d)
+        src = oracle.repurpose(d, V)
+        ref = oracle.raycast_subpixels(oracle.Scene(scene), d, L0, np.arange(img.size), V, src,
+                                       128)
+        ok, maxerr, nbad, st = envelope.accept(img, ref, TOL, f"raycast {case} tol={TOL:g}")
+        assert nbad == 0, f"{case}: {nbad} of {img.size} outside {TOL}; max |err| {maxerr:.3g}"
+        assert img.max() > 0.1
+    renderer.free_display(did)
+    renderer.free_scene(sid)
